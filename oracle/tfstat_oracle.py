@@ -1,0 +1,332 @@
+"""Plain FP64 CPU oracle for the semi-coherent time-frequency track statistic.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this
+module: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline (and its ``--impl reference`` arm) use it.  It shares no code with
+the CUDA path (no kernels, helpers, tables or constant generators).
+
+What it computes, step by step, each in the plainest form:
+
+* ``sft`` / ``power_table``: the SFTs d~_{alpha,k} of non-overlapping windowed
+  segments and the PSD-normalised power 4 Delta f |d~|^2 / S_n (Sec. II.B, the
+  detection statistic of Eq. (det_stat) and the inner product beneath it,
+  with Delta f = 1/T_SFT), generalised for a window so that noise gives a
+  chi^2 with two degrees of freedom and mean 2.
+* ``svd_basis``: the SVD track basis f_{i,alpha} = sum_p U_{i,p} S_p V_{p,alpha},
+  truncated to K rows of V (Sec. II.C).
+* ``track_x`` / ``bins_and_ties``: f_alpha = f_ref + sum_k xi_k V_{k,alpha}
+  (Sec. II.C) mapped to the nearest SFT bin.
+* ``statistic``: S~ = sum_alpha S_alpha, here with the nearest-bin reading of
+  S_alpha plus an optional +-m neighbour sum (Sec. II.B, Eq. det_stat).
+* ``topk``: keep the best k tracks (Sec. II.D keeps the best 512 of 1024).
+
+Readings where the paper is silent (window, normalisation constant, DC bin,
+rounding rule, tie band, out-of-range bins, segment times, quantised
+storage) are stated beside each function.
+
+Parity pins: every function here is pinned by tests/test_oracle_pins.py
+against closed forms, library routines, brute force or chi^2 moments.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TIE_BAND = 1e-9          # |frac(x) - 1/2| <= TIE_BAND is a rounding tie
+F8_E4M3_MAX = 448.0
+
+DTYPES = ("f32", "bf16", "f16", "f8e4m3")
+
+
+# --------------------------------------------------------------------------
+# Segmentation (Sec. II.B: segments alpha of duration T_SFT, Delta f = 1/T_SFT)
+# --------------------------------------------------------------------------
+def sft_layout(n_samples: int, dt: float, T_sft: float):
+    """Return (L, n_seg, n_bin): L = T_SFT/dt samples per segment (must be an
+    integer), n_seg = floor(n_samples / L) non-overlapping segments (a ragged
+    remainder is dropped), n_bin = L//2 + 1 one-sided bins."""
+    Lf = T_sft / dt
+    L = int(round(Lf))
+    if L < 2 or abs(Lf - L) > 1e-9 * max(1.0, Lf):
+        raise ValueError("T_sft / dt must be an integer >= 2")
+    return L, n_samples // L, L // 2 + 1
+
+
+def segment_times(n_seg: int, T_sft: float):
+    """Reading: t_alpha is the segment midpoint (alpha + 1/2) T_SFT."""
+    return (np.arange(n_seg, dtype=np.float64) + 0.5) * T_sft
+
+
+def window(L: int, kind: str = "hann"):
+    """Reading: the paper names no window; 'hann' is the periodic Hann
+    w[n] = sin^2(pi n / L); 'rect' is all ones."""
+    n = np.arange(L, dtype=np.float64)
+    if kind == "hann":
+        return np.sin(np.pi * n / L) ** 2
+    if kind == "rect":
+        return np.ones(L)
+    raise ValueError(kind)
+
+
+# --------------------------------------------------------------------------
+# DFT (Sec. II.B: d~_{alpha,k} is the SFT of the data in segment alpha)
+# --------------------------------------------------------------------------
+def dft_direct(x):
+    """X_k = sum_n x[n] exp(-2 pi i n k / L), k = 0..L//2, by the definition (O(L^2))."""
+    x = np.asarray(x, dtype=np.float64)
+    L = x.shape[-1]
+    nb = L // 2 + 1
+    out = np.empty(x.shape[:-1] + (nb,), dtype=np.complex128)
+    n = np.arange(L, dtype=np.int64)
+    for k in range(nb):
+        # reduce n k mod L exactly in integers before forming the angle
+        ang = -2.0 * np.pi * ((n * k) % L) / L
+        out[..., k] = x @ np.exp(1j * ang)
+    return out
+
+
+def sft(strain, dt: float, T_sft: float, window_kind: str = "hann", method: str = "fft"):
+    """d~_{alpha,k} = dt sum_n w[n] x[alpha L + n] e^{-2 pi i n k / L} for k = 0..L/2."""
+    strain = np.asarray(strain, dtype=np.float64)
+    L, n_seg, _ = sft_layout(strain.size, dt, T_sft)
+    seg = strain[: n_seg * L].reshape(n_seg, L) * window(L, window_kind)[None, :]
+    X = np.fft.rfft(seg, axis=1) if method == "fft" else dft_direct(seg)
+    return dt * X
+
+
+def power_table(strain, dt: float, T_sft: float, psd_bins, window_kind: str = "hann", method: str = "fft"):
+    """P[alpha,k] = 4 |d~_{alpha,k}|^2 / (dt * sum_n w[n]^2 * S_n(k/T_SFT))  (FP64).
+
+    Readings: this is the paper's 4 Delta f |d~|^2 / S_n with T_SFT = L dt
+    replaced by dt * sum w^2 (equal for the rectangular window) so that
+    Gaussian noise gives P ~ chi^2_2 with mean 2 in every interior bin; the
+    DC bin is set to 0; a bin whose S_n is not finite and positive gives 0.
+    """
+    L, n_seg, n_bin = sft_layout(np.asarray(strain).size, dt, T_sft)
+    d = sft(strain, dt, T_sft, window_kind, method)
+    w = window(L, window_kind)
+    sw2 = float(np.sum(w * w))
+    S = np.asarray(psd_bins, dtype=np.float64)
+    if S.shape != (n_bin,):
+        raise ValueError("psd must have n_bin entries")
+    ok = np.isfinite(S) & (S > 0)
+    denom = np.where(ok, dt * sw2 * np.where(ok, S, 1.0), 1.0)
+    P = 4.0 * (d.real ** 2 + d.imag ** 2) / denom[None, :]
+    P[:, ~ok] = 0.0
+    P[:, 0] = 0.0
+    return P
+
+
+# --------------------------------------------------------------------------
+# Reduced-precision storage of the table (the stored values, dequantised)
+# --------------------------------------------------------------------------
+def _round_to_grid(x, mant_bits: int, emin: int):
+    """Round-to-nearest-even of FP64 values onto a binary floating grid with
+    ``mant_bits`` explicit fraction bits and minimum normal exponent ``emin``
+    (subnormals below 2^emin); no overflow handling."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = (x != 0) & np.isfinite(x)
+    ax = np.abs(x[nz])
+    e = np.floor(np.log2(ax))
+    # guard against log2 rounding at exact powers of two
+    e = np.where(2.0 ** e > ax, e - 1, e)
+    e = np.where(2.0 ** (e + 1) <= ax, e + 1, e)
+    e = np.maximum(e, emin)
+    q = 2.0 ** (e - mant_bits)          # spacing of the grid near ax
+    out[nz] = np.sign(x[nz]) * np.rint(ax / q) * q   # np.rint is ties-to-even
+    out[~np.isfinite(x)] = x[~np.isfinite(x)]
+    return out
+
+
+def round_bf16(x):
+    """FP64 -> bfloat16 (8 exponent bits, 7 fraction bits), round to nearest even; overflow -> inf."""
+    y = _round_to_grid(x, 7, -126)
+    return np.where(np.abs(y) > 3.3895313892515355e38, np.copysign(np.inf, y), y)
+
+
+def round_f16(x):
+    """FP64 -> IEEE binary16 (5 exponent bits, 10 fraction bits), round to nearest even; overflow -> inf."""
+    y = _round_to_grid(x, 10, -14)
+    return np.where(np.abs(y) > 65504.0, np.copysign(np.inf, y), y)
+
+
+def round_f8e4m3(x):
+    """FP64 -> FP8 E4M3 (4 exponent bits, 3 fraction bits, bias 7, max 448, no inf),
+    round to nearest even, saturating at +-448."""
+    y = _round_to_grid(x, 3, -6)
+    return np.clip(y, -F8_E4M3_MAX, F8_E4M3_MAX)
+
+
+def quantise_table(P, dtype: str):
+    """Values the table holds in storage ``dtype``, returned dequantised in FP64,
+    plus the per-segment FP32 scales (FP8 only, else None).
+
+    f32 / bf16 / f16: P rounded to nearest even in that format.
+    f8e4m3: s_alpha = fp32(max_k P[alpha,k] / 448) (1 for an all-zero row),
+    q = e4m3(P / s_alpha) with the division in FP64, dequantised as q * s_alpha.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    if dtype == "f32":
+        return P.astype(np.float32).astype(np.float64), None
+    if dtype == "bf16":
+        return round_bf16(P), None
+    if dtype == "f16":
+        return round_f16(P), None
+    if dtype == "f8e4m3":
+        mx = P.max(axis=1)
+        s = np.where(mx > 0, mx / F8_E4M3_MAX, 1.0).astype(np.float32)
+        q = round_f8e4m3(P / s.astype(np.float64)[:, None])
+        # dequantisation is defined as the FP32 product q * s (q is exact in FP32)
+        deq = (q.astype(np.float32) * s[:, None]).astype(np.float64)
+        return deq, s
+    raise ValueError(dtype)
+
+
+# --------------------------------------------------------------------------
+# SVD basis (Sec. II.C: f_{i,alpha} = sum_p U_{i,p} S_p V_{p,alpha})
+# --------------------------------------------------------------------------
+def svd_basis(F, K: int = 0, tol: float = 1e-7):
+    """Uncentred thin SVD of the training tracks F [M, n_seg] (Hz at t_alpha).
+
+    Returns (V_K [K, n_seg] with orthonormal rows, sigma [K], cmin [K], cmax [K])
+    where the coefficients of the training tracks are C = F V_K^T and the
+    candidate box is their per-coefficient min/max.  K = 0 picks the smallest
+    K whose worst training-track relative reconstruction error
+    max_alpha |F - C V_K| / max_alpha |F| is <= tol.  Signs are fixed so that
+    the entry of largest magnitude in each row of V_K is positive.
+    """
+    F = np.asarray(F, dtype=np.float64)
+    _, s, Vt = np.linalg.svd(F, full_matrices=False)
+    if K <= 0:
+        K = Vt.shape[0]
+        fmax = np.max(np.abs(F), axis=1)
+        for k in range(1, Vt.shape[0] + 1):
+            R = F - (F @ Vt[:k].T) @ Vt[:k]
+            if np.max(np.max(np.abs(R), axis=1) / fmax) <= tol:
+                K = k
+                break
+    V = Vt[:K].copy()
+    for k in range(K):
+        j = int(np.argmax(np.abs(V[k])))
+        if V[k, j] < 0:
+            V[k] = -V[k]
+    C = F @ V.T
+    return V, s[:K].copy(), C.min(axis=0), C.max(axis=0)
+
+
+def reconstruction_error(F, V):
+    """Per-track relative error max_alpha |F - F V^T V| / max_alpha |F|."""
+    F = np.asarray(F, dtype=np.float64)
+    R = F - (F @ V.T) @ V
+    return np.max(np.abs(R), axis=1) / np.max(np.abs(F), axis=1)
+
+
+# --------------------------------------------------------------------------
+# Track -> bin (Sec. II.C: f_alpha = sum_p xi_p V_{p,alpha}, plus an offset f_ref)
+# --------------------------------------------------------------------------
+def track_x(V, coeffs, f_ref, T_sft: float):
+    """x_{t,alpha} = (f_ref[t] + sum_k c[t,k] V[k,alpha]) * T_SFT in FP64.
+
+    The sum runs k = 0..K-1 left to right, each product and sum rounded
+    separately (no fused multiply-add), then the frequency is scaled by T_SFT.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    c = np.asarray(coeffs, dtype=np.float64)
+    f = np.array(np.asarray(f_ref, dtype=np.float64)[:, None] * np.ones((1, V.shape[1])))
+    for k in range(V.shape[0]):
+        f = f + c[:, k : k + 1] * V[k][None, :]
+    return f * T_sft
+
+
+def bins_and_ties(x):
+    """Reading: bin k is centred at k / T_SFT, so b = floor(x + 1/2); a tie is
+    |x - floor(x) - 1/2| <= 1e-9.  A non-finite x maps to no bin (returned as
+    a huge sentinel that lies outside every table) and is never a tie."""
+    x = np.asarray(x, dtype=np.float64)
+    fin = np.isfinite(x)
+    xs = np.where(fin, x, 0.0)
+    z = np.floor(xs + 0.5)
+    big = 2.0 ** 62
+    b = np.where(fin, np.clip(z, -big, big), big).astype(np.int64)
+    tie = fin & (np.abs(xs - np.floor(xs) - 0.5) <= TIE_BAND)
+    return b, tie
+
+
+# --------------------------------------------------------------------------
+# The statistic (Sec. II.B, Eq. det_stat, nearest-bin reading with +-m neighbours)
+# --------------------------------------------------------------------------
+def statistic(P, b, m: int):
+    """S[t] = sum_alpha sum_{j=-m..m} P[alpha, b[t,alpha] + j] in FP64; a bin
+    outside [0, n_bin) contributes 0 (no clamping)."""
+    P = np.asarray(P, dtype=np.float64)
+    n_seg, n_bin = P.shape
+    b = np.asarray(b, dtype=np.int64)
+    S = np.zeros(b.shape[0], dtype=np.float64)
+    rows = np.arange(n_seg)[None, :]
+    for j in range(-m, m + 1):
+        idx = b + j
+        ok = (idx >= 0) & (idx < n_bin)
+        vals = P[rows, np.where(ok, idx, 0)]
+        S += np.sum(np.where(ok, vals, 0.0), axis=1)
+    return S
+
+
+def statistic_loop(P, b, m: int):
+    """The same sum written as plain Python loops (small cases only)."""
+    n_seg, n_bin = len(P), len(P[0])
+    out = []
+    for row in b:
+        s = 0.0
+        for a in range(n_seg):
+            for j in range(-m, m + 1):
+                k = int(row[a]) + j
+                if 0 <= k < n_bin:
+                    s += float(P[a][k])
+        out.append(s)
+    return np.array(out)
+
+
+# --------------------------------------------------------------------------
+# Top-k (Sec. II.D keeps the highest-scoring half of the population)
+# --------------------------------------------------------------------------
+def topk(S, k: int):
+    """The k largest S by a stable sort on (-S, index): equal values keep the
+    lower index first, -0.0 equals +0.0 and NaN ranks below every number."""
+    S = np.asarray(S, dtype=np.float64)
+    k = min(int(k), S.size)
+    nan = np.isnan(S)
+    key = np.where(nan, 0.0, -S) + 0.0   # + 0.0 turns -0.0 into +0.0
+    order = np.lexsort((np.arange(S.size), key, nan))
+    idx = order[:k]
+    return idx.astype(np.int64), S[idx]
+
+
+# --------------------------------------------------------------------------
+# The whole statistic call
+# --------------------------------------------------------------------------
+def eval_stat(P, V, coeffs, f_ref, T_sft: float, m: int, k: int = 0, chunk: int = 4096):
+    """S [N] (FP64), top-k (idx, val) and the list of tie (t, alpha) pairs."""
+    coeffs = np.asarray(coeffs, dtype=np.float64)
+    f_ref = np.asarray(f_ref, dtype=np.float64)
+    N = coeffs.shape[0]
+    S = np.empty(N)
+    ties = []
+    for s0 in range(0, N, chunk):
+        s1 = min(N, s0 + chunk)
+        x = track_x(V, coeffs[s0:s1], f_ref[s0:s1], T_sft)
+        b, tie = bins_and_ties(x)
+        S[s0:s1] = statistic(P, b, m)
+        tt, aa = np.nonzero(tie)
+        ties.extend(zip((tt + s0).tolist(), aa.tolist()))
+    idx, val = topk(S, k) if k > 0 else (np.zeros(0, np.int64), np.zeros(0))
+    return S, idx, val, ties
+
+
+def stat_relative_error(S_test, S_ref):
+    """max_t |S_test - S_ref| / |S_ref| (|S_ref| = 0 compares absolutely)."""
+    S_test = np.asarray(S_test, dtype=np.float64)
+    S_ref = np.asarray(S_ref, dtype=np.float64)
+    den = np.where(S_ref != 0, np.abs(S_ref), 1.0)
+    return float(np.max(np.abs(S_test - S_ref) / den)) if S_ref.size else 0.0

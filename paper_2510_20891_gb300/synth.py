@@ -1,0 +1,224 @@
+"""Seeded synthetic inputs for the semi-coherent track statistic.
+
+This module only draws inputs: strain time series (noise plus an injected
+single harmonic), training frequency tracks for the basis, and candidate
+track coefficients.  It holds none of the statistic's arithmetic (no SFT,
+no normalisation, no track->bin mapping, no gather), so the FP64 oracle and
+the CUDA path can both be fed from it without sharing any method code.
+
+The workloads follow the paper's setting (Sec. II.E): a single harmonic in
+stationary Gaussian noise with a known PSD, sampled every few seconds for up
+to one year.  The paper's own EMRI trajectories (Eq. 3, computed with an
+external package) are not available, so the frequency families below are
+analytic stand-ins: quadratic chirps and the power law f0 (1 - t/tau)^-p.
+
+Every generator takes a numpy ``Generator`` (PCG64, platform independent).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+YEAR_S = 365.0 * 86400.0          # 31,536,000 s: the one-year workloads
+JULIAN_YEAR_S = 365.25 * 86400.0  # the paper's year (Sec. II.B segment counts)
+
+
+# --------------------------------------------------------------------------
+# Power spectral densities (one-sided, Hz^-1)
+# --------------------------------------------------------------------------
+def psd_white(f, sigma: float = 1.0, dt: float = 1.0):
+    """One-sided PSD of white noise with per-sample std sigma: S_n = 2 sigma^2 dt."""
+    f = np.asarray(f, dtype=np.float64)
+    return np.full(f.shape, 2.0 * sigma * sigma * dt)
+
+
+def psd_oneyear(f):
+    """S_n(f) = 1e-40 [1 + (2e-3/f)^4] [1 + (f/2.5e-2)^2]; infinite at f = 0."""
+    f = np.asarray(f, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        s = 1e-40 * (1.0 + (2e-3 / f) ** 4) * (1.0 + (f / 2.5e-2) ** 2)
+    return np.where(f > 0, s, np.inf)
+
+
+def psd_bins(psd_fn, n_bin: int, T_sft: float):
+    """PSD sampled at the SFT bin frequencies k / T_sft, k = 0..n_bin-1."""
+    return psd_fn(np.arange(n_bin, dtype=np.float64) / T_sft)
+
+
+# --------------------------------------------------------------------------
+# Noise
+# --------------------------------------------------------------------------
+def white_noise(n: int, sigma: float, rng: np.random.Generator):
+    return sigma * rng.standard_normal(n)
+
+
+def coloured_noise(n: int, dt: float, psd_fn, rng: np.random.Generator):
+    """Stationary Gaussian noise with one-sided PSD ``psd_fn`` (frequency-domain synthesis).
+
+    The real FFT bins are complex Gaussians with E|X_k|^2 = S_n(f_k) n / (2 dt)
+    (the Nyquist bin, for even n, is real with the same second moment); the DC
+    bin is zero.  For white noise this reproduces per-sample variance sigma^2.
+    """
+    nf = n // 2 + 1
+    f = np.arange(nf, dtype=np.float64) / (n * dt)
+    s = psd_fn(f)
+    s = np.where(np.isfinite(s), s, 0.0)
+    var = s * n / (2.0 * dt)
+    X = np.sqrt(var / 2.0) * (rng.standard_normal(nf) + 1j * rng.standard_normal(nf))
+    X[0] = 0.0
+    if n % 2 == 0:
+        X[-1] = np.sqrt(var[-1]) * rng.standard_normal()
+    return np.fft.irfft(X, n=n)
+
+
+# --------------------------------------------------------------------------
+# Injected single harmonic
+# --------------------------------------------------------------------------
+def chirp_signal(n: int, dt: float, f0: float, fdot: float, amp: float, phi0: float = 0.0):
+    """h(t) = amp cos(2 pi (f0 t + fdot t^2 / 2) + phi0): instantaneous frequency f0 + fdot t."""
+    t = np.arange(n, dtype=np.float64) * dt
+    return amp * np.cos(2.0 * np.pi * (f0 * t + 0.5 * fdot * t * t) + phi0)
+
+
+def powerlaw_freq(t, f0: float, tau: float, p: float):
+    """f(t) = f0 (1 - t/tau)^(-p), the one-year family's frequency evolution."""
+    t = np.asarray(t, dtype=np.float64)
+    return f0 * (1.0 - t / tau) ** (-p)
+
+
+def powerlaw_phase(t, f0: float, tau: float, p: float):
+    """Phi(t) = 2 pi int_0^t f = 2 pi f0 tau / (1-p) [1 - (1 - t/tau)^(1-p)]."""
+    t = np.asarray(t, dtype=np.float64)
+    return 2.0 * np.pi * f0 * tau / (1.0 - p) * (1.0 - (1.0 - t / tau) ** (1.0 - p))
+
+
+def powerlaw_signal(n: int, dt: float, f0: float, tau: float, p: float, a0: float, phi0: float = 0.0):
+    """h(t) = a(t) cos(Phi(t) + phi0) with slowly varying a(t) = a0 (f(t)/f0)^(2/3)."""
+    t = np.arange(n, dtype=np.float64) * dt
+    f = powerlaw_freq(t, f0, tau, p)
+    a = a0 * (f / f0) ** (2.0 / 3.0)
+    return a * np.cos(powerlaw_phase(t, f0, tau, p) + phi0)
+
+
+def snr_of_amplitude(a_t, f_t, dt: float, psd_fn):
+    """SNR^2 = int a(t)^2 / S_n(f(t)) dt for a slowly varying harmonic (rectangle rule)."""
+    return math.sqrt(float(np.sum(a_t * a_t / psd_fn(f_t)) * dt))
+
+
+def powerlaw_amplitude_for_snr(n: int, dt: float, f0: float, tau: float, p: float, snr: float, psd_fn):
+    t = np.arange(n, dtype=np.float64) * dt
+    f = powerlaw_freq(t, f0, tau, p)
+    shape = (f / f0) ** (2.0 / 3.0)
+    return snr / snr_of_amplitude(shape, f, dt, psd_fn)
+
+
+# --------------------------------------------------------------------------
+# Frequency-track families for the basis and candidate coefficients
+# --------------------------------------------------------------------------
+def segment_midpoints(n_seg: int, T_sft: float):
+    """t_alpha = (alpha + 1/2) T_sft, relative to the first sample."""
+    return (np.arange(n_seg, dtype=np.float64) + 0.5) * T_sft
+
+
+def quad_chirp_tracks(M: int, t_alpha, rng: np.random.Generator,
+                      f0=(4e-3, 6e-3), fdot=(0.0, 2e-9), fddot=(0.0, 1e-16)):
+    """f(t) = f0 + fdot t + fddot t^2 / 2 with uniform draws; rows are tracks [M, n_seg]."""
+    a = rng.uniform(*f0, size=M)
+    b = rng.uniform(*fdot, size=M)
+    c = rng.uniform(*fddot, size=M)
+    t = np.asarray(t_alpha, dtype=np.float64)[None, :]
+    return a[:, None] + b[:, None] * t + 0.5 * c[:, None] * t * t
+
+
+def powerlaw_params(M: int, rng: np.random.Generator,
+                    f0=(2e-3, 8e-3), tau_yr=(1.5, 5.0), p=(0.25, 0.4)):
+    return (rng.uniform(*f0, size=M), rng.uniform(*tau_yr, size=M) * YEAR_S, rng.uniform(*p, size=M))
+
+
+def powerlaw_tracks(M: int, t_alpha, rng: np.random.Generator, **kw):
+    f0, tau, p = powerlaw_params(M, rng, **kw)
+    t = np.asarray(t_alpha, dtype=np.float64)[None, :]
+    return f0[:, None] * (1.0 - t / tau[:, None]) ** (-p[:, None])
+
+
+def uniform_coeffs(N: int, cmin, cmax, rng: np.random.Generator):
+    """Candidate coefficients drawn uniformly inside the box [cmin, cmax] (one row per track)."""
+    cmin = np.asarray(cmin, dtype=np.float64)
+    cmax = np.asarray(cmax, dtype=np.float64)
+    return cmin[None, :] + (cmax - cmin)[None, :] * rng.random((N, cmin.size))
+
+
+# --------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Workload:
+    name: str
+    dt: float
+    n_samples: int
+    T_sft: float
+    K: int
+    n_tracks: int
+    m: int
+    n_train: int
+    family: str          # "quad" or "powerlaw"
+    psd: str             # "white" or "oneyear"
+    seed: int = 0
+
+    @property
+    def L(self):
+        return int(round(self.T_sft / self.dt))
+
+    @property
+    def n_seg(self):
+        return self.n_samples // self.L
+
+    @property
+    def n_bin(self):
+        return self.L // 2 + 1
+
+    def psd_fn(self):
+        if self.psd == "white":
+            return lambda f: psd_white(f, 1.0, self.dt)
+        return psd_oneyear
+
+
+WORKLOADS = {
+    # 2^18 s of unit white noise, 64 x 4096-s segments, K = 3 quadratic-chirp basis, nearest bin.
+    "tiny_white_2p18": Workload("tiny_white_2p18", 1.0, 1 << 18, 4096.0, 3, 10_000, 0, 1000, "quad", "white"),
+    # one year at 5 s, 365 daily segments x 8641 bins, K = 6 power-law basis, +-1-bin neighbours.
+    "oneyear_daily_fp32": Workload("oneyear_daily_fp32", 5.0, 6_307_200, 86400.0, 6, 10_000_000, 1, 5000,
+                                   "powerlaw", "oneyear"),
+    # finer resolution: 1577 x 20000-s segments x 20001 bins (sampled at 0.5 s so segments are full).
+    "oneyear_fine_1577x20001": Workload("oneyear_fine_1577x20001", 0.5, 1577 * 40000, 20000.0, 6,
+                                        100_000_000, 1, 5000, "powerlaw", "oneyear"),
+}
+
+
+def make_strain(w: Workload, rng: np.random.Generator, snr: float | None = None, inject: bool = True):
+    """Noise plus one injected harmonic for a named workload; returns (strain, injection dict)."""
+    n, dt = w.n_samples, w.dt
+    if w.psd == "white":
+        x = white_noise(n, 1.0, rng)
+        inj = dict(kind="chirp", f0=5e-3, fdot=1e-9, amp=0.05)
+        if inject:
+            x = x + chirp_signal(n, dt, inj["f0"], inj["fdot"], inj["amp"])
+        return x, inj
+    x = coloured_noise(n, dt, psd_oneyear, rng)
+    f0, tau, p = powerlaw_params(1, rng)
+    inj = dict(kind="powerlaw", f0=float(f0[0]), tau=float(tau[0]), p=float(p[0]), snr=30.0 if snr is None else snr)
+    if inject:
+        a0 = powerlaw_amplitude_for_snr(n, dt, inj["f0"], inj["tau"], inj["p"], inj["snr"], psd_oneyear)
+        inj["a0"] = a0
+        x = x + powerlaw_signal(n, dt, inj["f0"], inj["tau"], inj["p"], a0)
+    return x, inj
+
+
+def make_training_tracks(w: Workload, rng: np.random.Generator, M: int | None = None):
+    t = segment_midpoints(w.n_seg, w.T_sft)
+    M = w.n_train if M is None else M
+    if w.family == "quad":
+        return quad_chirp_tracks(M, t, rng)
+    return powerlaw_tracks(M, t, rng)
