@@ -1,0 +1,194 @@
+/*
+ * tfstat.h -- C ABI of the GB300 library for the semi-coherent time-frequency
+ * track statistic of arXiv:2510.20891 ("Ab uno disce omnes: single-harmonic
+ * search for extreme mass-ratio inspirals").
+ *
+ * The method (paper Sec. II.B-II.D):
+ *   1. Cut the strain into non-overlapping segments of duration T_SFT, window
+ *      each and Fourier transform it (the SFTs d~_{alpha,k}, Delta f = 1/T_SFT).
+ *   2. Normalise the power by the known PSD: P[alpha,k] = 4 Delta f |d~|^2 / S_n,
+ *      generalised here for a window (see tfs_build_sfts).
+ *   3. Model a frequency track with an SVD basis, f_alpha = f_ref + sum_k c_k U_{k,alpha}
+ *      (Sec. II.C), evaluated at the segment midpoints t_alpha = (alpha + 1/2) T_SFT.
+ *   4. Sum the normalised power along the track, nearest bin b = floor(f T_SFT + 1/2)
+ *      plus +-m neighbours: S = sum_alpha sum_{|j|<=m} P[alpha, b_alpha + j]
+ *      (Eq. det_stat in its nearest-bin, non-chirping reading).
+ *   5. Keep the k best tracks (Sec. II.D keeps the best 512 of 1024 walkers).
+ *
+ * Conventions for every entry point:
+ *   - Return value: TFS_OK (0) or a negative TFS_ERR_* code; tfs_last_error()
+ *     then gives a human-readable reason (thread-local string).
+ *   - Nothing is written to caller buffers when a call fails validation.
+ *   - Ownership: the caller owns every buffer it passes; the library owns the
+ *     handles (tfs_table, tfs_basis) it returns, released with *_free.
+ *   - mem = TFS_MEM_HOST: all array arguments are host pointers; the call copies
+ *     inputs to the device, computes, copies results back and returns only
+ *     when they are in place.  mem = TFS_MEM_DEVICE: all array arguments are
+ *     device pointers of the current device; work is enqueued on `stream`
+ *     (a cudaStream_t, NULL = legacy default stream) and the call returns
+ *     without waiting, except where an entry point says otherwise.
+ *   - Handles are bound to the device that was current when they were made.
+ *   - Row-major layouts throughout; indices are 0-based.
+ */
+#ifndef TFSTAT_H_
+#define TFSTAT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TFS_OK 0
+#define TFS_ERR_INVALID_ARG (-1) /* shape, pointer, enum or range violation */
+#define TFS_ERR_OOM (-2)         /* device or host allocation failed, or over budget */
+#define TFS_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define TFS_ERR_TIMEOUT (-4)     /* a bounded device wait gave up; the context stays usable */
+#define TFS_ERR_BUSY (-5)        /* resource in use (e.g. server queue full) */
+#define TFS_ERR_NOT_FOUND (-6)   /* unknown id or ticket */
+
+/* ---- enums ------------------------------------------------------------- */
+#define TFS_F32 0    /* table storage: IEEE binary32 */
+#define TFS_BF16 1   /* bfloat16, round to nearest even */
+#define TFS_F16 2    /* IEEE binary16, round to nearest even (overflow -> inf) */
+#define TFS_F8E4M3 3 /* FP8 E4M3 with a per-segment FP32 scale s_alpha = max_k P / 448 */
+
+#define TFS_WINDOW_RECT 0 /* w[n] = 1 */
+#define TFS_WINDOW_HANN 1 /* periodic Hann, w[n] = sin^2(pi n / L) */
+
+#define TFS_MEM_HOST 0
+#define TFS_MEM_DEVICE 1
+
+typedef struct tfs_table tfs_table; /* device-resident normalised power table */
+typedef struct tfs_basis tfs_basis; /* device-resident track basis U [K][n_seg] (FP64) */
+
+/* Ties of the track->bin rounding (|frac(x) - 1/2| <= 1e-9, x = f T_SFT).
+ * The caller sets `capacity` and the two host arrays (or NULL with capacity 0);
+ * the library writes `count` (total ties) and `n_stored` = min(count, capacity)
+ * entries (track index, segment index) in unspecified order. */
+typedef struct {
+  int64_t count;
+  int32_t n_stored;
+  int32_t capacity;
+  int64_t* track;
+  int32_t* seg;
+} tfs_tie_report;
+
+/* ---- housekeeping ------------------------------------------------------ */
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int tfs_version(void);
+/* Reason for the last failing call on this thread ("" if none). Never NULL. */
+const char* tfs_last_error(void);
+
+/* ---- step 1-2: strain -> normalised power table (paper Sec. II.B, II.E) --
+ * strain [n] FP64 samples at spacing dt seconds.  L = T_sft/dt must be an
+ * even integer >= 4 with prime factors 2, 3, 5 only and L <= 2^20
+ * (else INVALID_ARG); n_seg = floor(n / L) segments (the ragged tail is
+ * dropped; 1 <= n_seg <= 65535 required); n_bin = L/2 + 1 bins at frequencies k / T_sft.
+ * psd [n_bin] FP64: the one-sided PSD S_n(k / T_sft) in Hz^-1.
+ * Output P[alpha][k] = 4 |d~_{alpha,k}|^2 / (dt * sum_n w[n]^2 * S_n(k/T_sft)),
+ * d~_{alpha,k} = dt sum_n w[n] x[alpha L + n] exp(-2 pi i n k / L), which is
+ * the paper's 4 Delta f |d~|^2 / S_n for the rectangular window and gives
+ * chi^2_2 (mean 2) noise power for any window.  P[alpha][0] = 0 and P = 0
+ * wherever S_n is not finite and positive.  Computed in FP64, stored in
+ * `dtype` (TFS_F32 / BF16 / F16 / F8E4M3).  mem refers to strain and psd.
+ * Synchronous: returns when the table is complete. */
+int tfs_build_sfts(const double* strain, int64_t n, double dt, double T_sft, int window, const double* psd,
+                   int dtype, int mem, void* stream, tfs_table** out);
+
+/* Recompute an existing table (made by tfs_build_sfts) from new strain of
+ * the same length in segments, with the dt, T_sft, window, PSD and dtype
+ * given at build time.  Allocates only stream-ordered scratch.  mem = DEVICE:
+ * enqueued on `stream`, returns without waiting (unless stream is NULL);
+ * mem = HOST: returns when done.  INVALID_ARG if n / L differs from n_seg or
+ * the table was not built from strain. */
+int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, int mem, void* stream);
+
+/* Wrap an existing FP64 power table P [n_seg][n_bin] (e.g. computed elsewhere)
+ * as a table stored in `dtype`, quantised exactly as tfs_build_sfts does.
+ * Synchronous. */
+int tfs_table_from_power(const double* P, int64_t n_seg, int64_t n_bin, double T_sft, int dtype, int mem,
+                         void* stream, tfs_table** out);
+
+/* Shape and storage of a table. Any output pointer may be NULL. row_stride is
+ * the element pitch of a row on the device (>= n_bin, a multiple of 32). */
+int tfs_table_info(const tfs_table* t, int64_t* n_seg, int64_t* n_bin, int* dtype, double* T_sft,
+                   int64_t* row_stride);
+
+/* Copy the table out to host memory as FP64 dequantised values P [n_seg][n_bin]
+ * (FP8: q * s_alpha in FP32, widened) and, for FP8, the scales [n_seg] (may be NULL). */
+int tfs_table_to_host(const tfs_table* t, double* P, float* scales);
+
+/* Device bytes held by the table. */
+int64_t tfs_table_bytes(const tfs_table* t);
+
+int tfs_table_free(tfs_table* t);
+
+/* ---- track basis (paper Sec. II.C) --------------------------------------
+ * tracks [M][n_seg] FP64: training frequency tracks (Hz) at t_alpha.
+ * Uncentred truncated SVD F = U S V^T; the basis is the first K rows of V^T
+ * (orthonormal rows, the paper's V_{p,alpha}), sign-fixed so the entry of
+ * largest magnitude of each row is positive.  K = 0 chooses the smallest K
+ * (<= min(M, n_seg, 32)) for which every training track reconstructs with
+ * max_alpha |F - F V^T V| / max_alpha |F| <= tol.  Also records the singular
+ * values and the box [cmin_k, cmax_k] of the training projections C = F V^T.
+ * Computed with FP64 kernels (randomised range finder with power iterations)
+ * plus host Gram-Schmidt and one-sided Jacobi on the thin factors.
+ * 0 <= K <= min(M, n_seg, 32).  Synchronous. */
+int tfs_build_basis(const double* tracks, int64_t M, int64_t n_seg, int K, double tol, int mem, void* stream,
+                    tfs_basis** out);
+
+/* Wrap a given basis U [K][n_seg] (host FP64, rows need not be orthonormal). */
+int tfs_basis_from_host(const double* U, int K, int64_t n_seg, tfs_basis** out);
+
+int tfs_basis_info(const tfs_basis* b, int* K, int64_t* n_seg);
+
+/* Copy out U [K][n_seg], sigma [K], cmin [K], cmax [K] (host; any may be NULL;
+ * sigma/cmin/cmax are zeros for a basis made by tfs_basis_from_host). */
+int tfs_basis_to_host(const tfs_basis* b, double* U, double* sigma, double* cmin, double* cmax);
+
+int tfs_basis_free(tfs_basis* b);
+
+/* ---- steps 3-5: the statistic over a batch of tracks --------------------
+ * coeffs [N][K] FP64 (K of the basis), f_ref [N] FP64 (Hz) or NULL for zeros.
+ * Track t: f_{t,alpha} = f_ref[t] + sum_k coeffs[t][k] U[k][alpha], x = f T_sft,
+ * b = floor(x + 1/2).  The bin equals the one FP64 arithmetic gives when
+ * the sum is formed left to right with each product and sum rounded
+ * separately (the GPU resolves every case that FP32 cannot decide in that
+ * FP64 order).  stat[t] = sum_alpha sum_{j=-m..m} P[alpha][b+j] with bins
+ * outside [0, n_bin) contributing 0 and non-finite x contributing 0,
+ * accumulated in FP32 from the stored (dequantised) values.  0 <= m <= 64.
+ * topk in [0, 1024]: if > 0, top_idx/top_val [min(topk, N)] receive the
+ * largest stat values in descending order (ties: lower index first; NaN
+ * lowest).  ties may be NULL; if given, the call waits for completion to
+ * fill it (even with mem = DEVICE).  The basis must have n_seg equal to the
+ * table's.  N may be 0.  stat may be NULL only if topk > 0 (then the
+ * per-track values are kept in library scratch). */
+int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis, const double* coeffs, const double* f_ref,
+                  int64_t N, int m, int topk, float* stat, int64_t* top_idx, float* top_val, tfs_tie_report* ties,
+                  int mem, void* stream);
+
+/* ---- step 4 alone, for verification: the bin of every (track, segment) ----
+ * Runs the same fused kernel as tfs_eval_stat and writes bins [N][n_seg]
+ * (int32): the bin b = floor(f T_sft + 1/2) whenever the window b-m..b+m
+ * overlaps [0, n_bin); INT32_MIN if it lies wholly below bin 0, INT32_MAX if
+ * wholly above the table or x is not finite.  N * n_seg < 2^34.  Synchronous. */
+int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis, const double* coeffs, const double* f_ref,
+                  int64_t N, int m, int32_t* bins, int mem, void* stream);
+
+/* Number of kernels this library has launched in this process (all devices). */
+long long tfs_kernel_launches(void);
+
+/* ---- step 5 alone: top-k of a float array ---------------------------------
+ * k in [1, 1024], 1 <= N < 2^31.  Writes min(k, N) entries of idx (int64) and
+ * val in descending order of val; equal values keep the lower index first,
+ * -0.0 equals +0.0, NaN ranks below every number.  Device scratch (about
+ * 8 KB plus 16 bytes per 2048 elements) is allocated stream-ordered per call. */
+int tfs_topk(const float* val_in, int64_t N, int k, int64_t* idx, float* val, int mem, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFSTAT_H_ */

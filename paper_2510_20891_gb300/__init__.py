@@ -1,0 +1,240 @@
+"""GB300-native semi-coherent time-frequency track statistic (arXiv:2510.20891).
+
+A thin ctypes binding over ``libtfstat.so`` (include/tfstat.h): every step of
+the computation runs in the library's CUDA kernels; this module only
+marshals arguments.  Functions keep the C names without the ``tfs_`` prefix:
+
+* ``build_sfts(strain, dt, T_sft, psd, window="hann", dtype="f32")`` -> ``Table``
+* ``table_from_power(P, T_sft, dtype="f32")`` -> ``Table``
+* ``build_basis(tracks, K=0, tol=1e-7)`` -> ``Basis``;  ``basis_from_host(U)`` -> ``Basis``
+* ``eval_stat(table, basis, coeffs, f_ref=None, m=0, topk=0, ...)`` -> ``EvalResult``
+* ``topk(values, k)`` -> (idx, val)
+
+Array arguments are numpy arrays (host memory: the call copies in and out
+and returns when done) or CUDA torch tensors (device memory: work is
+enqueued on the current torch stream).  The library must be built first
+(``paper_2510_20891_gb300.build.build()``); nothing falls back to the CPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+from ._lib import LIB_PATH, TfsError, check, lib  # noqa: F401
+
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "f8e4m3": 3}
+WINDOWS = {"rect": 0, "hann": 1}
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+
+
+class Table:
+    """Device-resident normalised power table P[alpha][k] (owned by the library)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        n_seg, n_bin, stride = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        dt, T = ctypes.c_int(), ctypes.c_double()
+        check(lib().tfs_table_info(self._h, ctypes.byref(n_seg), ctypes.byref(n_bin), ctypes.byref(dt),
+                                   ctypes.byref(T), ctypes.byref(stride)))
+        self.n_seg, self.n_bin, self.row_stride = n_seg.value, n_bin.value, stride.value
+        self.dtype = {v: k for k, v in DTYPES.items()}[dt.value]
+        self.T_sft = T.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nbytes(self) -> int:
+        return int(lib().tfs_table_bytes(self._h))
+
+    def to_host(self):
+        """Dequantised values as FP64 [n_seg, n_bin] and the FP8 scales (or None)."""
+        P = np.empty((self.n_seg, self.n_bin), dtype=np.float64)
+        sc = np.empty(self.n_seg, dtype=np.float32) if self.dtype == "f8e4m3" else None
+        check(lib().tfs_table_to_host(self._h, _ptr(P), _ptr(sc) if sc is not None else None))
+        return P, sc
+
+    def free(self):
+        if self._h:
+            lib().tfs_table_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Basis:
+    """Device-resident track basis U [K][n_seg] (FP64) plus its training statistics."""
+
+    def __init__(self, handle):
+        self._h = handle
+        K, n = ctypes.c_int(), ctypes.c_int64()
+        check(lib().tfs_basis_info(self._h, ctypes.byref(K), ctypes.byref(n)))
+        self.K, self.n_seg = K.value, n.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def to_host(self):
+        """(U [K, n_seg], sigma [K], cmin [K], cmax [K]) as FP64 numpy arrays."""
+        U = np.empty((self.K, self.n_seg))
+        s, lo, hi = np.empty(self.K), np.empty(self.K), np.empty(self.K)
+        check(lib().tfs_basis_to_host(self._h, _ptr(U), _ptr(s), _ptr(lo), _ptr(hi)))
+        return U, s, lo, hi
+
+    def free(self):
+        if self._h:
+            lib().tfs_basis_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_sfts(strain, dt: float, T_sft: float, psd, window: str = "hann", dtype: str = "f32", stream=None) -> Table:
+    """Strain -> normalised power table (tfs_build_sfts)."""
+    h = ctypes.c_void_p()
+    if _is_torch_cuda(strain):
+        torch = _torch()
+        psd_t = psd if _is_torch_cuda(psd) else torch.as_tensor(np.asarray(psd, np.float64), device=strain.device)
+        assert strain.dtype == torch.float64 and psd_t.dtype == torch.float64
+        check(lib().tfs_build_sfts(_ptr(strain), strain.numel(), float(dt), float(T_sft), WINDOWS[window],
+                                   _ptr(psd_t), DTYPES[dtype], MEM_DEVICE, _stream_ptr(stream), ctypes.byref(h)))
+    else:
+        s, p = _f64(strain), _f64(psd)
+        check(lib().tfs_build_sfts(_ptr(s), s.size, float(dt), float(T_sft), WINDOWS[window], _ptr(p),
+                                   DTYPES[dtype], MEM_HOST, None, ctypes.byref(h)))
+    return Table(h)
+
+
+def table_from_power(P, T_sft: float, dtype: str = "f32") -> Table:
+    """Wrap an FP64 power table [n_seg, n_bin] (tfs_table_from_power)."""
+    P = _f64(P)
+    h = ctypes.c_void_p()
+    check(lib().tfs_table_from_power(_ptr(P), P.shape[0], P.shape[1], float(T_sft), DTYPES[dtype], MEM_HOST, None,
+                                     ctypes.byref(h)))
+    return Table(h)
+
+
+def build_basis(tracks, K: int = 0, tol: float = 1e-7) -> Basis:
+    """Training tracks [M, n_seg] -> SVD basis (tfs_build_basis)."""
+    F = _f64(tracks)
+    h = ctypes.c_void_p()
+    check(lib().tfs_build_basis(_ptr(F), F.shape[0], F.shape[1], int(K), float(tol), MEM_HOST, None,
+                                ctypes.byref(h)))
+    return Basis(h)
+
+
+def basis_from_host(U) -> Basis:
+    U = _f64(np.atleast_2d(U))
+    h = ctypes.c_void_p()
+    check(lib().tfs_basis_from_host(_ptr(U), U.shape[0], U.shape[1], ctypes.byref(h)))
+    return Basis(h)
+
+
+class _TieReport(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("n_stored", ctypes.c_int32), ("capacity", ctypes.c_int32),
+                ("track", ctypes.c_void_p), ("seg", ctypes.c_void_p)]
+
+
+@dataclasses.dataclass
+class EvalResult:
+    stat: object            # [N] float32 (numpy, or torch on the device)
+    top_idx: object         # [min(topk, N)] int64
+    top_val: object         # [min(topk, N)] float32
+    tie_count: int | None   # total ties (None if not requested)
+    ties: list              # up to ties_capacity (track, segment) pairs
+
+
+def eval_stat(table: Table, basis: Basis, coeffs, f_ref=None, m: int = 0, topk: int = 0, ties_capacity: int = -1,
+              stat=None, top_idx=None, top_val=None, stream=None) -> EvalResult:
+    """Statistic of a batch of tracks, its top-k and the rounding ties (tfs_eval_stat).
+
+    ties_capacity < 0 skips the tie report (no synchronisation for device inputs).
+    """
+    want_ties = ties_capacity >= 0
+    cap = max(ties_capacity, 0)
+    tt = np.zeros(max(cap, 1), dtype=np.int64)
+    ts = np.zeros(max(cap, 1), dtype=np.int32)
+    rep = _TieReport(0, 0, cap, tt.ctypes.data, ts.ctypes.data)
+    rep_p = ctypes.byref(rep) if want_ties else None
+    if _is_torch_cuda(coeffs):
+        torch = _torch()
+        N = coeffs.shape[0]
+        dev = coeffs.device
+        if stat is None:
+            stat = torch.empty(N, dtype=torch.float32, device=dev)
+        kk = min(topk, N)
+        if topk > 0 and top_idx is None:
+            top_idx = torch.empty(kk, dtype=torch.int64, device=dev)
+            top_val = torch.empty(kk, dtype=torch.float32, device=dev)
+        check(lib().tfs_eval_stat(table.handle, basis.handle, _ptr(coeffs), _ptr(f_ref) if f_ref is not None else None,
+                                  N, m, topk, _ptr(stat), _ptr(top_idx) if topk else None,
+                                  _ptr(top_val) if topk else None, rep_p, MEM_DEVICE, _stream_ptr(stream)))
+    else:
+        c = _f64(coeffs).reshape(-1, basis.K)
+        N = c.shape[0]
+        fr = _f64(f_ref) if f_ref is not None else None
+        stat = np.empty(N, dtype=np.float32)
+        kk = min(topk, N)
+        top_idx = np.empty(kk, dtype=np.int64)
+        top_val = np.empty(kk, dtype=np.float32)
+        check(lib().tfs_eval_stat(table.handle, basis.handle, _ptr(c), _ptr(fr) if fr is not None else None, N, m,
+                                  topk, _ptr(stat), _ptr(top_idx) if topk else None, _ptr(top_val) if topk else None,
+                                  rep_p, MEM_HOST, None))
+    ties = list(zip(tt[: rep.n_stored].tolist(), ts[: rep.n_stored].tolist())) if want_ties else []
+    return EvalResult(stat, top_idx, top_val, int(rep.count) if want_ties else None, ties)
+
+
+def topk(values, k: int, stream=None):
+    """Indices and values of the k largest entries (tfs_topk)."""
+    if _is_torch_cuda(values):
+        torch = _torch()
+        N = values.numel()
+        kk = min(k, N)
+        idx = torch.empty(kk, dtype=torch.int64, device=values.device)
+        val = torch.empty(kk, dtype=torch.float32, device=values.device)
+        check(lib().tfs_topk(_ptr(values), N, k, _ptr(idx), _ptr(val), MEM_DEVICE, _stream_ptr(stream)))
+        return idx, val
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    kk = min(k, v.size)
+    idx = np.empty(kk, dtype=np.int64)
+    val = np.empty(kk, dtype=np.float32)
+    check(lib().tfs_topk(_ptr(v), v.size, k, _ptr(idx), _ptr(val), MEM_HOST, None))
+    return idx, val

@@ -1,0 +1,74 @@
+"""Loading libtfstat.so and declaring its C signatures (include/tfstat.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtfstat.so")
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tfstat.h")
+
+_lib = None
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+I64 = ctypes.c_int64
+D = ctypes.c_double
+
+SIGNATURES = {
+    "tfs_version": (I, []),
+    "tfs_last_error": (ctypes.c_char_p, []),
+    "tfs_build_sfts": (I, [P, I64, D, D, I, P, I, I, P, P]),
+    "tfs_table_from_power": (I, [P, I64, I64, D, I, I, P, P]),
+    "tfs_table_info": (I, [P, P, P, P, P, P]),
+    "tfs_table_to_host": (I, [P, P, P]),
+    "tfs_table_bytes": (I64, [P]),
+    "tfs_table_free": (I, [P]),
+    "tfs_build_basis": (I, [P, I64, I64, I, D, I, P, P]),
+    "tfs_basis_from_host": (I, [P, I, I64, P]),
+    "tfs_basis_info": (I, [P, P, P]),
+    "tfs_basis_to_host": (I, [P, P, P, P, P]),
+    "tfs_basis_free": (I, [P]),
+    "tfs_eval_stat": (I, [P, P, P, P, I64, I, I, P, P, P, P, I, P]),
+    "tfs_topk": (I, [P, I64, I, P, P, I, P]),
+    "tfs_table_rebuild": (I, [P, P, I64, I, P]),
+    "tfs_eval_bins": (I, [P, P, P, P, I64, I, P, I, P]),
+    "tfs_kernel_launches": (ctypes.c_longlong, []),
+}
+
+ERR_NAMES = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY", -6: "NOT_FOUND"}
+
+
+class TfsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tfstat error {code} ({ERR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def header_symbols(path: str = HEADER) -> list[str]:
+    """Names of the functions declared in include/tfstat.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tfs_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib():
+    """The loaded library (raises if it has not been built: there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2510_20891_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != 0:
+        msg = lib().tfs_last_error()
+        raise TfsError(rc, msg.decode() if msg else "")
+    return rc

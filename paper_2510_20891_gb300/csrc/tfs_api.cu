@@ -1,0 +1,486 @@
+// C-ABI entry points of libtfstat: error model, table and basis handles,
+// the statistic call (steps 3-5 of the method, paper Sec. II.B-II.D) and
+// the stand-alone top-k.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+
+#include "tfs_internal.cuh"
+
+namespace tfs {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? TFS_ERR_OOM : TFS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- tables
+int alloc_table(int64_t n_seg, int64_t n_bin, int dtype, double T_sft, tfs_table** out) {
+  tfs_table* t = new tfs_table();
+  cudaGetDevice(&t->device);
+  t->n_seg = n_seg;
+  t->n_bin = n_bin;
+  t->row_stride = ((n_bin + 31) / 32) * 32;
+  t->dtype = dtype;
+  t->T_sft = T_sft;
+  const size_t bytes = (size_t)n_seg * t->row_stride * esize_of(dtype);
+  cudaError_t e = cudaMalloc(&t->data, bytes);
+  if (e != cudaSuccess) {
+    delete t;
+    return cuda_fail(e, "cudaMalloc(table)");
+  }
+  e = cudaMemset(t->data, 0, bytes);
+  if (e == cudaSuccess && dtype == TFS_F8E4M3) {
+    e = cudaMalloc(&t->scales, (size_t)n_seg * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(t->scales, 0, (size_t)n_seg * sizeof(float));
+  }
+  if (e != cudaSuccess) {
+    cudaFree(t->data);
+    if (t->scales) cudaFree(t->scales);
+    delete t;
+    return cuda_fail(e, "table allocation");
+  }
+  t->bytes = (int64_t)bytes + (t->scales ? n_seg * 4 : 0);
+  *out = t;
+  return TFS_OK;
+}
+
+// ---------------------------------------------------------------- basis segment parameters
+// D_k,alpha = fl32(T U_k,alpha - T U_k,mid), and max_alpha |D|, max_alpha |U| per k (rounded up).
+__global__ void segparams_kernel(const double* __restrict__ U, int K, int KP, int n_seg, int nsp, int mid,
+                                 double T, float* __restrict__ segp, float* __restrict__ dmax,
+                                 float* __restrict__ umax) {
+  const int k = blockIdx.x;  // one CTA per padded coefficient slot
+  __shared__ float sd[32], su[32];
+  float md = 0.f, mu = 0.f;
+  if (k < K) {
+    const double wmid = T * U[(size_t)k * n_seg + mid];
+    for (int a = threadIdx.x; a < n_seg; a += blockDim.x) {
+      const double u = U[(size_t)k * n_seg + a];
+      const double dd = __dsub_rn(__dmul_rn(T, u), wmid);
+      const float df = (float)dd;
+      segp[(size_t)a * nsp + k] = df;
+      md = fmaxf(md, fabsf(df));
+      mu = fmaxf(mu, __double2float_ru(fabs(u)));
+    }
+  } else {
+    for (int a = threadIdx.x; a < n_seg; a += blockDim.x) segp[(size_t)a * nsp + k] = 0.f;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sd[threadIdx.x >> 5] = md;
+    su[threadIdx.x >> 5] = mu;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      md = fmaxf(md, sd[w]);
+      mu = fmaxf(mu, su[w]);
+    }
+    md = fmaxf(md, sd[0]);
+    mu = fmaxf(mu, su[0]);
+    dmax[k] = md * (1.0f + 1.0f / 1048576.0f);
+    umax[k] = mu * (1.0f + 1.0f / 1048576.0f);
+  }
+}
+
+static int pick_kp(int K) {
+  const int opts[] = {2, 4, 6, 8, 16, 32};
+  for (int v : opts)
+    if (K <= v) return v;
+  return -1;
+}
+
+static void free_segparams(SegParams& s) {
+  if (s.segp) cudaFree(s.segp);
+  if (s.dmax) cudaFree(s.dmax);
+  if (s.umax) cudaFree(s.umax);
+  s = SegParams();
+}
+
+int get_segparams(tfs_basis* b, double T, cudaStream_t st, SegParams** out) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->sp.segp && b->sp.T == T) {
+    *out = &b->sp;
+    return TFS_OK;
+  }
+  free_segparams(b->sp);
+  const int KP = pick_kp(b->K);
+  TFS_CHECK(KP > 0, TFS_ERR_INVALID_ARG, "basis size K=%d exceeds 32", b->K);
+  SegParams s;
+  s.T = T;
+  s.KP = KP;
+  s.nsp = ((KP + 3) / 4) * 4;
+  s.alpha_mid = (int)(b->n_seg / 2);
+  TFS_CUDA(cudaMalloc(&s.segp, (size_t)b->n_seg * s.nsp * sizeof(float)));
+  TFS_CUDA(cudaMalloc(&s.dmax, 32 * sizeof(float)));
+  TFS_CUDA(cudaMalloc(&s.umax, 32 * sizeof(float)));
+  TFS_CUDA(cudaMemsetAsync(s.segp, 0, (size_t)b->n_seg * s.nsp * sizeof(float), st));
+  segparams_kernel<<<KP, 256, 0, st>>>(b->U, b->K, KP, (int)b->n_seg, s.nsp, s.alpha_mid, T, s.segp, s.dmax,
+                                       s.umax);
+  count_launch();
+  TFS_CUDA(cudaGetLastError());
+  TFS_CUDA(cudaStreamSynchronize(st));  // one-off per (basis, T): later calls may use other streams
+  b->sp = s;
+  *out = &b->sp;
+  return TFS_OK;
+}
+
+int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
+  switch (L.table->dtype) {
+    case TFS_F32: return launch_eval_f32(L, tune, st);
+    case TFS_BF16: return launch_eval_bf16(L, tune, st);
+    case TFS_F16: return launch_eval_f16(L, tune, st);
+    case TFS_F8E4M3: return launch_eval_f8(L, tune, st);
+  }
+  set_error("bad table dtype");
+  return TFS_ERR_INVALID_ARG;
+}
+
+// A small device arena for one call: one cudaMallocAsync, freed stream-ordered.
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0, size = 0;
+  cudaStream_t st = nullptr;
+  ~Arena() {
+    if (base) cudaFreeAsync(base, st);
+  }
+  int init(size_t bytes, cudaStream_t s) {
+    st = s;
+    size = bytes;
+    if (bytes == 0) return TFS_OK;
+    TFS_CUDA(cudaMallocAsync((void**)&base, bytes, s));
+    return TFS_OK;
+  }
+  template <class T>
+  T* take(size_t n) {
+    used = (used + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += n * sizeof(T);
+    return p;
+  }
+};
+
+static size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace tfs
+
+using namespace tfs;
+
+extern "C" {
+
+int tfs_version(void) { return 10000; }
+
+const char* tfs_last_error(void) { return tfs::g_err; }
+
+int tfs_table_info(const tfs_table* t, int64_t* n_seg, int64_t* n_bin, int* dtype, double* T_sft,
+                   int64_t* row_stride) {
+  TFS_CHECK(t, TFS_ERR_INVALID_ARG, "null table");
+  if (n_seg) *n_seg = t->n_seg;
+  if (n_bin) *n_bin = t->n_bin;
+  if (dtype) *dtype = t->dtype;
+  if (T_sft) *T_sft = t->T_sft;
+  if (row_stride) *row_stride = t->row_stride;
+  return TFS_OK;
+}
+
+int64_t tfs_table_bytes(const tfs_table* t) { return t ? t->bytes : 0; }
+
+long long tfs_kernel_launches(void) { return tfs::g_launches.load(); }
+
+int tfs_table_free(tfs_table* t) {
+  if (!t) return TFS_OK;
+  if (t->sft_plan) free_sft_plan(t->sft_plan);
+  if (t->data) cudaFree(t->data);
+  if (t->scales) cudaFree(t->scales);
+  delete t;
+  return TFS_OK;
+}
+
+int tfs_basis_from_host(const double* U, int K, int64_t n_seg, tfs_basis** out) {
+  clear_error();
+  TFS_CHECK(U && out, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(K >= 1 && K <= 32, TFS_ERR_INVALID_ARG, "K must be in [1, 32] (got %d)", K);
+  TFS_CHECK(n_seg >= 1 && n_seg <= (1 << 24), TFS_ERR_INVALID_ARG, "bad n_seg");
+  for (int64_t i = 0; i < (int64_t)K * n_seg; ++i)
+    TFS_CHECK(std::isfinite(U[i]), TFS_ERR_INVALID_ARG, "basis has a non-finite entry");
+  tfs_basis* b = new tfs_basis();
+  cudaGetDevice(&b->device);
+  b->K = K;
+  b->n_seg = n_seg;
+  cudaError_t e = cudaMalloc(&b->U, (size_t)K * n_seg * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(b->U, U, (size_t)K * n_seg * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (b->U) cudaFree(b->U);
+    delete b;
+    return cuda_fail(e, "basis upload");
+  }
+  b->sigma.assign(K, 0.0);
+  b->cmin.assign(K, 0.0);
+  b->cmax.assign(K, 0.0);
+  *out = b;
+  return TFS_OK;
+}
+
+int tfs_basis_info(const tfs_basis* b, int* K, int64_t* n_seg) {
+  TFS_CHECK(b, TFS_ERR_INVALID_ARG, "null basis");
+  if (K) *K = b->K;
+  if (n_seg) *n_seg = b->n_seg;
+  return TFS_OK;
+}
+
+int tfs_basis_to_host(const tfs_basis* b, double* U, double* sigma, double* cmin, double* cmax) {
+  clear_error();
+  TFS_CHECK(b, TFS_ERR_INVALID_ARG, "null basis");
+  if (U) TFS_CUDA(cudaMemcpy(U, b->U, (size_t)b->K * b->n_seg * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < b->K; ++k) {
+    if (sigma) sigma[k] = b->sigma[k];
+    if (cmin) cmin[k] = b->cmin[k];
+    if (cmax) cmax[k] = b->cmax[k];
+  }
+  return TFS_OK;
+}
+
+int tfs_basis_free(tfs_basis* b) {
+  if (!b) return TFS_OK;
+  if (b->U) cudaFree(b->U);
+  if (b->sp.segp) cudaFree(b->sp.segp);
+  if (b->sp.dmax) cudaFree(b->sp.dmax);
+  if (b->sp.umax) cudaFree(b->sp.umax);
+  delete b;
+  return TFS_OK;
+}
+
+int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double* coeffs, const double* f_ref,
+                  int64_t N, int m, int topk, float* stat, int64_t* top_idx, float* top_val, tfs_tie_report* ties,
+                  int mem, void* stream) {
+  clear_error();
+  TFS_CHECK(table && basis_c, TFS_ERR_INVALID_ARG, "null table or basis");
+  tfs_basis* basis = const_cast<tfs_basis*>(basis_c);
+  TFS_CHECK(mem == TFS_MEM_HOST || mem == TFS_MEM_DEVICE, TFS_ERR_INVALID_ARG, "bad mem kind");
+  TFS_CHECK(basis->n_seg == table->n_seg, TFS_ERR_INVALID_ARG,
+            "basis has %lld segments, table %lld", (long long)basis->n_seg, (long long)table->n_seg);
+  TFS_CHECK(N >= 0 && N < ((int64_t)1 << 40), TFS_ERR_INVALID_ARG, "bad N");
+  TFS_CHECK(m >= 0 && m <= 64, TFS_ERR_INVALID_ARG, "m must be in [0, 64]");
+  TFS_CHECK(topk >= 0 && topk <= 1024, TFS_ERR_INVALID_ARG, "topk must be in [0, 1024]");
+  TFS_CHECK(N == 0 || coeffs, TFS_ERR_INVALID_ARG, "null coeffs");
+  TFS_CHECK(stat || topk > 0 || N == 0, TFS_ERR_INVALID_ARG, "need stat or topk > 0");
+  TFS_CHECK(topk == 0 || (top_idx && top_val), TFS_ERR_INVALID_ARG, "null top-k outputs");
+  TFS_CHECK(topk == 0 || N < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "top-k needs N < 2^31");
+  TFS_CHECK(!ties || ties->capacity == 0 || (ties->track && ties->seg), TFS_ERR_INVALID_ARG,
+            "tie report arrays missing");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int K = basis->K;
+  const bool host = (mem == TFS_MEM_HOST);
+  const int tie_cap = ties ? ties->capacity : 0;
+  const int kk = (int)std::min<int64_t>(topk, N);
+
+  SegParams* sp = nullptr;
+  int rc = get_segparams(basis, table->T_sft, st, &sp);
+  if (rc) return rc;
+
+  // one arena for everything this call needs on the device
+  size_t need = 0;
+  need += round256(sizeof(unsigned long long)) + round256(sizeof(int));
+  need += round256((size_t)std::max(tie_cap, 1) * 8) + round256((size_t)std::max(tie_cap, 1) * 4);
+  if (host) need += round256((size_t)N * K * 8) + round256((size_t)N * 8);
+  if (host || !stat) need += round256((size_t)N * 4);
+  if (kk > 0) need += round256((size_t)kk * 12) + round256(topk_workspace_bytes(N));
+  Arena ar;
+  rc = ar.init(need, st);
+  if (rc) return rc;
+  unsigned long long* d_tc = ar.take<unsigned long long>(1);
+  int* d_status = ar.take<int>(1);
+  int64_t* d_tt = ar.take<int64_t>(std::max(tie_cap, 1));
+  int* d_ts = ar.take<int>(std::max(tie_cap, 1));
+  const double* d_c = coeffs;
+  const double* d_f = f_ref;
+  float* d_stat = stat;
+  if (host) {
+    double* c = ar.take<double>((size_t)N * K);
+    TFS_CUDA(cudaMemcpyAsync(c, coeffs, (size_t)N * K * 8, cudaMemcpyHostToDevice, st));
+    d_c = c;
+    if (f_ref) {
+      double* f = ar.take<double>((size_t)N);
+      TFS_CUDA(cudaMemcpyAsync(f, f_ref, (size_t)N * 8, cudaMemcpyHostToDevice, st));
+      d_f = f;
+    }
+  }
+  if (host || !stat) d_stat = ar.take<float>((size_t)N);
+  TFS_CUDA(cudaMemsetAsync(d_tc, 0, sizeof(unsigned long long), st));
+  TFS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+
+  EvalLaunch L;
+  L.table = table;
+  L.basis = basis;
+  L.sp = sp;
+  L.coeffs = d_c;
+  L.f_ref = d_f;
+  L.N = N;
+  L.m = m;
+  L.stat = d_stat;
+  L.tie_count = d_tc;
+  L.tie_track = d_tt;
+  L.tie_seg = d_ts;
+  L.tie_cap = tie_cap;
+  L.status = d_status;
+  rc = launch_eval(L, EvalTuning(), st);
+  if (rc) return rc;
+
+  int64_t* d_ti = nullptr;
+  float* d_tv = nullptr;
+  if (kk > 0) {
+    d_ti = ar.take<int64_t>(kk);
+    d_tv = ar.take<float>(kk);
+    void* ws = ar.take<char>(topk_workspace_bytes(N));
+    rc = topk_device(d_stat, N, kk, host ? d_ti : top_idx, host ? d_tv : top_val, ws, st);
+    if (rc) return rc;
+  }
+  if (host) {
+    if (stat && N > 0) TFS_CUDA(cudaMemcpyAsync(stat, d_stat, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    if (kk > 0) {
+      TFS_CUDA(cudaMemcpyAsync(top_idx, d_ti, (size_t)kk * 8, cudaMemcpyDeviceToHost, st));
+      TFS_CUDA(cudaMemcpyAsync(top_val, d_tv, (size_t)kk * 4, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  const bool wait = host || ties || st == nullptr;
+  int h_status = 0;
+  if (wait) {
+    TFS_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    unsigned long long tc = 0;
+    if (ties) TFS_CUDA(cudaMemcpyAsync(&tc, d_tc, sizeof(tc), cudaMemcpyDeviceToHost, st));
+    TFS_CUDA(cudaStreamSynchronize(st));
+    if (ties) {
+      ties->count = (int64_t)tc;
+      ties->n_stored = (int32_t)std::min<unsigned long long>(tc, (unsigned long long)tie_cap);
+      if (ties->n_stored > 0) {
+        TFS_CUDA(cudaMemcpy(ties->track, d_tt, (size_t)ties->n_stored * 8, cudaMemcpyDeviceToHost));
+        TFS_CUDA(cudaMemcpy(ties->seg, d_ts, (size_t)ties->n_stored * 4, cudaMemcpyDeviceToHost));
+      }
+    }
+    TFS_CHECK(h_status == 0, TFS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", h_status);
+  }
+  return TFS_OK;
+}
+
+int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis_c, const double* coeffs, const double* f_ref,
+                  int64_t N, int m, int32_t* bins, int mem, void* stream) {
+  clear_error();
+  TFS_CHECK(table && basis_c && bins && (coeffs || N == 0), TFS_ERR_INVALID_ARG, "null argument");
+  tfs_basis* basis = const_cast<tfs_basis*>(basis_c);
+  TFS_CHECK(mem == TFS_MEM_HOST || mem == TFS_MEM_DEVICE, TFS_ERR_INVALID_ARG, "bad mem kind");
+  TFS_CHECK(basis->n_seg == table->n_seg, TFS_ERR_INVALID_ARG, "basis and table segment counts differ");
+  TFS_CHECK(N >= 0 && N * table->n_seg < ((int64_t)1 << 34), TFS_ERR_INVALID_ARG, "bad N");
+  TFS_CHECK(m >= 0 && m <= 64, TFS_ERR_INVALID_ARG, "m must be in [0, 64]");
+  if (N == 0) return TFS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SegParams* sp = nullptr;
+  int rc = get_segparams(basis, table->T_sft, st, &sp);
+  if (rc) return rc;
+  const bool host = mem == TFS_MEM_HOST;
+  const int K = basis->K;
+  const size_t nb = (size_t)N * table->n_seg;
+  Arena ar;
+  size_t need = round256(8) + round256(4) + round256(8) + round256(4) + round256((size_t)N * 4);
+  if (host) need += round256((size_t)N * K * 8) + round256((size_t)N * 8) + round256(nb * 4);
+  rc = ar.init(need, st);
+  if (rc) return rc;
+  unsigned long long* d_tc = ar.take<unsigned long long>(1);
+  int* d_status = ar.take<int>(1);
+  int64_t* d_tt = ar.take<int64_t>(1);
+  int* d_ts = ar.take<int>(1);
+  float* d_stat = ar.take<float>(N);
+  const double* d_c = coeffs;
+  const double* d_f = f_ref;
+  int* d_b = bins;
+  if (host) {
+    double* c = ar.take<double>((size_t)N * K);
+    TFS_CUDA(cudaMemcpyAsync(c, coeffs, (size_t)N * K * 8, cudaMemcpyHostToDevice, st));
+    d_c = c;
+    if (f_ref) {
+      double* f = ar.take<double>(N);
+      TFS_CUDA(cudaMemcpyAsync(f, f_ref, (size_t)N * 8, cudaMemcpyHostToDevice, st));
+      d_f = f;
+    }
+    d_b = ar.take<int>(nb);
+  }
+  TFS_CUDA(cudaMemsetAsync(d_tc, 0, 8, st));
+  TFS_CUDA(cudaMemsetAsync(d_status, 0, 4, st));
+  EvalLaunch L;
+  L.table = table;
+  L.basis = basis;
+  L.sp = sp;
+  L.coeffs = d_c;
+  L.f_ref = d_f;
+  L.N = N;
+  L.m = m;
+  L.stat = d_stat;
+  L.tie_count = d_tc;
+  L.tie_track = d_tt;
+  L.tie_seg = d_ts;
+  L.tie_cap = 0;
+  L.status = d_status;
+  L.bins_out = d_b;
+  rc = launch_eval(L, EvalTuning(), st);
+  if (rc) return rc;
+  if (host) TFS_CUDA(cudaMemcpyAsync(bins, d_b, nb * 4, cudaMemcpyDeviceToHost, st));
+  int h_status = 0;
+  TFS_CUDA(cudaMemcpyAsync(&h_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+  TFS_CUDA(cudaStreamSynchronize(st));
+  TFS_CHECK(h_status == 0, TFS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", h_status);
+  return TFS_OK;
+}
+
+int tfs_topk(const float* val_in, int64_t N, int k, int64_t* idx, float* val, int mem, void* stream) {
+  clear_error();
+  TFS_CHECK(val_in && idx && val, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(N >= 1 && N < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "N must be in [1, 2^31)");
+  TFS_CHECK(k >= 1 && k <= 1024, TFS_ERR_INVALID_ARG, "k must be in [1, 1024]");
+  TFS_CHECK(mem == TFS_MEM_HOST || mem == TFS_MEM_DEVICE, TFS_ERR_INVALID_ARG, "bad mem kind");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int kk = (int)std::min<int64_t>(k, N);
+  const bool host = mem == TFS_MEM_HOST;
+  Arena ar;
+  size_t need = round256(topk_workspace_bytes(N));
+  if (host) need += round256((size_t)N * 4) + round256((size_t)kk * 8) + round256((size_t)kk * 4);
+  int rc = ar.init(need, st);
+  if (rc) return rc;
+  void* ws = ar.take<char>(topk_workspace_bytes(N));
+  const float* d_in = val_in;
+  int64_t* d_i = idx;
+  float* d_v = val;
+  if (host) {
+    float* p = ar.take<float>(N);
+    TFS_CUDA(cudaMemcpyAsync(p, val_in, (size_t)N * 4, cudaMemcpyHostToDevice, st));
+    d_in = p;
+    d_i = ar.take<int64_t>(kk);
+    d_v = ar.take<float>(kk);
+  }
+  rc = topk_device(d_in, N, kk, d_i, d_v, ws, st);
+  if (rc) return rc;
+  if (host) {
+    TFS_CUDA(cudaMemcpyAsync(idx, d_i, (size_t)kk * 8, cudaMemcpyDeviceToHost, st));
+    TFS_CUDA(cudaMemcpyAsync(val, d_v, (size_t)kk * 4, cudaMemcpyDeviceToHost, st));
+  }
+  if (host || st == nullptr) TFS_CUDA(cudaStreamSynchronize(st));
+  return TFS_OK;
+}
+
+}  // extern "C"

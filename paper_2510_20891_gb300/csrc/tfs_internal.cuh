@@ -1,0 +1,184 @@
+// Internal declarations shared by the CUDA translation units of libtfstat.
+// Nothing here is part of the C ABI (include/tfstat.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tfstat.h"
+
+namespace tfs {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char* what);  // records the message, returns TFS_ERR_CUDA
+
+#define TFS_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ::tfs::cuda_fail(e_, #call); \
+  } while (0)
+
+#define TFS_CHECK(cond, code, ...)     \
+  do {                                 \
+    if (!(cond)) {                     \
+      ::tfs::set_error(__VA_ARGS__);   \
+      return (code);                   \
+    }                                  \
+  } while (0)
+
+// Device status word values written by kernels (0 = ok).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD = 2 };
+
+// Process-wide count of kernel launches made by this library.
+void count_launch(int n = 1);
+void free_sft_plan(void* p);
+
+// ---------------------------------------------------------------- handles
+struct SegParams {          // per (basis, T_sft) data for the FP32 filter of the track evaluation
+  double T = 0.0;
+  int KP = 0;               // coefficient slots in the kernel (>= K, zero padded)
+  int nsp = 0;              // floats per segment row of `segp` (multiple of 4, >= KP)
+  int alpha_mid = 0;
+  float* segp = nullptr;    // device [n_seg][nsp]: D_k,alpha = fl32(T U_k,alpha - T U_k,mid)
+  float* dmax = nullptr;    // device [KP]: max_alpha |D_k,alpha| (rounded up)
+  float* umax = nullptr;    // device [KP]: max_alpha |U_k,alpha| (rounded up)
+};
+
+}  // namespace tfs
+
+struct tfs_table {
+  int device = 0;
+  int64_t n_seg = 0, n_bin = 0, row_stride = 0;
+  int dtype = TFS_F32;
+  double T_sft = 0.0;
+  void* data = nullptr;     // device [n_seg][row_stride], zero padded beyond n_bin
+  float* scales = nullptr;  // device [n_seg] (FP8 only)
+  int64_t bytes = 0;
+  double dt = 0.0;
+  void* sft_plan = nullptr; // cached SFT plan (window, twiddles, PSD normalisation) when built from strain
+};
+
+struct tfs_basis {
+  int device = 0;
+  int K = 0;
+  int64_t n_seg = 0;
+  double* U = nullptr;      // device [K][n_seg]
+  std::vector<double> sigma, cmin, cmax;
+  std::mutex mu;            // guards the cached segment parameters
+  tfs::SegParams sp;
+};
+
+namespace tfs {
+
+inline int esize_of(int dtype) { return dtype == TFS_F32 ? 4 : (dtype == TFS_F8E4M3 ? 1 : 2); }
+
+// Cached FP32 filter parameters of a basis for a given T_sft (built on first use).
+int get_segparams(tfs_basis* b, double T, cudaStream_t st, SegParams** out);
+
+// ---------------------------------------------------------------- kernels (host launchers)
+struct EvalLaunch {
+  const tfs_table* table;
+  const tfs_basis* basis;
+  const SegParams* sp;
+  const double* coeffs;   // device
+  const double* f_ref;    // device or null
+  int64_t N;
+  int m;
+  float* stat;            // device
+  unsigned long long* tie_count;  // device
+  int64_t* tie_track;     // device [tie_cap]
+  int* tie_seg;
+  int tie_cap;
+  int* status;            // device
+  int* bins_out = nullptr;  // device [N][n_seg] or null: the bin of every pair (verification only)
+};
+struct EvalTuning {       // launch shape; zeros select defaults
+  int threads = 0;
+  int stages = 0;
+  int cap = 0;            // staged band capacity per row (elements)
+  int qcap = 0;
+};
+int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st);
+
+// dtype-specific launchers (one translation unit each)
+int launch_eval_f32(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
+int launch_eval_bf16(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
+int launch_eval_f16(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
+int launch_eval_f8(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
+
+// top-k over device floats; scratch from `ws` (size from topk_workspace_bytes) or allocated.
+size_t topk_workspace_bytes(int64_t N);
+int topk_device(const float* val, int64_t N, int k, int64_t* idx_out, float* val_out, void* ws, cudaStream_t st);
+
+// quantise an FP64 device table P [n_seg][n_bin] (row pitch `ld`) into a table's storage
+int quantise_into(const double* P, int64_t ld, tfs_table* t, cudaStream_t st);
+
+// allocate a zeroed table of the given shape/dtype (data + scales)
+int alloc_table(int64_t n_seg, int64_t n_bin, int dtype, double T_sft, tfs_table** out);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared, completing `bytes` of transaction count on `bar`.
+// dst, src 16-byte aligned; bytes a positive multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier to complete; gives up after ~limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t a = smem_u32(bar);
+  uint32_t done = 0;
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 0) {
+      const uint64_t now = global_ns();
+      if (it == 0) t0 = now;
+      else if (now - t0 > limit_ns) return false;
+    }
+  }
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+}  // namespace tfs

@@ -1,0 +1,72 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports every
+symbol include/tfstat.h declares, and rejects bad arguments on the host
+before touching the device."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2510_20891_gb300 import _lib
+from paper_2510_20891_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return _lib.lib()
+
+
+def test_header_declares_the_boundary_calls():
+    syms = _lib.header_symbols()
+    for name in ("tfs_build_sfts", "tfs_build_basis", "tfs_eval_stat", "tfs_topk"):
+        assert name in syms
+
+
+def test_library_exports_every_header_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [s for s in _lib.header_symbols() if s not in exported]
+    assert not missing, missing
+    for s in _lib.header_symbols():
+        assert hasattr(L, s)
+
+
+def test_binding_declares_exactly_the_header(L):
+    assert set(_lib.SIGNATURES) == set(_lib.header_symbols())
+
+
+def test_library_targets_sm103a(L):
+    out = subprocess.run(["cuobjdump", "--list-elf", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_version_and_error_string(L):
+    assert L.tfs_version() == 10000
+    assert L.tfs_last_error() is not None
+
+
+def test_host_validation_without_device(L):
+    P = ctypes.c_void_p
+    # null handles and shapes are rejected before any CUDA call
+    assert L.tfs_eval_stat(None, None, None, None, 0, 0, 0, None, None, None, None, 0, None) == -1
+    assert b"null" in L.tfs_last_error()
+    buf = (ctypes.c_float * 4)()
+    idx = (ctypes.c_int64 * 4)()
+    val = (ctypes.c_float * 4)()
+    assert L.tfs_topk(ctypes.cast(buf, P), 0, 4, ctypes.cast(idx, P), ctypes.cast(val, P), 0, None) == -1
+    assert L.tfs_topk(ctypes.cast(buf, P), 4, 2000, ctypes.cast(idx, P), ctypes.cast(val, P), 0, None) == -1
+    x = (ctypes.c_double * 64)()
+    out = P()
+    # T_sft / dt = 7 is not even and 2,3,5-smooth
+    assert L.tfs_build_sfts(ctypes.cast(x, P), 64, 1.0, 7.0, 1, ctypes.cast(x, P), 0, 0, None, ctypes.byref(out)) == -1
+    assert L.tfs_build_sfts(ctypes.cast(x, P), 64, 1.0, 14.0, 1, ctypes.cast(x, P), 0, 0, None, ctypes.byref(out)) == -1
+    assert b"prime factors" in L.tfs_last_error()
+    assert L.tfs_build_basis(ctypes.cast(x, P), 8, 8, 40, 0.0, 0, None, ctypes.byref(out)) == -1
+    assert L.tfs_basis_from_host(ctypes.cast(x, P), 0, 8, ctypes.byref(out)) == -1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.lib()

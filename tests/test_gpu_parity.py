@@ -1,0 +1,349 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Tolerances (stated per check):
+* bins: bit-exact for every (track, segment), ties included;
+* statistic: max relative error over tracks <= 1e-5 against the oracle on the
+  same stored table (FP32 accumulation of at most ~5000 non-negative terms in
+  two levels of <= 32 + 50 additions: <= 90 * 2^-24 = 5.4e-6); against the
+  exact FP64 table, additionally the storage rounding: <= 1e-5 (f32),
+  4e-3 (bf16, 2^-9), 2e-3 (f16, 2^-11), 6.5e-2 (f8e4m3, 2^-4 plus subnormals);
+* tables: f32 elements within 2^-24 relative plus the FP64 FFT error
+  (1e-12 of the row's largest value); other dtypes equal to the oracle's
+  rounding except at rounding boundaries (one unit in the last place, in at
+  most 1e-4 of the elements);
+* top-k: the exact top-k of the statistic values (ties by lower index).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.tfstat_oracle as O
+from paper_2510_20891_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+STAT_TOL_P64 = {"f32": 1e-5, "bf16": 4e-3, "f16": 2e-3, "f8e4m3": 6.5e-2}
+STAT_TOL_SAME_TABLE = 1e-5
+INT_MIN, INT_MAX = -(2 ** 31), 2 ** 31 - 1
+
+
+@pytest.fixture(scope="session")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_20891_gb300 import build as B
+
+    B.build()
+    import paper_2510_20891_gb300 as pkg
+
+    return pkg
+
+
+def oracle_bins_mapped(x, m, n_bin):
+    """Oracle bins with the ABI's sentinels for windows wholly outside the table."""
+    b, tie = O.bins_and_ties(x)
+    out = b.copy()
+    out[b + m < 0] = INT_MIN
+    out[b - m >= n_bin] = INT_MAX
+    out[~np.isfinite(x)] = INT_MAX
+    return out.astype(np.int64), tie
+
+
+def dataset(name, seed=0):
+    w = synth.WORKLOADS[name]
+    rng = np.random.default_rng(seed)
+    x, inj = synth.make_strain(w, rng)
+    psd = synth.psd_bins(w.psd_fn(), w.n_bin, w.T_sft)
+    F = synth.make_training_tracks(w, rng)
+    P64 = O.power_table(x, w.dt, w.T_sft, psd)
+    V, s, cmin, cmax = O.svd_basis(F, w.K)
+    return dict(w=w, x=x, psd=psd, F=F, P64=P64, V=V, s=s, cmin=cmin, cmax=cmax, inj=inj)
+
+
+@pytest.fixture(scope="session")
+def tiny():
+    return dataset("tiny_white_2p18")
+
+
+@pytest.fixture(scope="session")
+def oneyear():
+    return dataset("oneyear_daily_fp32")
+
+
+# --------------------------------------------------------------------------- tables
+def _check_table(T, table, P64, dtype):
+    got, sc = table.to_host()
+    assert got.shape == P64.shape
+    if dtype == "f32":
+        ref = P64
+        tol = 2.0 ** -24 * np.abs(ref) + 1e-12 * np.max(np.abs(ref), axis=1, keepdims=True)
+        bad = np.abs(got - ref) > tol
+        assert not bad.any(), (np.argwhere(bad)[:5], got[bad][:5], ref[bad][:5])
+        return
+    ref, ref_sc = O.quantise_table(P64, dtype)
+    if dtype == "f8e4m3":
+        assert np.allclose(sc, ref_sc, rtol=2.0 ** -23)
+    diff = got != ref
+    frac = diff.mean()
+    assert frac <= 1e-4, frac
+    if diff.any():
+        # a rounding-boundary disagreement is one unit in the last place of the format
+        rel = np.abs(got[diff] - ref[diff]) / np.maximum(np.abs(ref[diff]), 1e-300)
+        ulp = {"bf16": 2.0 ** -7, "f16": 2.0 ** -10, "f8e4m3": 2.0 ** -3}[dtype]
+        assert np.all(rel <= ulp * 1.01), rel.max()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16", "f8e4m3"])
+def test_build_sfts_tiny(T, tiny, dtype):
+    w = tiny["w"]
+    table = T.build_sfts(tiny["x"], w.dt, w.T_sft, tiny["psd"], "hann", dtype)
+    assert (table.n_seg, table.n_bin) == (64, 2049)
+    _check_table(T, table, tiny["P64"], dtype)
+
+
+def test_build_sfts_oneyear_red_noise(T, oneyear):
+    w = oneyear["w"]
+    table = T.build_sfts(oneyear["x"], w.dt, w.T_sft, oneyear["psd"], "hann", "f32")
+    assert (table.n_seg, table.n_bin) == (365, 8641)
+    _check_table(T, table, oneyear["P64"], "f32")
+
+
+@pytest.mark.parametrize("L", [4, 6, 12, 30, 250, 2000, 4000, 4096, 10000, 17280, 20000, 40000])
+@pytest.mark.parametrize("window", ["hann", "rect"])
+def test_build_sfts_lengths(T, L, window):
+    rng = np.random.default_rng(L)
+    n_seg = 3
+    x = rng.standard_normal(n_seg * L + 7)          # a ragged tail that must be dropped
+    psd = np.full(L // 2 + 1, 2.0)
+    psd[1] = np.inf
+    P64 = O.power_table(x, 1.0, float(L), psd, window)
+    table = T.build_sfts(x, 1.0, float(L), psd, window, "f32")
+    _check_table(T, table, P64, "f32")
+
+
+def test_build_sfts_closed_form(T):
+    L, A, k0 = 4096, 0.05, 40
+    n = np.arange(4 * L)
+    x = A * np.cos(2 * np.pi * k0 * n / L + 0.3)
+    table = T.build_sfts(x, 1.0, float(L), np.full(L // 2 + 1, 2.0), "hann", "f32")
+    P, _ = table.to_host()
+    assert np.allclose(P[:, k0], 3.4133333333333333, rtol=1e-6)
+    assert np.allclose(P[:, k0 + 1], 0.8533333333333333, rtol=1e-6)
+
+
+def test_table_rebuild_equals_build(T, tiny):
+    w = tiny["w"]
+    table = T.build_sfts(tiny["x"], w.dt, w.T_sft, tiny["psd"], "hann", "bf16")
+    x2 = np.random.default_rng(9).standard_normal(w.n_samples)
+    T.check(T.lib().tfs_table_rebuild(table.handle, x2.ctypes.data, x2.size, 0, None))
+    fresh = T.build_sfts(x2, w.dt, w.T_sft, tiny["psd"], "hann", "bf16")
+    assert np.array_equal(table.to_host()[0], fresh.to_host()[0])
+
+
+# --------------------------------------------------------------------------- basis
+def _basis_tol(s, k):
+    gap = min([abs(s[k] - s[j]) for j in range(len(s)) if j != k] + [s[k]])
+    return 1e-12 * s[0] / gap + 1e-12
+
+
+@pytest.mark.parametrize("name", ["tiny_white_2p18", "oneyear_daily_fp32"])
+def test_build_basis_parity(T, name):
+    w = synth.WORKLOADS[name]
+    F = synth.make_training_tracks(w, np.random.default_rng(3))
+    V, s, cmin, cmax = O.svd_basis(F, w.K)
+    b = T.build_basis(F, w.K)
+    U, sg, lo, hi = b.to_host()
+    assert U.shape == V.shape
+    assert np.allclose(sg, s, rtol=1e-9)
+    for k in range(w.K):
+        assert np.max(np.abs(U[k] - V[k])) <= _basis_tol(s, k), k
+    assert np.allclose(U @ U.T, np.eye(w.K), atol=1e-12)
+    scale = np.max(np.abs(F)) * math.sqrt(w.n_seg)
+    assert np.max(np.abs(lo - cmin)) <= 1e-9 * scale and np.max(np.abs(hi - cmax)) <= 1e-9 * scale
+
+
+def test_build_basis_auto_k(T):
+    w = synth.WORKLOADS["tiny_white_2p18"]
+    F = synth.make_training_tracks(w, np.random.default_rng(4))
+    b = T.build_basis(F, 0, 1e-10)
+    assert b.K == 3 == O.svd_basis(F, 0, 1e-10)[0].shape[0]
+    w2 = synth.WORKLOADS["oneyear_daily_fp32"]
+    F2 = synth.make_training_tracks(w2, np.random.default_rng(4), 800)
+    for tol in (1e-3, 1e-5):
+        assert T.build_basis(F2, 0, tol).K == O.svd_basis(F2, 0, tol)[0].shape[0]
+
+
+# --------------------------------------------------------------------------- statistic
+def _eval_and_check(T, P64, V, coeffs, f_ref, Tsft, m, dtype, topk=0, check_bins=True):
+    table = T.table_from_power(P64, Tsft, dtype)
+    basis = T.basis_from_host(V)
+    res = T.eval_stat(table, basis, coeffs, f_ref, m=m, topk=topk, ties_capacity=4096)
+    fr = np.zeros(len(coeffs)) if f_ref is None else f_ref
+    Pq, _ = O.quantise_table(P64, dtype)
+    Sq, idx, val, ties = O.eval_stat(Pq, V, coeffs, fr, Tsft, m, topk)
+    S64, *_ = O.eval_stat(P64, V, coeffs, fr, Tsft, m, 0)
+    e_same = O.stat_relative_error(res.stat, Sq)
+    e_64 = O.stat_relative_error(res.stat, S64)
+    assert e_same <= STAT_TOL_SAME_TABLE, e_same
+    assert e_64 <= STAT_TOL_P64[dtype], e_64
+    assert res.tie_count == len(ties)
+    assert sorted(res.ties) == sorted(ties)[: len(res.ties)] or set(res.ties) <= set(ties)
+    if topk:
+        gi, gv = O.topk(res.stat, topk)
+        assert np.array_equal(res.top_idx, gi)
+        assert np.array_equal(res.top_val, res.stat[gi])
+    if check_bins:
+        bins = np.empty((len(coeffs), P64.shape[0]), dtype=np.int32)
+        T.check(T.lib().tfs_eval_bins(table.handle, basis.handle, np.ascontiguousarray(coeffs).ctypes.data,
+                                      None if f_ref is None else f_ref.ctypes.data, len(coeffs), m,
+                                      bins.ctypes.data, 0, None))
+        ob, _ = oracle_bins_mapped(O.track_x(V, coeffs, fr, Tsft), m, P64.shape[1])
+        mism = np.argwhere(bins.astype(np.int64) != ob)
+        assert mism.size == 0, (mism[:5], bins[tuple(mism[0])], ob[tuple(mism[0])])
+    return res, e_same, e_64
+
+
+@pytest.mark.parametrize("m", [0, 1])
+def test_eval_stat_tiny(T, tiny, m):
+    w = tiny["w"]
+    coeffs = synth.uniform_coeffs(w.n_tracks, tiny["cmin"], tiny["cmax"], np.random.default_rng(5))
+    _eval_and_check(T, tiny["P64"], tiny["V"], coeffs, None, w.T_sft, m, "f32", topk=128)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16", "f8e4m3"])
+def test_eval_stat_oneyear_dtypes(T, oneyear, dtype):
+    w = oneyear["w"]
+    N = 3 * 2048 + 777                       # several tiles and a ragged tail
+    coeffs = synth.uniform_coeffs(N, oneyear["cmin"], oneyear["cmax"], np.random.default_rng(6))
+    res, e_same, e_64 = _eval_and_check(T, oneyear["P64"], oneyear["V"], coeffs, None, w.T_sft, 1, dtype,
+                                        topk=64, check_bins=(dtype == "f32"))
+    print(f"{dtype}: max rel err vs same table {e_same:.2e}, vs FP64 table {e_64:.2e}")
+
+
+def test_eval_stat_full_size_sampled(T, oneyear):
+    """Ten million tracks in the benchmark's launch configuration (device memory,
+    top-128); a sample of 20000 tracks is recomputed by the oracle."""
+    torch = pytest.importorskip("torch")
+    w = oneyear["w"]
+    N = w.n_tracks
+    rng = np.random.default_rng(7)
+    coeffs = synth.uniform_coeffs(N, oneyear["cmin"], oneyear["cmax"], rng)
+    table = T.table_from_power(oneyear["P64"], w.T_sft, "f32")
+    basis = T.basis_from_host(oneyear["V"])
+    dc = torch.from_numpy(coeffs).cuda()
+    res = T.eval_stat(table, basis, dc, None, m=1, topk=128)
+    torch.cuda.synchronize()
+    stat = res.stat.cpu().numpy()
+    sample = rng.choice(N, 20000, replace=False)
+    Pq, _ = O.quantise_table(oneyear["P64"], "f32")
+    S, *_ = O.eval_stat(Pq, oneyear["V"], coeffs[sample], np.zeros(sample.size), w.T_sft, 1)
+    assert O.stat_relative_error(stat[sample], S) <= STAT_TOL_SAME_TABLE
+    gi, _ = O.topk(stat, 128)
+    assert np.array_equal(res.top_idx.cpu().numpy(), gi)
+    St, *_ = O.eval_stat(Pq, oneyear["V"], coeffs[gi], np.zeros(gi.size), w.T_sft, 1)
+    assert O.stat_relative_error(res.top_val.cpu().numpy(), St) <= STAT_TOL_SAME_TABLE
+
+
+def test_injected_track_is_the_top_candidate(T, tiny):
+    w = tiny["w"]
+    t = O.segment_times(w.n_seg, w.T_sft)
+    f_true = tiny["inj"]["f0"] + tiny["inj"]["fdot"] * t
+    c_true = f_true @ tiny["V"].T
+    coeffs = synth.uniform_coeffs(5000, tiny["cmin"], tiny["cmax"], np.random.default_rng(8))
+    coeffs[1234] = c_true
+    table = T.build_sfts(tiny["x"], w.dt, w.T_sft, tiny["psd"], "hann", "f32")
+    res = T.eval_stat(table, T.basis_from_host(tiny["V"]), coeffs, None, m=1, topk=4)
+    assert res.top_idx[0] == 1234
+
+
+# --------------------------------------------------------------------------- edge cases
+def _rand_problem(n_seg, n_bin, K, N, seed, T_sft=4096.0):
+    rng = np.random.default_rng(seed)
+    P = rng.exponential(2.0, (n_seg, n_bin))
+    V = rng.standard_normal((K, n_seg)) / math.sqrt(n_seg)
+    coeffs = rng.standard_normal((N, K)) * (n_bin / T_sft) * 0.3
+    f_ref = rng.uniform(0, n_bin / T_sft, N)
+    return P, V, coeffs, f_ref
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 7, 8, 12, 20, 32])
+def test_eval_stat_basis_sizes(T, K):
+    P, V, c, f = _rand_problem(40, 300, K, 3000, K)
+    _eval_and_check(T, P, V, c, f, 4096.0, 1, "f32", topk=10)
+
+
+@pytest.mark.parametrize("m", [0, 2, 7, 64])
+def test_eval_stat_neighbour_widths(T, m):
+    P, V, c, f = _rand_problem(33, 257, 4, 2500, 100 + m)
+    _eval_and_check(T, P, V, c, f, 4096.0, m, "f32", topk=5)
+
+
+@pytest.mark.parametrize("n_seg", [1, 2, 31, 32, 33, 65])
+def test_eval_stat_segment_counts(T, n_seg):
+    P, V, c, f = _rand_problem(n_seg, 129, 3, 2100, 200 + n_seg)
+    _eval_and_check(T, P, V, c, f, 4096.0, 1, "bf16", topk=3)
+
+
+@pytest.mark.parametrize("N", [0, 1, 2047, 2048, 2049])
+def test_eval_stat_track_counts(T, N):
+    P, V, c, f = _rand_problem(8, 100, 3, max(N, 1), 300 + N)
+    c, f = c[:N], f[:N]
+    if N == 0:
+        table = T.table_from_power(P, 4096.0, "f32")
+        res = T.eval_stat(table, T.basis_from_host(V), np.zeros((0, 3)), None, m=1)
+        assert res.stat.size == 0
+        return
+    _eval_and_check(T, P, V, c, f, 4096.0, 1, "f32", topk=min(N, 7))
+
+
+def test_eval_stat_exact_ties_everywhere(T):
+    """Every pair lands exactly on a half-integer: all pairs take the FP64 path,
+    the per-segment queues overflow and the tie report lists every pair."""
+    n_seg, n_bin, Tsft = 6, 64, 4096.0
+    P = np.random.default_rng(1).exponential(2.0, (n_seg, n_bin))
+    V = np.zeros((1, n_seg))
+    N = 3000
+    k = np.random.default_rng(2).integers(0, n_bin - 1, N)
+    f_ref = (k + 0.5) / Tsft
+    coeffs = np.zeros((N, 1))
+    res, _, _ = _eval_and_check(T, P, V, coeffs, f_ref, Tsft, 0, "f32")
+    assert res.tie_count == N * n_seg
+
+
+def test_eval_stat_out_of_range_and_nonfinite(T):
+    P, V, c, f = _rand_problem(10, 50, 2, 400, 9)
+    f[:50] = -1.0                    # far below bin 0
+    f[50:100] = 1e3                  # far above the table
+    c[100:110, 0] = np.nan           # not finite: contributes 0
+    c[110:120, 1] = 1e9              # huge coefficients: the FP64 path for every segment
+    f[120:130] = -0.2 / 4096.0       # straddling bin 0
+    f[130:140] = (49.6) / 4096.0     # straddling the last bin
+    res, _, _ = _eval_and_check(T, P, V, c, f, 4096.0, 1, "f32")
+    assert np.all(res.stat[:100] == 0) and np.all(res.stat[100:110] == 0)
+
+
+# --------------------------------------------------------------------------- top-k
+@pytest.mark.parametrize("N", [1, 5, 4096, 4097, 1_000_003])
+@pytest.mark.parametrize("k", [1, 7, 128, 1024])
+def test_topk_parity(T, N, k):
+    rng = np.random.default_rng(N + k)
+    v = rng.integers(0, 50, N).astype(np.float32) * 0.5
+    if N > 10:
+        v[rng.choice(N, 5, replace=False)] = np.nan
+        v[rng.choice(N, 5, replace=False)] = -0.0
+        v[rng.choice(N, 3, replace=False)] = -np.inf
+    idx, val = T.topk(v, k)
+    ri, rv = O.topk(v.astype(np.float64), k)
+    assert np.array_equal(idx, ri)
+    assert np.array_equal(val.astype(np.float64), rv, equal_nan=True)
+
+
+def test_topk_device_distinct_values(T):
+    torch = pytest.importorskip("torch")
+    v = torch.randn(3_000_001, device="cuda")
+    idx, val = T.topk(v, 1000)
+    vh = v.cpu().numpy()
+    ri, _ = O.topk(vh.astype(np.float64), 1000)
+    assert np.array_equal(idx.cpu().numpy(), ri)
