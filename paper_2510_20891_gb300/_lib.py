@@ -5,7 +5,7 @@ import ctypes
 import os
 import re
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtfstat.so")
+LIB_PATH = os.environ.get("TFS_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtfstat.so")
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tfstat.h")
 
 _lib = None

@@ -16,8 +16,9 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-OUT_DIR = os.path.join(PKG, "_build")
-LIB = os.path.join(PKG, "libtfstat.so")
+_DEBUG = os.environ.get("TFS_DEBUG_CHECKS") == "1"
+OUT_DIR = os.path.join(PKG, "_build_debug" if _DEBUG else "_build")
+LIB = os.path.join(PKG, "libtfstat_debug.so" if _DEBUG else "libtfstat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +31,7 @@ def nvcc_path() -> str:
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                   "-I", os.path.join(ROOT, "include")]
+                   "-I", os.path.join(ROOT, "include")] + (["-DTFS_DEBUG_CHECKS"] if _DEBUG else [])
 
 
 def _newest_dep() -> float:

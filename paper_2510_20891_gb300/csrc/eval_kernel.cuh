@@ -78,6 +78,8 @@ struct EvalArgs {
   int tie_cap;
   int* status;
   int* bins_out;  // [N][n_seg] or null; INT_MIN / INT_MAX mark windows wholly below / above the table
+  unsigned long long* dbg;  // self-check record (builds with TFS_DEBUG_CHECKS only), else unused
+  int smem_bytes;
   // launch shape
   int nst, cap, padl, slot_elems, qcap;
   // shared-memory carve-up (byte offsets)
@@ -92,6 +94,23 @@ struct SlotHdr {
 };
 
 constexpr int kSegTile = 32;  // FP32 partial sums are flushed every kSegTile segments
+
+// Self-checks of every shared and global index (compiled in with TFS_DEBUG_CHECKS): a failing
+// check records (site, two values) once and the caller skips the access.
+#ifdef TFS_DEBUG_CHECKS
+__device__ __forceinline__ bool dbg_ok(const EvalArgs& a, bool cond, int where, long long i0, long long i1) {
+  if (!cond && a.dbg) {
+    if (atomicAdd(&a.dbg[0], 1ull) == 0ull) {
+      a.dbg[1] = (unsigned long long)where;
+      a.dbg[2] = (unsigned long long)i0;
+      a.dbg[3] = (unsigned long long)i1;
+    }
+  }
+  return cond;
+}
+#else
+__device__ __forceinline__ bool dbg_ok(const EvalArgs&, bool, int, long long, long long) { return true; }
+#endif
 
 template <int DT>
 __device__ __forceinline__ float window_global(const EvalArgs& a, int seg, int lo, int W) {
@@ -122,6 +141,10 @@ __device__ __forceinline__ float window_smem(const typename Store<DT>::T* p, int
 template <int DT, int WT>
 __device__ float exact_pair(const EvalArgs& a, long long t, int seg, const typename Store<DT>::T* slot,
                             const SlotHdr& h, float scale, bool* tie) {
+  if (!dbg_ok(a, t >= 0 && t < a.N && seg >= 0 && seg < a.n_seg, 1, t, seg)) {
+    *tie = false;
+    return 0.f;
+  }
   double f = a.f_ref ? a.f_ref[t] : 0.0;
   const double* c = a.coeffs + t * (long long)a.K;
   for (int k = 0; k < a.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], a.U[(size_t)k * a.n_seg + seg]));
@@ -144,11 +167,13 @@ __device__ float exact_pair(const EvalArgs& a, long long t, int seg, const typen
   if (bo) *bo = b;
   const int lo = b - m;
   const int W = 2 * m + 1;
-  float v;
-  if ((unsigned)(lo - h.vlo) < (unsigned)h.span1)
-    v = window_smem<DT, WT>(slot + a.padl + (lo - h.blo), W);
-  else
+  float v = 0.f;
+  if ((unsigned)(lo - h.vlo) < (unsigned)h.span1) {
+    const int ix = a.padl + (lo - h.blo);
+    if (dbg_ok(a, ix >= 0 && ix + W <= a.slot_elems, 3, ix, lo)) v = window_smem<DT, WT>(slot + ix, W);
+  } else {
     v = window_global<DT>(a, seg, lo, W);
+  }
   return Store<DT>::scaled ? v * scale : v;
 }
 
@@ -342,16 +367,25 @@ __global__ void __launch_bounds__(NT) eval_stat_kernel(const EvalArgs a) {
     h.span1 = max(0, vhi - vlo - W + 1);
     h.pad = 0;
     hdr[s] = h;
-    const uint32_t dbytes = (uint32_t)blen * S::esize;
+    uint32_t dbytes = (uint32_t)blen * S::esize;
+    {
+      const long long dst_off = (long long)a.off_data + (long long)s * a.slot_bytes + (long long)a.padl * S::esize;
+      const long long src_el = (long long)sg * a.row_stride + blo;
+      const bool ok = dbg_ok(a, s >= 0 && s < a.nst && dst_off + dbytes <= a.smem_bytes, 7, dst_off, dbytes) &&
+                      dbg_ok(a, blo >= 0 && src_el + blen <= (long long)a.n_seg * a.row_stride, 8, src_el, blen) &&
+                      dbg_ok(a, ((dst_off | (long long)dbytes | (src_el * S::esize)) & 15) == 0, 9, dst_off, src_el) &&
+                      dbg_ok(a, (long long)a.off_segp + (long long)(s + 1) * a.nsp * 4 <= a.off_red, 10, s, a.nsp);
+      if (!ok) dbytes = 0;
+    }
     mbar_arrive_expect_tx(&mbar[s], dbytes + (uint32_t)a.nsp * 4u);
-    if (blen > 0)
+    if (dbytes > 0)
       bulk_g2s(sdata + (size_t)s * a.slot_bytes + (size_t)a.padl * S::esize,
                static_cast<const T*>(a.table) + (size_t)sg * a.row_stride + blo, dbytes, &mbar[s]);
     bulk_g2s(sseg + (size_t)s * a.nsp, dr, (uint32_t)a.nsp * 4u, &mbar[s]);
   };
 
   if (tid == 0) {
-    for (int sg = 0; sg < a.nst - 1 && sg < n_seg; ++sg) issue(sg, sg);
+    for (int sg = 0; sg < a.nst && sg < n_seg; ++sg) issue(sg, sg);
   }
 
   // ---------------------------------------------------------------- segments
@@ -402,10 +436,11 @@ __global__ void __launch_bounds__(NT) eval_stat_kernel(const EvalArgs a) {
         continue;
       }
       const int lo = b - m;
-      float v;
-      if ((unsigned)(lo - h.vlo) < (unsigned)h.span1)
-        v = window_smem<DT, WT>(slot + a.padl + (lo - h.blo), W);
-      else if (b + m < 0 || lo >= a.n_bin)
+      float v = 0.f;
+      if ((unsigned)(lo - h.vlo) < (unsigned)h.span1) {
+        const int ix = a.padl + (lo - h.blo);
+        if (dbg_ok(a, ix >= 0 && ix + W <= a.slot_elems, 5, ix, lo)) v = window_smem<DT, WT>(slot + ix, W);
+      } else if (b + m < 0 || lo >= a.n_bin)
         v = 0.f;
       else
         v = window_global<DT>(a, sg, lo, W);
@@ -437,6 +472,7 @@ __global__ void __launch_bounds__(NT) eval_stat_kernel(const EvalArgs a) {
     const int cnt = min(qcnt[q], a.qcap);
     for (int i = tid; i < cnt; i += NT) {
       const int lt = qent[q * a.qcap + i];
+      if (!dbg_ok(a, lt < NT * R, 6, lt, i)) continue;
       const long long t = tile0 + lt;
       bool tie;
       corr[lt] += exact_pair<DT, WT>(a, t, sg, slot, h, scale, &tie);
@@ -512,6 +548,7 @@ int launch_eval_dt(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st)
   a.tie_cap = L.tie_cap;
   a.status = L.status;
   a.bins_out = L.bins_out;
+  a.dbg = L.dbg;
 
   const int W = 2 * L.m + 1;
   a.nst = tune.stages > 0 ? tune.stages : 3;
@@ -546,6 +583,7 @@ int launch_eval_dt(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st)
   off = (off + 127) & ~(size_t)127;
   a.off_data = (int)off; off += (size_t)a.nst * a.slot_bytes;
   const size_t smem = off;
+  a.smem_bytes = (int)smem;
 
   const long long tile = (long long)NT * R;
   const long long gl = (L.N + tile - 1) / tile;

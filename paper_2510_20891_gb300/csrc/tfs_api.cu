@@ -13,6 +13,9 @@ namespace tfs {
 
 static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
+#ifdef TFS_DEBUG_CHECKS
+static unsigned long long g_dbg_last[4] = {0, 0, 0, 0};
+#endif
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
@@ -205,6 +208,13 @@ int64_t tfs_table_bytes(const tfs_table* t) { return t ? t->bytes : 0; }
 
 long long tfs_kernel_launches(void) { return tfs::g_launches.load(); }
 
+#ifdef TFS_DEBUG_CHECKS
+// Self-check record of the last statistic call (debug builds only): count, site, two values.
+void tfs_debug_last(unsigned long long* out) {
+  for (int i = 0; i < 4; ++i) out[i] = tfs::g_dbg_last[i];
+}
+#endif
+
 int tfs_table_free(tfs_table* t) {
   if (!t) return TFS_OK;
   if (t->sft_plan) free_sft_plan(t->sft_plan);
@@ -341,8 +351,19 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   L.tie_seg = d_ts;
   L.tie_cap = tie_cap;
   L.status = d_status;
+#ifdef TFS_DEBUG_CHECKS
+  unsigned long long* d_dbg = nullptr;
+  TFS_CUDA(cudaMallocAsync((void**)&d_dbg, 32, st));
+  TFS_CUDA(cudaMemsetAsync(d_dbg, 0, 32, st));
+  L.dbg = d_dbg;
+#endif
   rc = launch_eval(L, EvalTuning(), st);
   if (rc) return rc;
+#ifdef TFS_DEBUG_CHECKS
+  TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
+  TFS_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(d_dbg, st);
+#endif
 
   int64_t* d_ti = nullptr;
   float* d_tv = nullptr;

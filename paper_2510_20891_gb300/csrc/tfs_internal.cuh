@@ -100,6 +100,7 @@ struct EvalLaunch {
   int tie_cap;
   int* status;            // device
   int* bins_out = nullptr;  // device [N][n_seg] or null: the bin of every pair (verification only)
+  unsigned long long* dbg = nullptr;  // self-check record (TFS_DEBUG_CHECKS builds)
 };
 struct EvalTuning {       // launch shape; zeros select defaults
   int threads = 0;
