@@ -392,13 +392,16 @@ __global__ void __launch_bounds__(NT) eval_stat_kernel(const EvalArgs a) {
   int last_waited = -1;
   for (int sg = 0; sg < n_seg; ++sg) {
     const int s = sg % a.nst;
-    if (!mbar_wait_bounded(&mbar[s], (uint32_t)((sg / a.nst) & 1), kWaitLimitNs)) {
+    const bool filled = mbar_wait_bounded(&mbar[s], (uint32_t)((sg / a.nst) & 1), kWaitLimitNs);
+    if (!filled) {
+      // the slot never filled: touch none of it; the CTA leaves together after the barrier below
       qcnt[4 + (sg & 1)] = 1;  // per-parity flag: a thread already in the next segment cannot flip this one
       atomicExch(a.status, DEV_TIMEOUT);
     } else {
       last_waited = sg;
     }
-    const SlotHdr h = hdr[s];
+    SlotHdr h = {0, 0, 0, 0};
+    if (filled) h = hdr[s];
     const T* slot = reinterpret_cast<const T*>(sdata + (size_t)s * a.slot_bytes);
     float d[KP];
     {
@@ -414,6 +417,7 @@ __global__ void __launch_bounds__(NT) eval_stat_kernel(const EvalArgs a) {
     }
     const float scale = S::scaled ? __ldg(a.scales + sg) : 1.f;
     const int q = sg % 3;
+    if (filled) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       float y = y0[r];
@@ -451,6 +455,7 @@ __global__ void __launch_bounds__(NT) eval_stat_kernel(const EvalArgs a) {
           a.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (lo >= a.n_bin ? 0x7fffffff : b);
       }
     }
+    }  // filled
     if ((sg % kSegTile) == kSegTile - 1) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {

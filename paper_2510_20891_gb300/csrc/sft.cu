@@ -222,20 +222,58 @@ __global__ void quantise_rows(const double* __restrict__ P, long long ld, int n_
   void* row = static_cast<char*>(data) + (size_t)seg * row_stride * (DT == TFS_F32 ? 4 : (DT == TFS_F8E4M3 ? 1 : 2));
   double inv_s = 1.0;
   if (DT == TFS_F8E4M3) {
+    // M = min(max P, 256 * 2^e*), e* the lower median of floor(log2 P) over P > 0; s = fp32(M / 448)
+    constexpr int kEmin = -1100, kEbins = 2201;  // floor(log2) of any positive double, offset
+    __shared__ unsigned int hist[kEbins];
     __shared__ double wm[32];
+    __shared__ unsigned int npos_s[32];
+    __shared__ int estar;
+    for (int i = threadIdx.x; i < kEbins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
     double mx = 0.0;
-    for (int k = threadIdx.x; k < n_bin; k += blockDim.x) mx = fmax(mx, p[k]);
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+    unsigned int npos = 0;
+    for (int k = threadIdx.x; k < n_bin; k += blockDim.x) {
+      const double v = p[k];
+      if (v > 0.0) {
+        mx = fmax(mx, v);
+        ++npos;
+        const int e = ilogb(v);  // floor(log2 v), exact for every positive double
+        atomicAdd(&hist[min(max(e, kEmin), kEmin + kEbins - 1) - kEmin], 1u);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      npos += __shfl_xor_sync(0xffffffffu, npos, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wm[threadIdx.x >> 5] = mx;
+      npos_s[threadIdx.x >> 5] = npos;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wm[w]);
-      wm[0] = fmax(mx, wm[0]);
+      unsigned int n = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        mx = fmax(mx, wm[w]);
+        n += npos_s[w];
+      }
+      wm[0] = mx;
+      const unsigned int need = (n + 1) / 2;
+      unsigned int run = 0;
+      int es = 0;
+      for (int i = 0; i < kEbins && n > 0; ++i) {
+        run += hist[i];
+        if (run >= need) {
+          es = i + kEmin;
+          break;
+        }
+      }
+      estar = n > 0 ? es : 0;
+      npos_s[0] = n;
     }
     __syncthreads();
     mx = wm[0];
-    // s = fp32(max / 448) (1 for an all-zero row); the division P / s is FP64
-    const float s = mx > 0.0 ? __double2float_rn(mx / 448.0) : 1.0f;
+    const double M = npos_s[0] > 0 ? fmin(mx, 256.0 * ldexp(1.0, estar)) : 0.0;
+    const float s = M > 0.0 ? __double2float_rn(M / 448.0) : 1.0f;
     if (threadIdx.x == 0) scales[seg] = s;
     for (int k = threadIdx.x; k < n_bin; k += blockDim.x) {
       const double q = p[k] / (double)s;

@@ -298,10 +298,19 @@ def test_round_f8e4m3_matches_torch_and_hand_values():
 
 
 def test_quantise_f8_per_segment_scale():
+    # row 0: positive exponents floor(log2) = [0, 10]; lower median 0 -> M = min(1344, 256) = 256
     P = np.array([[0.0, 1.0, 448.0 * 3], [0.0, 0.0, 0.0]])
     deq, s = O.quantise_table(P, "f8e4m3")
-    assert s.dtype == np.float32 and s.tolist() == [3.0, 1.0]
-    assert deq.tolist() == [[0.0, 3.0 * O.round_f8e4m3(np.array([1 / 3]))[0], 1344.0], [0.0, 0.0, 0.0]]
+    assert s.dtype == np.float32 and s.tolist() == [np.float32(256 / 448), 1.0]
+    s0 = float(np.float32(256 / 448))
+    q1 = O.round_f8e4m3(np.array([1.0 / s0]))[0]
+    assert deq[0].tolist() == [0.0, float(np.float32(q1) * np.float32(s0)), float(np.float32(448.0) * np.float32(s0))]
+    assert deq[1].tolist() == [0.0, 0.0, 0.0]
+    # hand values of the row reference: exponents [1, 1, 5, 2] -> lower median 1 -> min(40, 512) = 40
+    assert O.f8_row_reference([2.0, 3.0, 40.0, 5.0]) == 40.0
+    # a leakage outlier: exponents [0, 1, 1, 26] -> lower median 1 -> M = 256 * 2 = 512
+    assert O.f8_row_reference([1.0, 2.0, 3.0, 1e8]) == 512.0
+    assert O.f8_row_reference([0.0, -1.0]) == 0.0
 
 
 # --------------------------------------------------------------------------
