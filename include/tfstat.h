@@ -188,6 +188,26 @@ long long tfs_kernel_launches(void);
  * 8 KB plus 16 bytes per 2048 elements) is allocated stream-ordered per call. */
 int tfs_topk(const float* val_in, int64_t N, int k, int64_t* idx, float* val, int mem, void* stream);
 
+/* ---- top-k that allocates nothing -----------------------------------------
+ * The paper has no counterpart; this is a service for callers that must not
+ * allocate device memory themselves or through the library: for example a
+ * serving loop that reserved all of its device memory up front under a
+ * budget, code that runs while another framework's allocator owns the
+ * device's free memory, or a latency-critical loop that cannot afford
+ * cudaMalloc / cudaFree, which may synchronise the device.
+ * Same result as tfs_topk (mem = DEVICE): val_in [N], idx [min(k, N)] and
+ * val [min(k, N)] are device pointers of the current device; work is enqueued
+ * on `stream` and the call returns without waiting.  The scratch is a fixed
+ * file-scope device array (about 74 KB, held by every device that loads the
+ * library until the process exits) for 1 <= N <= 2^26; larger N returns
+ * INVALID_ARG.  The call makes no allocation of any kind.  The first call on
+ * a device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and reinitialises what must start at zero,
+ * so calls whose work overlaps on the device (on different streams, or from
+ * different threads) race and give wrong results: order them. */
+int tfs_topk_noalloc(const float* val_in, int64_t N, int k, int64_t* idx, float* val, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

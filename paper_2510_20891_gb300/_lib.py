@@ -34,6 +34,7 @@ SIGNATURES = {
     "tfs_table_rebuild": (I, [P, P, I64, I, P]),
     "tfs_eval_bins": (I, [P, P, P, P, I64, I, P, I, P]),
     "tfs_kernel_launches": (ctypes.c_longlong, []),
+    "tfs_topk_noalloc": (I, [P, I64, I, P, P, P]),
 }
 
 ERR_NAMES = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY", -6: "NOT_FOUND"}

@@ -220,3 +220,47 @@ int topk_device(const float* v, int64_t N, int k, int64_t* idx_out, float* val_o
 }
 
 }  // namespace tfs
+
+// ---------------------------------------------------------------- top-k without allocation
+// Scratch for tfs_topk_noalloc: a file-scope device array sized for kNoAllocMaxN
+// inputs, held by every device that loads the library until the process exits.
+namespace tfs {
+namespace {
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 26;
+constexpr size_t kNoAllocBytes = 256 * 4 + 256 + (size_t)((kNoAllocMaxN + 4095) / 4096) * 4 + 1024 * 8 + 256;
+}  // namespace
+}  // namespace tfs
+
+static __device__ __align__(256) unsigned char g_topk_noalloc_ws[tfs::kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[128] = {nullptr};  // device address of the array, per device ordinal
+}  // namespace
+
+extern "C" int tfs_topk_noalloc(const float* val_in, int64_t N, int k, int64_t* idx, float* val, void* stream) {
+  using namespace tfs;
+  clear_error();
+  TFS_CHECK(val_in && idx && val, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(N >= 1 && N <= kNoAllocMaxN, TFS_ERR_INVALID_ARG,
+            "tfs_topk_noalloc handles 1 <= N <= %lld (got %lld)", (long long)kNoAllocMaxN, (long long)N);
+  TFS_CHECK(k >= 1 && k <= 1024, TFS_ERR_INVALID_ARG, "k must be in [1, 1024]");
+  TFS_CHECK(kNoAllocBytes >= topk_workspace_bytes(N), TFS_ERR_INVALID_ARG, "scratch too small");
+  int dev = 0;
+  TFS_CUDA(cudaGetDevice(&dev));
+  TFS_CHECK(dev >= 0 && dev < 128, TFS_ERR_INVALID_ARG, "device ordinal out of range");
+  void* ws = nullptr;
+  {
+    // one-time set-up per device, with that device current: the array's device address
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_topk_noalloc_ws);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(top-k scratch)");
+      g_noalloc_ptr[dev] = p;
+    }
+    ws = g_noalloc_ptr[dev];
+  }
+  const int kk = (int)std::min<int64_t>(k, N);
+  return topk_device(val_in, N, kk, idx, val, ws, static_cast<cudaStream_t>(stream));
+}
