@@ -72,8 +72,9 @@ constexpr int kProd = 128;            // producer warpgroup
 constexpr int kCons = 256;            // two consumer warpgroups
 constexpr int kThreads = kProd + kCons;
 constexpr int kConsWarps = kCons / 32;
-constexpr int kProdRegs = 56;         // setmaxnreg targets: 128*56 + 256*224 = 384*168
-constexpr int kConsRegs = 224;
+constexpr int kProdRegs = 72;         // setmaxnreg targets: 128*72 + 256*216 = 384*168
+constexpr int kConsRegs = 216;
+static_assert(kProd * kProdRegs + kCons * kConsRegs <= kThreads * 168, "register split exceeds the launch");
 constexpr int kNQ = 4;                // window-sum (Q) slots
 constexpr int kNP = 4;                // staging slots
 constexpr int kQT = 32;               // fix-up queue entries per consumer thread
@@ -316,7 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
     // ================================================================ producer warpgroup
     setmaxnreg_dec<kProdRegs>();
     uint32_t p_issue = 0, p_use = 0, q_seq = 0;
-    int plo_s[kNP], plen_s[kNP];  // thread 0's record of what each staging slot holds
+    int* plo_s = reinterpret_cast<int*>(smem + a.off_flags) + 4;  // [kNP] band start per staging slot
+    int* plen_s = plo_s + kNP;                                     // [kNP] band length
     float bx_lo[KP], bx_hi[KP];   // the current tile's coefficient box (thread 0)
     int bm = 0, bxm = -1;
     auto stage = [&](int sg) {  // thread 0
@@ -445,12 +447,17 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
 #pragma unroll
             for (int j = 0; j < 4; ++j) e[EALIGN + j] = nx[j];
             if (vi < nvec) {
+              // compile-time window widths keep e[] in registers; same order: ((0 + e0) + e1) + ...
               float out[EALIGN];
+              if (W == 1) {
 #pragma unroll
-              for (int i = 0; i < EALIGN; ++i) {
-                float s = 0.f;
-                for (int j = 0; j < W; ++j) s += e[i + j];
-                out[i] = s;
+                for (int i = 0; i < EALIGN; ++i) out[i] = 0.f + e[i];
+              } else if (W == 3) {
+#pragma unroll
+                for (int i = 0; i < EALIGN; ++i) out[i] = ((0.f + e[i]) + e[i + 1]) + e[i + 2];
+              } else {
+#pragma unroll
+                for (int i = 0; i < EALIGN; ++i) out[i] = ((((0.f + e[i]) + e[i + 1]) + e[i + 2]) + e[i + 3]) + e[i + 4];
               }
               float4* qv = reinterpret_cast<float4*>(q + (size_t)vi * EALIGN);
 #pragma unroll
@@ -790,7 +797,7 @@ int launch_eval_dt(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st)
   off = (off + 15) & ~(size_t)15;
   a.off_red = (int)off;   off += (size_t)2 * kConsWarps * RW * 4;
   off = (off + 15) & ~(size_t)15;
-  a.off_flags = (int)off; off += 16;
+  a.off_flags = (int)off; off += 16 + 2 * kNP * 4;  // flags, then the staging slots' band records
   a.off_queue = (int)off; off += (size_t)kQT * kCons * 4;
   a.off_acc = (int)off;   off += (size_t)2 * R * kCons * 4;
   off = (off + 127) & ~(size_t)127;
