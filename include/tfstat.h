@@ -53,7 +53,9 @@ extern "C" {
 #define TFS_F32 0    /* table storage: IEEE binary32 */
 #define TFS_BF16 1   /* bfloat16, round to nearest even */
 #define TFS_F16 2    /* IEEE binary16, round to nearest even (overflow -> inf) */
-#define TFS_F8E4M3 3 /* FP8 E4M3 with a per-segment FP32 scale s_alpha = max_k P / 448 */
+#define TFS_F8E4M3 3 /* FP8 E4M3 with a per-segment FP32 scale s_alpha: with e* the lower median of
+                        floor(log2 P) over the row's positive entries, s_alpha = fl32(min(max_k P,
+                        256 * 2^e*) / 448); stored codes saturate at 448 (outliers clip) */
 
 #define TFS_WINDOW_RECT 0 /* w[n] = 1 */
 #define TFS_WINDOW_HANN 1 /* periodic Hann, w[n] = sin^2(pi n / L) */
@@ -177,6 +179,39 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis, const double* 
  * wholly above the table or x is not finite.  N * n_seg < 2^34.  Synchronous. */
 int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis, const double* coeffs, const double* f_ref,
                   int64_t N, int m, int32_t* bins, int mem, void* stream);
+
+/* ---- steps 3-5 for many datasets in one launch ------------------------------
+ * The paper evaluates one dataset at a time; this entry point serves a batch
+ * of independent searches (different tables, bases, track counts, m) with a
+ * single persistent kernel launch per table dtype, so that small searches fill
+ * the GPU together.  Each job's results are bit-identical to tfs_eval_stat
+ * (mem = DEVICE) on the same job.  All pointers inside the jobs are device
+ * pointers of the current device; `jobs` itself is a host array of n_jobs
+ * (1 <= n_jobs <= 4096) entries, read during the call only.  Per job: table
+ * and basis with equal n_seg, 0 <= N < 2^31, 0 <= m <= 64, 0 <= topk <= 1024,
+ * stat [N] or NULL (then topk > 0), top_idx/top_val [min(topk, N)] when
+ * topk > 0.  Ties are not reported.
+ * dev_status: a device int, or NULL.  Given, the call is fully asynchronous
+ * and enqueues only stream-ordered work (cudaMallocAsync scratch, kernels,
+ * memsets), so it can be captured into a CUDA graph: it zeroes *dev_status,
+ * and a kernel sets it to 1 if a bounded device wait gave up.  NULL: the call
+ * waits for completion and returns TFS_ERR_TIMEOUT in that case.  The first
+ * call for a (basis, T_sft, coefficient slot count) builds cached per-segment
+ * data and synchronises `stream` once: make it before any capture. */
+typedef struct tfs_job {
+  const tfs_table* table;
+  const tfs_basis* basis;
+  const double* coeffs; /* [N][K] */
+  const double* f_ref;  /* [N] or NULL */
+  int64_t N;
+  int32_t m;
+  int32_t topk;
+  float* stat;          /* [N] or NULL */
+  int64_t* top_idx;     /* [min(topk, N)] */
+  float* top_val;       /* [min(topk, N)] */
+} tfs_job;
+
+int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* stream);
 
 /* Number of kernels this library has launched in this process (all devices). */
 long long tfs_kernel_launches(void);

@@ -8,6 +8,7 @@ marshals arguments.  Functions keep the C names without the ``tfs_`` prefix:
 * ``table_from_power(P, T_sft, dtype="f32")`` -> ``Table``
 * ``build_basis(tracks, K=0, tol=1e-7)`` -> ``Basis``;  ``basis_from_host(U)`` -> ``Basis``
 * ``eval_stat(table, basis, coeffs, f_ref=None, m=0, topk=0, ...)`` -> ``EvalResult``
+* ``eval_batch([Job(table, basis, coeffs, ...), ...], dev_status=None)`` -> the jobs, outputs filled
 * ``topk(values, k)`` -> (idx, val)
 
 Array arguments are numpy arrays (host memory: the call copies in and out
@@ -23,6 +24,7 @@ import os
 
 import numpy as np
 
+from . import _lib
 from ._lib import LIB_PATH, TfsError, check, lib  # noqa: F401
 
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "f8e4m3": 3}
@@ -220,6 +222,47 @@ def eval_stat(table: Table, basis: Basis, coeffs, f_ref=None, m: int = 0, topk: 
                                   rep_p, MEM_HOST, None))
     ties = list(zip(tt[: rep.n_stored].tolist(), ts[: rep.n_stored].tolist())) if want_ties else []
     return EvalResult(stat, top_idx, top_val, int(rep.count) if want_ties else None, ties)
+
+
+@dataclasses.dataclass
+class Job:
+    """One dataset of a batched evaluation (struct tfs_job); tensors on the CUDA device."""
+
+    table: Table
+    basis: Basis
+    coeffs: object
+    f_ref: object = None
+    m: int = 0
+    topk: int = 0
+    stat: object = None
+    top_idx: object = None
+    top_val: object = None
+
+
+def eval_batch(jobs, dev_status=None, stream=None):
+    """Statistic (and top-k) of many datasets in one persistent launch per dtype (tfs_eval_batch).
+
+    Outputs missing from a Job (stat, top-k) are allocated here and set on it.  With a device int32
+    `dev_status` the call is asynchronous and capturable into a CUDA graph; without one it waits.
+    """
+    torch = _torch()
+    arr = (_lib.TfsJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        N = j.coeffs.shape[0]
+        dev = j.coeffs.device
+        if j.stat is None:
+            j.stat = torch.empty(N, dtype=torch.float32, device=dev)
+        if j.topk > 0 and j.top_idx is None:
+            kk = min(j.topk, N)
+            j.top_idx = torch.empty(kk, dtype=torch.int64, device=dev)
+            j.top_val = torch.empty(kk, dtype=torch.float32, device=dev)
+        arr[i] = _lib.TfsJob(j.table.handle, j.basis.handle, _ptr(j.coeffs),
+                             _ptr(j.f_ref) if j.f_ref is not None else None, N, j.m, j.topk,
+                             _ptr(j.stat) if j.stat is not None else None,
+                             _ptr(j.top_idx) if j.topk else None, _ptr(j.top_val) if j.topk else None)
+    check(lib().tfs_eval_batch(arr, len(jobs), _ptr(dev_status) if dev_status is not None else None,
+                               _stream_ptr(stream)))
+    return jobs
 
 
 def topk(values, k: int, stream=None):

@@ -35,7 +35,25 @@ SIGNATURES = {
     "tfs_eval_bins": (I, [P, P, P, P, I64, I, P, I, P]),
     "tfs_kernel_launches": (ctypes.c_longlong, []),
     "tfs_topk_noalloc": (I, [P, I64, I, P, P, P]),
+    "tfs_eval_batch": (I, [P, I, P, P]),
 }
+
+
+class TfsJob(ctypes.Structure):
+    """struct tfs_job (include/tfstat.h): one dataset of a batched statistic launch."""
+
+    _fields_ = [
+        ("table", P),
+        ("basis", P),
+        ("coeffs", P),
+        ("f_ref", P),
+        ("N", I64),
+        ("m", ctypes.c_int32),
+        ("topk", ctypes.c_int32),
+        ("stat", P),
+        ("top_idx", P),
+        ("top_val", P),
+    ]
 
 ERR_NAMES = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY", -6: "NOT_FOUND"}
 

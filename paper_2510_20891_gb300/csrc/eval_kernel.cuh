@@ -2,35 +2,43 @@
 // (paper Sec. II.B Eq. det_stat, nearest-bin reading with +-m neighbours;
 // tracks from the SVD basis of Sec. II.C).
 //
-// Persistent, warp-specialised kernel: one CTA per SM walks tiles of 256*R
-// tracks (static round-robin).  Three warpgroups:
+// Persistent, warp-specialised kernel.  One CTA per SM walks a list of tiles
+// (static round-robin); a tile is 256*R tracks of one job, a job is one
+// dataset (table, basis, batch of tracks), so datasets of different shapes
+// run in one launch.  Three warpgroups:
 //
-//   producer warpgroup (128 threads, registers lowered with setmaxnreg) --
-//     thread 0 stages, for every segment alpha of the tile, the band of table
-//     row alpha the tile can touch (a rigorous interval bound from the tile's
-//     coefficient box) with a 1-D bulk copy (cp.async.bulk) completing on an
-//     mbarrier; the warpgroup then turns the staged band into window sums
-//         Q[b] = sum_{j=-m..m} P[alpha][b+j]       (FP32, fixed order)
-//     with 16-byte vector loads and lane shuffles, and signals the Q slot's
-//     "full" barrier;
-//   two consumer warpgroups (256 threads, registers raised with setmaxnreg) --
+//   producer warpgroup (128 threads, registers lowered with setmaxnreg)
+//     * at a tile start, all 128 threads compute, from the tile's coefficient
+//       box, a rigorous interval of the bins the tile can touch in every
+//       segment (the "band");
+//     * warp 0 (the stager) stages, segment after segment, the band of table
+//       row alpha into a staging slot with a 1-D bulk copy (cp.async.bulk)
+//       completing on an mbarrier;
+//     * warps 1-3 (the builders) turn each staged band into window sums
+//           Q[b] = sum_{j=-m..m} P[alpha][b+j]      (FP32, fixed order)
+//       with 16-byte vector loads and lane shuffles and signal the Q slot;
+//   two consumer warpgroups (256 threads, registers raised with setmaxnreg)
 //     per segment, each thread evaluates x = f T_SFT for its R tracks in FP32,
-//         y = (x_mid - B) + sum_k c_k D_k,alpha,    b = B + rint(y),
+//           y = (x_mid - B) + sum_k c_k D_k,alpha,    b = B + rint(y),
 //     (B = rint(x_mid), x_mid an FP64 per-track constant) and adds Q[b] with a
-//     single shared load, then its warp arrives on the slot's "empty" barrier.
-//     Pairs within a warp-uniform error bound g of a half-integer, and pairs
-//     whose centre falls outside the staged band, go to the thread's own queue
-//     and are recomputed at the end of the tile in the FP64 operation order
-//     of the oracle (separately rounded products and sums): every bin equals
-//     the FP64 bin exactly, ties included.
+//     single shared load.  Pairs within a warp-uniform error bound g of a
+//     half-integer, and pairs whose centre falls outside the staged band, go
+//     to the thread's own queue and are recomputed at the end of the tile in
+//     the FP64 operation order of the oracle (separately rounded products and
+//     sums): every bin equals the FP64 bin exactly, ties included.
 //
-// No CTA-wide barrier runs inside the segment loop: producer and consumers
-// meet only on mbarriers (Q ring, staging ring, per-tile box hand-off), so the
-// consumer warps run up to kNQ segments apart.  FP32 sums are flushed to a
-// second accumulator every 32 segments; fix-up contributions accumulate
-// separately in segment order, so a track's result does not depend on its
-// tile neighbours.  Every wait is bounded (2 s) and warp-uniform; a timeout
-// makes every role leave its loops and the call return TFS_ERR_TIMEOUT.
+// Inside a tile the roles meet only on mbarriers (staging ring full/empty,
+// Q ring full/empty, per-tile box hand-off); the consumer warps run up to kNQ
+// segments apart.  FP32 sums are flushed to a second accumulator every 32
+// segments; fix-up contributions accumulate separately in segment order.  The
+// result is deterministic for a given launch; which pairs take the fix-up path
+// depends on the warp's decision limit and the tile's band, so a track's FP32
+// rounding (never its bins) can change with its tile neighbours.  Tiles never
+// straddle jobs: a job gives bit-identical results alone and inside a batch
+// whose launch uses the same tracks per thread.
+// Every wait is bounded (2 s) and warp-uniform; after a timeout every role
+// keeps iterating without work (so barriers stay matched) and the call
+// returns TFS_ERR_TIMEOUT.
 #pragma once
 
 #include "tfs_internal.cuh"
@@ -68,7 +76,8 @@ struct Store<TFS_F8E4M3> {
   __device__ static float ld(const T* p) { return static_cast<float>(*p); }
 };
 
-constexpr int kProd = 128;            // producer warpgroup
+constexpr int kProd = 128;            // producer warpgroup: stager warp + 3 builder warps
+constexpr int kBuild = kProd - 32;    // builder threads
 constexpr int kCons = 256;            // two consumer warpgroups
 constexpr int kThreads = kProd + kCons;
 constexpr int kConsWarps = kCons / 32;
@@ -80,37 +89,44 @@ constexpr int kNP = 4;                // staging slots
 constexpr int kQT = 32;               // fix-up queue entries per consumer thread
 constexpr int kPadL = 16;             // zero elements before the staged band in a staging slot
 constexpr int kSegTile = 32;          // FP32 partial sums are flushed every kSegTile segments
+constexpr int kBandCap = 2048;        // segments whose bands are precomputed per tile
 
-struct EvalArgs {
+struct JobDesc {
   const void* table;
   const float* scales;
-  int n_seg, n_bin, row_stride;
-  double T;
-  const double* U;  // [K][n_seg]
-  int K, alpha_mid;
-  const float* segp;  // [n_seg][nsp]
-  int nsp;
-  const float* dmax;  // [KP]
-  const float* umax;  // [KP]
+  const double* U;      // [K][n_seg]
+  const float* segp;    // [n_seg][nsp]
+  const float* dmax;    // [KP]
+  const float* umax;    // [KP]
   const double* coeffs;
   const double* f_ref;
-  long long N;
-  int m;
   float* stat;
+  int* bins_out;        // [N][n_seg] (BINS instantiations); INT_MIN / INT_MAX: window wholly below / above
+  long long N;
+  double T;
+  int n_seg, n_bin, row_stride, m, K, alpha_mid;
+  int seg_resident;     // segp (and scales) copied to shared memory for this job's tiles
+  int pad;
+};
+
+template <int MJ>
+struct EvalArgs {
   unsigned long long* tie_count;
   long long* tie_track;
   int* tie_seg;
   int tie_cap;
   int* status;
-  int* bins_out;  // [N][n_seg] (BINS instantiations); INT_MIN / INT_MAX: window wholly below / above
   unsigned long long* dbg;  // self-check record (TFS_DEBUG_CHECKS builds)
   int smem_bytes;
+  int nsp;       // floats per segment row of segp (launch-wide)
   int qcap;      // floats per Q slot (>= kPadL + pcap + vector tail)
   int pcap;      // table elements of band per staging slot (multiple of 16 bytes)
   int n_tiles;
+  int n_jobs;
   // shared-memory carve-up (byte offsets)
-  int off_qhdr, off_red, off_flags, off_queue, off_acc, off_q, off_p;
-  int off_seg;  // resident copy of segp [n_seg][nsp] and scales [n_seg] (-1: read from global)
+  int off_qhdr, off_red, off_flags, off_band, off_seg, off_queue, off_acc, off_q, off_p;
+  int tile_start[MJ + 1];  // first tile of each job (prefix sums), tile_start[n_jobs] = n_tiles
+  JobDesc jobs[MJ];
 };
 
 struct QHdr {
@@ -121,36 +137,37 @@ struct QHdr {
 };
 
 #ifdef TFS_DEBUG_CHECKS
-__device__ __forceinline__ bool dbg_ok(const EvalArgs& a, bool cond, int where, long long i0, long long i1) {
-  if (!cond && a.dbg) {
-    if (atomicAdd(&a.dbg[0], 1ull) == 0ull) {
-      a.dbg[1] = (unsigned long long)where;
-      a.dbg[2] = (unsigned long long)i0;
-      a.dbg[3] = (unsigned long long)i1;
+__device__ __forceinline__ bool dbg_ok(unsigned long long* dbg, bool cond, int where, long long i0, long long i1) {
+  if (!cond && dbg) {
+    if (atomicAdd(&dbg[0], 1ull) == 0ull) {
+      dbg[1] = (unsigned long long)where;
+      dbg[2] = (unsigned long long)i0;
+      dbg[3] = (unsigned long long)i1;
     }
   }
   return cond;
 }
 #else
-__device__ __forceinline__ bool dbg_ok(const EvalArgs&, bool, int, long long, long long) { return true; }
+__device__ __forceinline__ bool dbg_ok(unsigned long long*, bool, int, long long, long long) { return true; }
 #endif
 
 // Window sum from the table in global memory; elements outside [0, n_bin) are 0.
 // The additions run in the same order as the shared-memory window sums.
 template <int DT>
-__device__ __forceinline__ float window_global(const EvalArgs& a, int seg, int lo, int W, float scale) {
+__device__ __forceinline__ float window_global(const JobDesc& J, int seg, int lo, int W, float scale) {
   using S = Store<DT>;
-  const typename S::T* row = static_cast<const typename S::T*>(a.table) + (size_t)seg * a.row_stride;
+  const typename S::T* row = static_cast<const typename S::T*>(J.table) + (size_t)seg * J.row_stride;
   float v = 0.f;
   for (int j = 0; j < W; ++j) {
     const int k = lo + j;
-    const float p = (k >= 0 && k < a.n_bin) ? S::ld(row + k) : 0.f;
+    const float p = (k >= 0 && k < J.n_bin) ? S::ld(row + k) : 0.f;
     v += S::scaled ? p * scale : p;
   }
   return v;
 }
 
-__device__ __forceinline__ void report_tie(const EvalArgs& a, long long t, int seg) {
+template <int MJ>
+__device__ __forceinline__ void report_tie(const EvalArgs<MJ>& a, long long t, int seg) {
   const unsigned long long i = atomicAdd(a.tie_count, 1ull);
   if (i < (unsigned long long)a.tie_cap) {
     a.tie_track[i] = t;
@@ -158,16 +175,16 @@ __device__ __forceinline__ void report_tie(const EvalArgs& a, long long t, int s
   }
 }
 
-// FP64 bin of (track t, segment seg) in the oracle's operation order, and its
-// window sum from global memory.
-template <int DT, bool BINS>
-__device__ float exact_pair(const EvalArgs& a, long long t, int seg) {
-  if (!dbg_ok(a, t >= 0 && t < a.N && seg >= 0 && seg < a.n_seg, 1, t, seg)) return 0.f;
-  double f = a.f_ref ? a.f_ref[t] : 0.0;
-  const double* c = a.coeffs + t * (long long)a.K;
-  for (int k = 0; k < a.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], a.U[(size_t)k * a.n_seg + seg]));
-  const double x = __dmul_rn(f, a.T);
-  int* bo = BINS ? a.bins_out + t * (long long)a.n_seg + seg : nullptr;
+// FP64 bin of (track t, segment seg) of job J in the oracle's operation order,
+// and its window sum from global memory.
+template <int DT, bool BINS, int MJ>
+__device__ float exact_pair(const EvalArgs<MJ>& a, const JobDesc& J, long long t, int seg) {
+  if (!dbg_ok(a.dbg, t >= 0 && t < J.N && seg >= 0 && seg < J.n_seg, 1, t, seg)) return 0.f;
+  double f = J.f_ref ? J.f_ref[t] : 0.0;
+  const double* c = J.coeffs + t * (long long)J.K;
+  for (int k = 0; k < J.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], J.U[(size_t)k * J.n_seg + seg]));
+  const double x = __dmul_rn(f, J.T);
+  int* bo = BINS ? J.bins_out + t * (long long)J.n_seg + seg : nullptr;
   if (!isfinite(x)) {
     if (BINS) *bo = 0x7fffffff;
     return 0.f;
@@ -175,15 +192,15 @@ __device__ float exact_pair(const EvalArgs& a, long long t, int seg) {
   const double fl = floor(x);
   if (fabs(__dsub_rn(__dsub_rn(x, fl), 0.5)) <= 1e-9) report_tie(a, t, seg);
   const double z = __dadd_rn(x, 0.5);
-  const int m = a.m;
-  if (z < -(double)m || z >= (double)a.n_bin + (double)m) {
+  const int m = J.m;
+  if (z < -(double)m || z >= (double)J.n_bin + (double)m) {
     if (BINS) *bo = z < 0.0 ? (int)0x80000000 : 0x7fffffff;
     return 0.f;
   }
   const int b = (int)floor(z);
   if (BINS) *bo = b;
-  const float scale = Store<DT>::scaled ? a.scales[seg] : 1.f;
-  return window_global<DT>(a, seg, b - m, 2 * m + 1, scale);
+  const float scale = Store<DT>::scaled ? J.scales[seg] : 1.f;
+  return window_global<DT>(J, seg, b - m, 2 * m + 1, scale);
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -201,13 +218,20 @@ __device__ __forceinline__ uint32_t mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done;
 }
-// Warp-uniform bounded wait: every lane observes the phase (acquire); the timeout and
-// abort decisions are lane 0's, broadcast to the warp.
+// Warp-uniform bounded wait.  Lane 0 alone polls (32 lanes polling one barrier flood the
+// shared-memory pipe that the working warps need); once it sees the phase complete, every
+// lane observes it too (acquire).  The timeout and abort decisions are lane 0's, broadcast
+// to the warp.  Returns false at once after an abort.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* flags) {
+  if (__any_sync(0xffffffffu, flags[0] != 0)) return false;
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
-    const uint32_t done = mbar_try(bar, parity);
-    if (__all_sync(0xffffffffu, done)) return true;
+    uint32_t done = 1;
+    if ((threadIdx.x & 31) == 0) done = mbar_try(bar, parity);
+    if (__shfl_sync(0xffffffffu, done, 0)) {
+      (void)mbar_try(bar, parity);  // the phase cannot move on before this warp's own next arrival
+      return true;
+    }
     if ((it & 31) == 0) {
       int stop = 0;
       if ((threadIdx.x & 31) == 0) {
@@ -215,24 +239,31 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
         if (it == 0) t0 = now;
         stop = flags[0] != 0 || (it != 0 && now - t0 > kWaitLimitNs);
       }
-      if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+      if (__shfl_sync(0xffffffffu, stop, 0)) {
+        flags[0] = 1;
+        return false;
+      }
     }
   }
 }
-// Single-thread bounded wait (producer thread 0).
+// Single-thread bounded wait.
 __device__ __forceinline__ bool thread_wait(uint64_t* bar, uint32_t parity, volatile int* flags) {
+  if (flags[0]) return false;
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 31) == 0) {
       const uint64_t now = global_ns();
       if (it == 0) t0 = now;
-      else if (flags[0] != 0 || now - t0 > kWaitLimitNs) return false;
+      else if (flags[0] != 0 || now - t0 > kWaitLimitNs) {
+        flags[0] = 1;
+        return false;
+      }
     }
   }
 }
-__device__ __forceinline__ void prod_bar() {  // named barrier 1 among the producer warpgroup
-  asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory");
+__device__ __forceinline__ void prod_bar() {  // named barrier 1 among the producer warpgroup (warps may be diverged)
+  asm volatile("barrier.sync 1, %0;" ::"n"(kProd) : "memory");
 }
 template <int N>
 __device__ __forceinline__ void setmaxnreg_inc() {
@@ -256,40 +287,84 @@ __device__ __forceinline__ void unpack16(const uint4 raw, float scale, float* ou
   }
 }
 
-template <int DT, int KP, int R, bool BINS>
-__global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a) {
+template <int MJ>
+__device__ __forceinline__ int job_of(const EvalArgs<MJ>& a, int tile) {
+  int j = 0;
+  while (j + 1 < a.n_jobs && tile >= a.tile_start[j + 1]) ++j;
+  return j;
+}
+
+// Band of staged table elements [blo, blo + blen) for segment row d of a tile whose
+// coefficient box is [lo_k, hi_k] and base bins [bm, bx] (FP32 with a margin covering
+// its rounding: the band only steers staging, bins outside it take the exact path).
+template <int KP, int EALIGN>
+__device__ __forceinline__ void band_of(const float* d, const float* blo_k, const float* bhi_k, int bm, int bx,
+                                        int m, int n_bin, int row_stride, int pcap, int* out_lo, int* out_len) {
+  int blo = 0, blen = 0;
+  if (bm <= bx) {
+    float lo = 0.f, hi = 0.f, mag = 0.f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const float p1 = blo_k[k] * d[k], p2 = bhi_k[k] * d[k];
+      lo += fminf(p1, p2);
+      hi += fmaxf(p1, p2);
+      mag += fmaxf(fabsf(p1), fabsf(p2));
+    }
+    const float fm = 4.f + 1e-5f * mag + 1e-6f * fmaxf(fabsf((float)bm), fabsf((float)bx));
+    const float bl = fmaxf(floorf((float)bm + lo - fm) - 2 * m, 0.f);
+    const float bh = fminf(floorf((float)bx + 1.f + hi + fm) + 2 * m, (float)(n_bin - 1));
+    if (bl <= bh) {
+      const int il = ((int)bl) & ~(EALIGN - 1);
+      int ih = ((int)bh + EALIGN) & ~(EALIGN - 1);
+      ih = min(ih, row_stride);
+      blo = il;
+      blen = min(ih - il, pcap);
+    }
+  }
+  *out_lo = blo;
+  *out_len = blen;
+}
+
+template <int DT, int KP, int R, bool BINS, int MJ>
+__global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_constant__ EvalArgs<MJ> a) {
   using S = Store<DT>;
   using T = typename S::T;
   constexpr int EALIGN = 16 / S::esize;  // table elements per 16 bytes (= EPV)
   constexpr int RW = 2 * KP + 2;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* full_p = bars;                     // [kNP] staging copies landed (tx)
-  uint64_t* full_q = bars + kNP;               // [kNQ] window sums ready (producer threads)
-  uint64_t* empty_q = bars + kNP + kNQ;        // [kNQ] consumers done with the slot (consumer warps)
-  uint64_t* tile_ready = bars + kNP + 2 * kNQ; // [2] a tile's coefficient box is ready (consumer warps)
-  QHdr* qhdr = reinterpret_cast<QHdr*>(smem + a.off_qhdr);     // [kNQ], then [kNQ][nsp] floats of D
+  uint64_t* full_p = bars;                           // [kNP] staged copy landed (tx)
+  uint64_t* empty_p = bars + kNP;                    // [kNP] builders done with the slot (3 warps)
+  uint64_t* full_q = bars + 2 * kNP;                 // [kNQ] window sums ready (96 builder threads)
+  uint64_t* empty_q = bars + 2 * kNP + kNQ;          // [kNQ] consumers done with the slot (8 warps)
+  uint64_t* tile_ready = bars + 2 * kNP + 2 * kNQ;   // [2] a tile's coefficient box is ready (8 warps)
+  QHdr* qhdr = reinterpret_cast<QHdr*>(smem + a.off_qhdr);  // [kNQ], then [kNQ][nsp] floats of D
   float* qdseg = reinterpret_cast<float*>(smem + a.off_qhdr + kNQ * sizeof(QHdr));
-  float* red = reinterpret_cast<float*>(smem + a.off_red);     // [2][kConsWarps][RW]
-  volatile int* flags = reinterpret_cast<volatile int*>(smem + a.off_flags);  // [0] abort, [1] producer go
-  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + a.off_queue);          // [kQT][kCons]
-  float* corr = reinterpret_cast<float*>(smem + a.off_acc);                   // [R][kCons]
-  float* tot = corr + R * kCons;                                              // [R][kCons]
-  float* qslots = reinterpret_cast<float*>(smem + a.off_q);                   // [kNQ][qcap]
-  unsigned char* pslots = smem + a.off_p;                                     // [kNP][pslot_bytes]
+  float* red = reinterpret_cast<float*>(smem + a.off_red);  // [2][kConsWarps][RW]
+  volatile int* flags = reinterpret_cast<volatile int*>(smem + a.off_flags);  // [0] abort
+  int* plo_s = reinterpret_cast<int*>(smem + a.off_flags) + 4;  // [kNP] band start per staging slot
+  int* plen_s = plo_s + kNP;                                    // [kNP] band length
+  float* box = reinterpret_cast<float*>(plen_s + kNP);          // [2*KP] floats, then 2 ints
+  int* band = reinterpret_cast<int*>(smem + a.off_band);        // [kBandCap][2]
+  float* segs = reinterpret_cast<float*>(smem + a.off_seg);     // resident segp [n_seg][nsp], scales [n_seg]
+  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + a.off_queue);  // [kQT][kCons]
+  float* corr = reinterpret_cast<float*>(smem + a.off_acc);           // [R][kCons]
+  float* tot = corr + R * kCons;                                      // [R][kCons]
+  float* qslots = reinterpret_cast<float*>(smem + a.off_q);           // [kNQ][qcap]
+  unsigned char* pslots = smem + a.off_p;                             // [kNP][pslot_bytes]
   const int pslot_bytes = (kPadL + a.pcap + EALIGN) * S::esize + a.nsp * 4;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int m = a.m;
-  const int W = 2 * m + 1;
-  const int n_seg = a.n_seg;
 
   if (tid < 4) flags[tid] = 0;
   if (tid == 0) {
-    for (int i = 0; i < kNP; ++i) mbar_init(&full_p[i], 1);
+    for (int i = 0; i < kNP; ++i) {
+      mbar_init(&full_p[i], 1);
+      mbar_init(&empty_p[i], kProd / 32 - 1);
+    }
     for (int i = 0; i < kNQ; ++i) {
-      mbar_init(&full_q[i], kProd);
+      mbar_init(&full_q[i], kBuild);
       mbar_init(&empty_q[i], kConsWarps);
     }
     for (int i = 0; i < 2; ++i) mbar_init(&tile_ready[i], kConsWarps);
@@ -300,198 +375,207 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
     T* sd = reinterpret_cast<T*>(pslots + (size_t)s * pslot_bytes);
     for (int i = tid; i < kPadL; i += kThreads) sd[i] = T(0.f);
   }
-  // the per-segment basis deltas (and FP8 scales) stay resident for the whole launch
-  const float* segp = a.segp;
-  const float* scales = a.scales;
-  if (a.off_seg >= 0) {
-    float* ss = reinterpret_cast<float*>(smem + a.off_seg);
-    for (int i = tid; i < n_seg * a.nsp; i += kThreads) ss[i] = a.segp[i];
-    if (S::scaled)
-      for (int i = tid; i < n_seg; i += kThreads) ss[n_seg * a.nsp + i] = a.scales[i];
-    segp = ss;
-    scales = ss + n_seg * a.nsp;
-  }
   __syncthreads();
 
   if (tid < kProd) {
     // ================================================================ producer warpgroup
     setmaxnreg_dec<kProdRegs>();
-    uint32_t p_issue = 0, p_use = 0, q_seq = 0;
-    int* plo_s = reinterpret_cast<int*>(smem + a.off_flags) + 4;  // [kNP] band start per staging slot
-    int* plen_s = plo_s + kNP;                                     // [kNP] band length
-    float bx_lo[KP], bx_hi[KP];   // the current tile's coefficient box (thread 0)
-    int bm = 0, bxm = -1;
-    auto stage = [&](int sg) {  // thread 0
-      const int ps = (int)(p_issue % kNP);
-      const float* dr = segp + (size_t)sg * a.nsp;
-      const float* drg = a.segp + (size_t)sg * a.nsp;  // the bulk copy's source stays global
-      int blo = 0, blen = 0;
-      if (bm <= bxm) {
-        float lo = 0.f, hi = 0.f, mag = 0.f;
-        for (int k = 0; k < KP; ++k) {
-          const float d = dr[k];
-          const float p1 = bx_lo[k] * d, p2 = bx_hi[k] * d;
-          lo += fminf(p1, p2);
-          hi += fmaxf(p1, p2);
-          mag += fmaxf(fabsf(p1), fabsf(p2));
-        }
-        // FP32 with a margin that covers its rounding: the band only steers staging
-        const float fm = 4.f + 1e-5f * mag + 1e-6f * fmaxf(fabsf((float)bm), fabsf((float)bxm));
-        const float bl = fmaxf(floorf((float)bm + lo - fm) - 2 * m, 0.f);
-        const float bh = fminf(floorf((float)bxm + 1.f + hi + fm) + 2 * m, (float)(a.n_bin - 1));
-        if (bl <= bh) {
-          const int il = ((int)bl) & ~(EALIGN - 1);
-          int ih = ((int)bh + EALIGN) & ~(EALIGN - 1);
-          ih = min(ih, a.row_stride);
-          blo = il;
-          blen = min(ih - il, a.pcap);
-        }
-      }
-      plo_s[ps] = blo;
-      plen_s[ps] = blen;
-      unsigned char* dst = pslots + (size_t)ps * pslot_bytes;
-      uint32_t dbytes = (uint32_t)blen * S::esize;
-      {
-        const long long src_el = (long long)sg * a.row_stride + blo;
-        const bool ok =
-            dbg_ok(a, (long long)a.off_p + (long long)(ps + 1) * pslot_bytes <= a.smem_bytes, 7, ps, pslot_bytes) &&
-            dbg_ok(a, blo >= 0 && src_el + blen <= (long long)a.n_seg * a.row_stride, 8, src_el, blen) &&
-            dbg_ok(a, ((a.off_p + (long long)ps * pslot_bytes) & 15) == 0 && (dbytes & 15) == 0 &&
-                          ((src_el * S::esize) & 15) == 0 && ((pslot_bytes & 15) == 0), 9, ps, src_el);
-        if (!ok) dbytes = 0;
-      }
-      fence_proxy_async_smem();  // the slot's previous contents were read through the generic proxy
-      mbar_arrive_expect_tx(&full_p[ps], dbytes + (uint32_t)a.nsp * 4u);
-      if (dbytes > 0)
-        bulk_g2s(dst + kPadL * S::esize, static_cast<const T*>(a.table) + (size_t)sg * a.row_stride + blo, dbytes,
-                 &full_p[ps]);
-      bulk_g2s(dst + (size_t)(kPadL + a.pcap + EALIGN) * S::esize, drg, (uint32_t)a.nsp * 4u, &full_p[ps]);
-      ++p_issue;
-    };
+    const int pw = tid >> 5;  // 0: stager, 1..3: builders
+    uint32_t p_seq = 0, b_seq = 0, q_seq = 0;
+    int cur_job = -1;
     int ltile = 0;
-    bool stop = false;
-    for (int tile = blockIdx.x; tile < a.n_tiles && !stop; tile += gridDim.x, ++ltile) {
-      // the consumers' coefficient box of this tile
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
+      const int j = job_of(a, tile);
+      const JobDesc& J = a.jobs[j];
+      const int n_seg = J.n_seg, m = J.m, W = 2 * m + 1;
+      // -------------------------------------------------------------- tile set-up (all 128)
       if (tid == 0) {
-        int go = thread_wait(&tile_ready[ltile & 1], (uint32_t)((ltile >> 1) & 1), flags);
-        if (go) {
+        if (thread_wait(&tile_ready[ltile & 1], (uint32_t)((ltile >> 1) & 1), flags)) {
           const float* rb = red + (ltile & 1) * kConsWarps * RW;
-          bm = 0x7fffffff;
-          bxm = -0x7fffffff;
+          int bm = 0x7fffffff, bx = -0x7fffffff;
           for (int k = 0; k < KP; ++k) {
-            bx_lo[k] = __int_as_float(0x7f800000);
-            bx_hi[k] = -__int_as_float(0x7f800000);
+            float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+            for (int w = 0; w < kConsWarps; ++w) {
+              lo = fminf(lo, rb[w * RW + k]);
+              hi = fmaxf(hi, rb[w * RW + KP + k]);
+            }
+            box[k] = lo;
+            box[KP + k] = hi;
           }
           for (int w = 0; w < kConsWarps; ++w) {
-            for (int k = 0; k < KP; ++k) {
-              bx_lo[k] = fminf(bx_lo[k], rb[w * RW + k]);
-              bx_hi[k] = fmaxf(bx_hi[k], rb[w * RW + KP + k]);
-            }
             bm = min(bm, reinterpret_cast<const int*>(rb)[w * RW + 2 * KP]);
-            bxm = max(bxm, reinterpret_cast<const int*>(rb)[w * RW + 2 * KP + 1]);
+            bx = max(bx, reinterpret_cast<const int*>(rb)[w * RW + 2 * KP + 1]);
           }
-          for (int sg = 0; sg < kNP && sg < n_seg; ++sg) stage(sg);
-        } else {
-          flags[0] = 1;
+          reinterpret_cast<int*>(box)[2 * KP] = bm;
+          reinterpret_cast<int*>(box)[2 * KP + 1] = bx;
         }
       }
-      for (int sg = 0; sg < n_seg; ++sg) {
-        const int ps = (int)(p_use % kNP), qs = (int)(q_seq % kNQ);
-        if (tid == 0) {
-          int go = !flags[0] && thread_wait(&full_p[ps], (p_use / kNP) & 1u, flags);
-          if (go && q_seq >= kNQ) go = thread_wait(&empty_q[qs], ((q_seq / kNQ) - 1u) & 1u, flags);
-          flags[1] = go ? plo_s[ps] : 0;
-          flags[2] = go ? plen_s[ps] : 0;
-          flags[3] = go;
-          if (!go) flags[0] = 1;
+      __syncwarp();
+      if (j != cur_job && J.seg_resident) {
+        prod_bar();  // no producer thread still reads the previous job's resident rows or scales
+        for (int i = tid; i < n_seg * a.nsp; i += kProd) segs[i] = J.segp[i];
+        if (S::scaled)
+          for (int i = tid; i < n_seg; i += kProd) segs[n_seg * a.nsp + i] = J.scales[i];
+      }
+      cur_job = j;
+      prod_bar();
+      const float* segrows = J.seg_resident ? segs : J.segp;
+      const float* sscales = J.seg_resident ? segs + n_seg * a.nsp : J.scales;
+      const int bm = reinterpret_cast<const int*>(box)[2 * KP];
+      const int bx = reinterpret_cast<const int*>(box)[2 * KP + 1];
+      if (n_seg <= kBandCap) {  // (band_of gives an in-range band for any box, even after an abort)
+        for (int sg = tid; sg < n_seg; sg += kProd) {
+          int lo, len;
+          band_of<KP, EALIGN>(segrows + (size_t)sg * a.nsp, box, box + KP, bm, bx, m, J.n_bin, J.row_stride,
+                              a.pcap, &lo, &len);
+          band[2 * sg] = lo;
+          band[2 * sg + 1] = len;
         }
-        prod_bar();
-        if (!flags[3]) {
-          stop = true;
-          break;
+      }
+      prod_bar();
+      if (pw == 0) {
+        // ------------------------------------------------------------ stager warp
+        for (int sg = 0; sg < n_seg; ++sg) {
+          const int ps = (int)(p_seq % kNP);
+          bool go = true;
+          if (p_seq >= kNP) go = warp_wait(&empty_p[ps], ((p_seq / kNP) - 1u) & 1u, flags);
+          else go = !__any_sync(0xffffffffu, flags[0] != 0);
+          if (go && lane == 0) {
+            int blo, blen;
+            if (n_seg <= kBandCap) {
+              blo = band[2 * sg];
+              blen = band[2 * sg + 1];
+            } else {
+              band_of<KP, EALIGN>(segrows + (size_t)sg * a.nsp, box, box + KP, bm, bx, m, J.n_bin, J.row_stride,
+                                  a.pcap, &blo, &blen);
+            }
+            plo_s[ps] = blo;
+            plen_s[ps] = blen;
+            unsigned char* dst = pslots + (size_t)ps * pslot_bytes;
+            uint32_t dbytes = (uint32_t)blen * S::esize;
+            {
+              const long long src_el = (long long)sg * J.row_stride + blo;
+              const bool ok =
+                  dbg_ok(a.dbg, (long long)a.off_p + (long long)(ps + 1) * pslot_bytes <= a.smem_bytes, 7, ps,
+                         pslot_bytes) &&
+                  dbg_ok(a.dbg, blo >= 0 && src_el + blen <= (long long)n_seg * J.row_stride, 8, src_el, blen) &&
+                  dbg_ok(a.dbg,
+                         ((a.off_p + (long long)ps * pslot_bytes) & 15) == 0 && (dbytes & 15) == 0 &&
+                             ((src_el * S::esize) & 15) == 0 && ((pslot_bytes & 15) == 0),
+                         9, ps, src_el);
+              if (!ok) dbytes = 0;
+            }
+            fence_proxy_async_smem();  // the slot's previous contents were read through the generic proxy
+            mbar_arrive_expect_tx(&full_p[ps], dbytes + (uint32_t)a.nsp * 4u);
+            if (dbytes > 0)
+              bulk_g2s(dst + kPadL * S::esize, static_cast<const T*>(J.table) + (size_t)sg * J.row_stride + blo,
+                       dbytes, &full_p[ps]);
+            bulk_g2s(dst + (size_t)(kPadL + a.pcap + EALIGN) * S::esize, J.segp + (size_t)sg * a.nsp,
+                     (uint32_t)a.nsp * 4u, &full_p[ps]);
+          }
+          __syncwarp();
+          ++p_seq;
         }
-        const int plo = flags[1], plen = flags[2];
-        const unsigned char* src = pslots + (size_t)ps * pslot_bytes;
-        // valid window starts (slot coordinates): wholly inside the staged band, or in the zero
-        // pad when the band starts at bin 0
-        // (windows reaching further below bin 0 than the pad covers are left to the FP64 queue)
-        const int ws_lo = plo == 0 ? max(kPadL - m, 0) : kPadL;
-        const int ws_hi = kPadL + plen - (W - 1);
-        const int qn = plen == 0 ? 0 : max(0, min(ws_hi, a.qcap - EALIGN) - ws_lo);
-        float* q = qslots + (size_t)qs * a.qcap;
-        const float scale = S::scaled ? scales[sg] : 1.f;
-        if (m <= 2) {
-          // vector path: thread j sums the windows starting at its EPV elements, taking the
-          // next 2m elements from the next lane (or, on a warp's last lane, from memory)
-          // vectors holding valid window starts, and (up to 4 elements further) the ones their
-          // windows reach into; both stay inside the slot (band + one vector of tail)
-          const int nvec = (ws_lo + qn + EALIGN - 1) / EALIGN;
-          const int nload = min((ws_lo + qn + 4 + EALIGN - 1) / EALIGN, kPadL / EALIGN + a.pcap / EALIGN + 1);
-          for (int v0 = 0; v0 < nvec; v0 += kProd) {
-            const int vi = v0 + tid;
-            float e[EALIGN + 4];
-            uint4 raw = make_uint4(0u, 0u, 0u, 0u);
-            if (vi < nload) raw = reinterpret_cast<const uint4*>(src)[vi];
-            unpack16<DT>(raw, scale, e);
-            float nx[4];
+      } else {
+        // ------------------------------------------------------------ builder warps
+        const int btid = tid - 32;
+        for (int sg = 0; sg < n_seg; ++sg) {
+          const int ps = (int)(b_seq % kNP), qs = (int)(q_seq % kNQ);
+          bool go = warp_wait(&full_p[ps], (b_seq / kNP) & 1u, flags);
+          if (go && q_seq >= kNQ) go = warp_wait(&empty_q[qs], ((q_seq / kNQ) - 1u) & 1u, flags);
+          if (go) {
+            const int plo = plo_s[ps], plen = plen_s[ps];
+            const unsigned char* src = pslots + (size_t)ps * pslot_bytes;
+            // valid window starts (slot coordinates): wholly inside the staged band, or in the zero
+            // pad when the band starts at bin 0 (windows reaching further below bin 0 than the pad
+            // covers are left to the FP64 queue)
+            const int ws_lo = plo == 0 ? max(kPadL - m, 0) : kPadL;
+            const int ws_hi = kPadL + plen - (W - 1);
+            const int qn = plen == 0 ? 0 : max(0, min(ws_hi, a.qcap - EALIGN) - ws_lo);
+            float* q = qslots + (size_t)qs * a.qcap;
+            const float scale = S::scaled ? sscales[sg] : 1.f;
+            if (m <= 2) {
+              // vector path: thread j sums the windows starting at its EPV elements, taking the next
+              // 2m elements from the next lane (or, on a warp's last lane, from shared memory)
+              const int nvec = (ws_lo + qn + EALIGN - 1) / EALIGN;
+              const int nload = min((ws_lo + qn + 4 + EALIGN - 1) / EALIGN, kPadL / EALIGN + a.pcap / EALIGN + 1);
+              // each pass: UV vectors (16 table elements) per thread, all loads issued first
+              constexpr int UV = 16 / EALIGN;
+              for (int v0 = 0; v0 < nvec; v0 += kBuild * UV) {
+                uint4 raw[UV];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) nx[j] = __shfl_down_sync(0xffffffffu, e[j], 1);
-            if (lane == 31 && vi < nvec) {
-              const T* tail = reinterpret_cast<const T*>(src) + (size_t)(vi + 1) * EALIGN;
+                for (int u = 0; u < UV; ++u) {
+                  const int vi = v0 + u * kBuild + btid;
+                  raw[u] = vi < nload ? reinterpret_cast<const uint4*>(src)[vi] : make_uint4(0u, 0u, 0u, 0u);
+                }
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const float p = S::ld(tail + j);
-                nx[j] = S::scaled ? p * scale : p;
+                for (int u = 0; u < UV; ++u) {
+                  const int vi = v0 + u * kBuild + btid;
+                  float e[EALIGN + 4];
+                  unpack16<DT>(raw[u], scale, e);
+                  float nx[4];
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) nx[k] = __shfl_down_sync(0xffffffffu, e[k], 1);
+                  if (lane == 31 && vi < nvec) {
+                    const T* tail = reinterpret_cast<const T*>(src) + (size_t)(vi + 1) * EALIGN;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                      const float p = S::ld(tail + k);
+                      nx[k] = S::scaled ? p * scale : p;
+                    }
+                  }
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) e[EALIGN + k] = nx[k];
+                  if (vi < nvec) {
+                    // compile-time window widths keep e[] in registers; same order: ((0 + e0) + e1) + ...
+                    float out[EALIGN];
+                    if (W == 1) {
+#pragma unroll
+                      for (int i = 0; i < EALIGN; ++i) out[i] = 0.f + e[i];
+                    } else if (W == 3) {
+#pragma unroll
+                      for (int i = 0; i < EALIGN; ++i) out[i] = ((0.f + e[i]) + e[i + 1]) + e[i + 2];
+                    } else {
+#pragma unroll
+                      for (int i = 0; i < EALIGN; ++i)
+                        out[i] = ((((0.f + e[i]) + e[i + 1]) + e[i + 2]) + e[i + 3]) + e[i + 4];
+                    }
+                    float4* qv = reinterpret_cast<float4*>(q + (size_t)vi * EALIGN);
+#pragma unroll
+                    for (int i4 = 0; i4 < EALIGN / 4; ++i4)
+                      qv[i4] = make_float4(out[4 * i4], out[4 * i4 + 1], out[4 * i4 + 2], out[4 * i4 + 3]);
+                  }
+                }
+              }
+            } else {
+              const T* pb = reinterpret_cast<const T*>(src);
+              for (int ws = ws_lo + btid; ws < ws_lo + qn; ws += kBuild) {
+                float s = 0.f;
+                for (int k = 0; k < W; ++k) {
+                  const float p = S::ld(pb + ws + k);
+                  s += S::scaled ? p * scale : p;
+                }
+                q[ws] = s;
               }
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) e[EALIGN + j] = nx[j];
-            if (vi < nvec) {
-              // compile-time window widths keep e[] in registers; same order: ((0 + e0) + e1) + ...
-              float out[EALIGN];
-              if (W == 1) {
-#pragma unroll
-                for (int i = 0; i < EALIGN; ++i) out[i] = 0.f + e[i];
-              } else if (W == 3) {
-#pragma unroll
-                for (int i = 0; i < EALIGN; ++i) out[i] = ((0.f + e[i]) + e[i + 1]) + e[i + 2];
-              } else {
-#pragma unroll
-                for (int i = 0; i < EALIGN; ++i) out[i] = ((((0.f + e[i]) + e[i + 1]) + e[i + 2]) + e[i + 3]) + e[i + 4];
-              }
-              float4* qv = reinterpret_cast<float4*>(q + (size_t)vi * EALIGN);
-#pragma unroll
-              for (int i4 = 0; i4 < EALIGN / 4; ++i4)
-                qv[i4] = make_float4(out[4 * i4], out[4 * i4 + 1], out[4 * i4 + 2], out[4 * i4 + 3]);
+            if (btid < a.nsp)
+              qdseg[qs * a.nsp + btid] =
+                  reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[btid];
+            if (btid == 0) {
+              QHdr h;
+              h.ws_lo = ws_lo;
+              h.qn = qn;
+              h.qbase = plo - kPadL + ws_lo + m;  // centre of the window starting at ws_lo
+              h.pad = 0;
+              qhdr[qs] = h;
             }
+            mbar_arrive(&full_q[qs]);  // every builder thread releases its own writes
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_p[ps]);
           }
-        } else {
-          const T* pb = reinterpret_cast<const T*>(src);
-          for (int ws = ws_lo + tid; ws < ws_lo + qn; ws += kProd) {
-            float s = 0.f;
-            for (int j = 0; j < W; ++j) {
-              const float p = S::ld(pb + ws + j);
-              s += S::scaled ? p * scale : p;
-            }
-            q[ws] = s;
-          }
+          ++b_seq;
+          ++q_seq;
         }
-        if (tid < a.nsp)
-          qdseg[qs * a.nsp + tid] =
-              reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[tid];
-        if (tid == 0) {
-          QHdr h;
-          h.ws_lo = ws_lo;
-          h.qn = qn;
-          h.qbase = plo - kPadL + ws_lo + m;  // centre of the window starting at ws_lo
-          h.pad = 0;
-          qhdr[qs] = h;
-        }
-        mbar_arrive(&full_q[qs]);  // every producer thread releases its own writes
-        prod_bar();                // the staging slot has been read by the whole warpgroup
-        ++p_use;
-        ++q_seq;
-        if (tid == 0 && sg + kNP < n_seg) stage(sg + kNP);
       }
     }
   } else {
@@ -502,15 +586,20 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
     uint32_t q_seq = 0;
     int ltile = 0;
     for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
-      if (__any_sync(0xffffffffu, flags[0] != 0)) break;  // warp-uniform
-      const long long tile0 = (long long)tile * (kCons * R);
+      const int j = job_of(a, tile);
+      const JobDesc& J = a.jobs[j];
+      const int n_seg = J.n_seg, m = J.m, K = J.K;
+      const long long tile0 = (long long)(tile - a.tile_start[j]) * (kCons * R);
+      const bool live = !__any_sync(0xffffffffu, flags[0] != 0);  // warp-uniform
       // -------------------------------------------------------------- tile prologue
       float c[R][KP];
       int B[R];
       float y0[R], acc[R];
-      float wlim = 2.f;  // warp-uniform decision limit: min over the warp's tracks of 1/2 - g
+      // warp-uniform decision limit: min over the warp's tracks of 1/2 - g; at most 1/2, so the
+      // tracks that take the FP64 path for every pair (y = 1/2) are never decided in FP32
+      float wlim = 0.5f;
       int nq = 0;        // entries in this thread's fix-up queue
-      {
+      if (live) {
         float cmn[KP], cmx[KP];
         int bmin = 0x7fffffff, bmax = -0x7fffffff;
 #pragma unroll
@@ -528,30 +617,30 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
           corr[r * kCons + ctid] = 0.f;
           tot[r * kCons + ctid] = 0.f;
           const long long t = tile0 + ctid + r * kCons;
-          if (t < a.N) {
-            const double fr = a.f_ref ? a.f_ref[t] : 0.0;
+          if (t < J.N) {
+            const double fr = J.f_ref ? J.f_ref[t] : 0.0;
             double f = fr;
             float A = 0.f, Um = fabsf((float)fr);
-            const double* cp = a.coeffs + t * (long long)a.K;
+            const double* cp = J.coeffs + t * (long long)K;
             float cf[KP];
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
-              const double cd = (k < a.K) ? cp[k] : 0.0;
-              if (k < a.K) f = fma(cd, a.U[(size_t)k * n_seg + a.alpha_mid], f);
+              const double cd = (k < K) ? cp[k] : 0.0;
+              if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
               cf[k] = (float)cd;
-              A = fmaf(fabsf(cf[k]), a.dmax[k], A);
-              Um = fmaf(fabsf(cf[k]), a.umax[k], Um);
+              A = fmaf(fabsf(cf[k]), J.dmax[k], A);
+              Um = fmaf(fabsf(cf[k]), J.umax[k], Um);
             }
             A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
             Um *= 1.0001f;
-            const double xm = f * a.T;
+            const double xm = f * J.T;
             // |fp32 estimate - exact x| <= err = 2^-24 ((K+1)/2 + (K+2.001) A) + e64, where
             // e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid, the
             // deltas D, and the oracle's own evaluation).  Pairs closer than g to a half-integer
             // are resolved in FP64; outside that band the exact, the oracle's and this bin
             // coincide and none of them is within the 1e-9 tie band.
-            const float e64 = 7.105427357601002e-15f * (float)a.T * Um;
-            const float err = 5.9604644775390625e-08f * (0.5f * (a.K + 1) + (a.K + 2.001f) * A) + e64;
+            const float e64 = 7.105427357601002e-15f * (float)J.T * Um;
+            const float err = 5.9604644775390625e-08f * (0.5f * (K + 1) + (K + 2.001f) * A) + e64;
             const float g = 1.25f * (err + e64) + 4e-9f;
             const bool exact = !(fabs(xm) < 1073741824.0) || !(g < 0.25f) || !(A < 1048576.0f);
             if (!exact) {
@@ -603,22 +692,19 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
         if (lane == 0) mbar_arrive(&tile_ready[ltile & 1]);
       }
       // -------------------------------------------------------------- segments
-      bool ok = true;
+      const unsigned nin = (unsigned)(J.n_bin + 2 * m);
       for (int sg = 0; sg < n_seg; ++sg) {
         const int qs = (int)(q_seq % kNQ);
+        ++q_seq;
+        if (!live || !warp_wait(&full_q[qs], ((q_seq - 1u) / kNQ) & 1u, flags)) continue;
         if (nq > kQT - R) {
           // not enough queue room for this segment: resolve the queue now, in (segment) order
           for (int i = 0; i < nq; ++i) {
             const uint32_t e = queue[i * kCons + ctid];
             const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
-            corr[r2 * kCons + ctid] += exact_pair<DT, BINS>(a, tile0 + ctid + r2 * kCons, s2);
+            corr[r2 * kCons + ctid] += exact_pair<DT, BINS>(a, J, tile0 + ctid + r2 * kCons, s2);
           }
           nq = 0;
-        }
-        if (!warp_wait(&full_q[qs], (q_seq / kNQ) & 1u, flags)) {
-          flags[0] = 1;
-          ok = false;
-          break;
         }
         const QHdr h = qhdr[qs];
         const float* q = qslots + (size_t)qs * a.qcap + h.ws_lo;
@@ -639,7 +725,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
         // the table iff 0 <= b + m < n_bin + 2m, i.e. (unsigned)(off + qbase + m) < n_bin + 2m.
         const int koff = -0x4B400000 - h.qbase;
         const int kin = h.qbase + m;
-        const unsigned nin = (unsigned)(a.n_bin + 2 * m);
         const unsigned qn = (unsigned)h.qn;
         unsigned offv[R];
         unsigned undecided = 0u, outside = 0u;
@@ -677,8 +762,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
           for (int r = 0; r < R; ++r) {
             const int b = (int)offv[r] + h.qbase;
             const long long t = tile0 + ctid + r * kCons;
-            if (t < a.N && !((pend >> r) & 1u))
-              a.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= a.n_bin ? 0x7fffffff : b);
+            if (t < J.N && !((pend >> r) & 1u))
+              J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
           }
         }
         if ((sg % kSegTile) == kSegTile - 1) {
@@ -690,19 +775,19 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_q[qs]);
-        ++q_seq;
       }
-      if (!ok) break;
       // -------------------------------------------------------------- tile epilogue
-      for (int i = 0; i < nq; ++i) {
-        const uint32_t e = queue[i * kCons + ctid];
-        const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
-        corr[r2 * kCons + ctid] += exact_pair<DT, BINS>(a, tile0 + ctid + r2 * kCons, s2);
-      }
+      if (live && !__any_sync(0xffffffffu, flags[0] != 0)) {
+        for (int i = 0; i < nq; ++i) {
+          const uint32_t e = queue[i * kCons + ctid];
+          const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
+          corr[r2 * kCons + ctid] += exact_pair<DT, BINS>(a, J, tile0 + ctid + r2 * kCons, s2);
+        }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const long long t = tile0 + ctid + r * kCons;
-        if (t < a.N) a.stat[t] = (tot[r * kCons + ctid] + acc[r]) + corr[r * kCons + ctid];
+        for (int r = 0; r < R; ++r) {
+          const long long t = tile0 + ctid + r * kCons;
+          if (t < J.N) J.stat[t] = (tot[r * kCons + ctid] + acc[r]) + corr[r * kCons + ctid];
+        }
       }
     }
   }
@@ -718,9 +803,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const EvalArgs a
 }
 
 // ---------------------------------------------------------------- host side
-template <int DT, int KP, int R, bool BINS>
-int launch_one(const EvalArgs& a0, int grid, size_t smem, cudaStream_t st) {
-  auto kern = eval_stat_kernel<DT, KP, R, BINS>;
+template <int DT, int KP, int R, bool BINS, int MJ>
+int launch_one(const EvalArgs<MJ>& a0, int grid, size_t smem, cudaStream_t st) {
+  auto kern = eval_stat_kernel<DT, KP, R, BINS, MJ>;
   static int configured = -1;
   if (configured < (int)smem) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -745,59 +830,89 @@ inline int sm_count() {
   return n;
 }
 
-template <int DT>
-int launch_eval_dt(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
+inline int r_of_kp(int KP) { return KP <= 6 ? 16 : (KP <= 8 ? 12 : (KP <= 16 ? 8 : 2)); }
+
+template <int DT, int MJ>
+int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
   constexpr int esize = Store<DT>::esize;
   constexpr int EPV = 16 / esize;
-  const tfs_table* tb = L.table;
-  const SegParams* sp = L.sp;
-  const int KP = sp->KP;
-  const int R = KP <= 8 ? 16 : (KP <= 16 ? 8 : 4);  // must match the instantiations below
-  if (L.N <= 0) return TFS_OK;
+  int KP = 0;
+  for (int i = 0; i < L.n_jobs; ++i) KP = std::max(KP, L.jobs[i].sp->KP);
+  const int R = r_of_kp(KP);
+  const int nsp = ((KP + 3) / 4) * 4;
 
-  EvalArgs a{};
-  a.table = tb->data;
-  a.scales = tb->scales;
-  a.n_seg = (int)tb->n_seg;
-  a.n_bin = (int)tb->n_bin;
-  a.row_stride = (int)tb->row_stride;
-  a.T = tb->T_sft;
-  a.U = L.basis->U;
-  a.K = L.basis->K;
-  a.alpha_mid = sp->alpha_mid;
-  a.segp = sp->segp;
-  a.nsp = sp->nsp;
-  a.dmax = sp->dmax;
-  a.umax = sp->umax;
-  a.coeffs = L.coeffs;
-  a.f_ref = L.f_ref;
-  a.N = L.N;
-  a.m = L.m;
-  a.stat = L.stat;
+  EvalArgs<MJ> a{};
   a.tie_count = L.tie_count;
   a.tie_track = reinterpret_cast<long long*>(L.tie_track);
   a.tie_seg = L.tie_seg;
   a.tie_cap = L.tie_cap;
   a.status = L.status;
-  a.bins_out = L.bins_out;
   a.dbg = L.dbg;
+  a.nsp = nsp;
+  const long long tile = (long long)kCons * R;
+  long long nt = 0;
+  int row_max = 0, seg_max = 0;
+  bool bins = false;
+  for (int i = 0; i < L.n_jobs; ++i) {
+    const EvalJob& E = L.jobs[i];
+    const tfs_table* tb = E.table;
+    if (E.sp->KP != KP || E.sp->nsp != nsp) {
+      set_error("internal: job %d has %d coefficient slots, launch %d", i, E.sp->KP, KP);
+      return TFS_ERR_INVALID_ARG;
+    }
+    JobDesc& D = a.jobs[i];
+    D.table = tb->data;
+    D.scales = tb->scales;
+    D.U = E.basis->U;
+    D.segp = E.sp->segp;
+    D.dmax = E.sp->dmax;
+    D.umax = E.sp->umax;
+    D.coeffs = E.coeffs;
+    D.f_ref = E.f_ref;
+    D.stat = E.stat;
+    D.bins_out = E.bins_out;
+    D.N = E.N;
+    D.T = tb->T_sft;
+    D.n_seg = (int)tb->n_seg;
+    D.n_bin = (int)tb->n_bin;
+    D.row_stride = (int)tb->row_stride;
+    D.m = E.m;
+    D.K = E.basis->K;
+    D.alpha_mid = E.sp->alpha_mid;
+    a.tile_start[i] = (int)nt;
+    nt += (E.N + tile - 1) / tile;
+    row_max = std::max(row_max, (int)tb->row_stride);
+    seg_max = std::max(seg_max, (int)tb->n_seg);
+    bins = bins || E.bins_out != nullptr;
+  }
+  if (nt == 0) return TFS_OK;
+  if (nt > 0x7fffffffLL) {
+    set_error("too many tracks for one launch");
+    return TFS_ERR_INVALID_ARG;
+  }
+  a.n_jobs = L.n_jobs;
+  a.tile_start[L.n_jobs] = (int)nt;
+  a.n_tiles = (int)nt;
 
   // staging slots hold up to pcap band elements; Q slots the window sums of a whole slot
   int pcap = tune.cap > 0 ? tune.cap : 2048;
-  pcap = std::max(64, std::min(pcap, (int)tb->row_stride));
+  pcap = std::max(64, std::min(pcap, row_max));
   pcap = (pcap + 31) / 32 * 32;
-  if (pcap > (int)tb->row_stride) pcap = (int)tb->row_stride;
+  if (pcap > row_max) pcap = row_max;
   a.pcap = pcap;
   a.qcap = kPadL + pcap + 2 * EPV;
   const int RW = 2 * KP + 2;
-  const size_t pslot_bytes = (size_t)(kPadL + pcap + EPV) * esize + sp->nsp * 4;
-  size_t off = 8 * (kNP + 2 * kNQ + 2);
+  const size_t pslot_bytes = (size_t)(kPadL + pcap + EPV) * esize + nsp * 4;
+  size_t off = 8 * (2 * kNP + 2 * kNQ + 2);
   off = (off + 15) & ~(size_t)15;
-  a.off_qhdr = (int)off;  off += kNQ * sizeof(QHdr) + (size_t)kNQ * sp->nsp * 4;
+  a.off_qhdr = (int)off;  off += kNQ * sizeof(QHdr) + (size_t)kNQ * nsp * 4;
   off = (off + 15) & ~(size_t)15;
   a.off_red = (int)off;   off += (size_t)2 * kConsWarps * RW * 4;
   off = (off + 15) & ~(size_t)15;
-  a.off_flags = (int)off; off += 16 + 2 * kNP * 4;  // flags, then the staging slots' band records
+  a.off_flags = (int)off; off += 16 + 2 * kNP * 4 + (size_t)(2 * KP + 2) * 4;
+  off = (off + 15) & ~(size_t)15;
+  a.off_band = (int)off;  off += (size_t)2 * std::min(seg_max, kBandCap) * 4;
+  off = (off + 15) & ~(size_t)15;
   a.off_queue = (int)off; off += (size_t)kQT * kCons * 4;
   a.off_acc = (int)off;   off += (size_t)2 * R * kCons * 4;
   off = (off + 127) & ~(size_t)127;
@@ -805,44 +920,48 @@ int launch_eval_dt(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st)
   off = (off + 127) & ~(size_t)127;
   a.off_p = (int)off;     off += (size_t)kNP * pslot_bytes;
   off = (off + 15) & ~(size_t)15;
-  const size_t seg_bytes = (size_t)tb->n_seg * (sp->nsp + 1) * 4;
-  a.off_seg = -1;
-  if (off + seg_bytes <= 200 * 1024) {  // resident per-segment data when it fits
-    a.off_seg = (int)off;
-    off += seg_bytes;
-  }
+  a.off_seg = (int)off;
+  size_t seg_bytes = (size_t)seg_max * (nsp + 1) * 4;
+  const bool resident = off + seg_bytes <= 200 * 1024;  // resident per-segment data when it fits
+  if (!resident) seg_bytes = 0;
+  for (int i = 0; i < L.n_jobs; ++i) a.jobs[i].seg_resident = resident ? 1 : 0;
+  off += seg_bytes;
   const size_t smem = off;
   a.smem_bytes = (int)smem;
   if (smem > 227 * 1024) {
     set_error("statistic kernel needs %zu bytes of shared memory", smem);
     return TFS_ERR_INVALID_ARG;
   }
-
-  const long long tile = (long long)kCons * R;
-  const long long nt = (L.N + tile - 1) / tile;
-  if (nt > 0x7fffffffLL) {
-    set_error("too many tracks for one launch");
-    return TFS_ERR_INVALID_ARG;
-  }
-  a.n_tiles = (int)nt;
   const int grid = (int)std::min<long long>(nt, (long long)sm_count());
-  const bool bins = L.bins_out != nullptr;
 
 #define TFS_LAUNCH_KP(KPV, RV)                                                          \
   if (KP == KPV) {                                                                      \
-    return bins ? launch_one<DT, KPV, RV, true>(a, grid, smem, st)                      \
-                : launch_one<DT, KPV, RV, false>(a, grid, smem, st);                    \
+    if constexpr (MJ == 1) {                                                            \
+      if (bins) return launch_one<DT, KPV, RV, true, MJ>(a, grid, smem, st);            \
+    }                                                                                   \
+    return launch_one<DT, KPV, RV, false, MJ>(a, grid, smem, st);                        \
   }
   TFS_LAUNCH_KP(2, 16)
   TFS_LAUNCH_KP(4, 16)
   TFS_LAUNCH_KP(6, 16)
-  TFS_LAUNCH_KP(8, 16)
+  TFS_LAUNCH_KP(8, 12)
   TFS_LAUNCH_KP(16, 8)
-  TFS_LAUNCH_KP(32, 4)
+  TFS_LAUNCH_KP(32, 2)
 #undef TFS_LAUNCH_KP
   (void)R;
-  set_error("unsupported basis size K=%d", L.basis->K);
+  set_error("unsupported coefficient slot count %d", KP);
   return TFS_ERR_INVALID_ARG;
+}
+
+template <int DT>
+int launch_eval_dt(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
+  if (L.n_jobs <= 0) return TFS_OK;
+  if (L.n_jobs == 1) return launch_eval_jobs<DT, 1>(L, tune, st);
+  if (L.n_jobs > kMaxJobs) {
+    set_error("at most %d jobs per launch", kMaxJobs);
+    return TFS_ERR_INVALID_ARG;
+  }
+  return launch_eval_jobs<DT, kMaxJobs>(L, tune, st);
 }
 
 }  // namespace tfs

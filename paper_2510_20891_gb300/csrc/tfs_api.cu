@@ -104,50 +104,58 @@ __global__ void segparams_kernel(const double* __restrict__ U, int K, int KP, in
   }
 }
 
-static int pick_kp(int K) {
+int pick_kp(int K) {
   const int opts[] = {2, 4, 6, 8, 16, 32};
   for (int v : opts)
     if (K <= v) return v;
   return -1;
 }
 
-static void free_segparams(SegParams& s) {
-  if (s.segp) cudaFree(s.segp);
-  if (s.dmax) cudaFree(s.dmax);
-  if (s.umax) cudaFree(s.umax);
-  s = SegParams();
+static void free_segparams(SegParams* s) {
+  if (!s) return;
+  if (s->segp) cudaFree(s->segp);
+  if (s->dmax) cudaFree(s->dmax);
+  if (s->umax) cudaFree(s->umax);
+  delete s;
 }
 
-int get_segparams(tfs_basis* b, double T, cudaStream_t st, SegParams** out) {
+int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams** out) {
   std::lock_guard<std::mutex> lk(b->mu);
-  if (b->sp.segp && b->sp.T == T) {
-    *out = &b->sp;
-    return TFS_OK;
+  const int KP = pick_kp(std::max(b->K, kp_min));
+  TFS_CHECK(KP > 0, TFS_ERR_INVALID_ARG, "basis size K=%d exceeds 32", std::max(b->K, kp_min));
+  for (SegParams* s : b->sps)
+    if (s->T == T && s->KP == KP) {
+      *out = s;
+      return TFS_OK;
+    }
+  SegParams* s = new SegParams();
+  s->T = T;
+  s->KP = KP;
+  s->nsp = ((KP + 3) / 4) * 4;
+  s->alpha_mid = (int)(b->n_seg / 2);
+  cudaError_t e = cudaMalloc(&s->segp, (size_t)b->n_seg * s->nsp * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->dmax, 32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->umax, 32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->segp, 0, (size_t)b->n_seg * s->nsp * sizeof(float), st);
+  if (e == cudaSuccess) {
+    segparams_kernel<<<KP, 256, 0, st>>>(b->U, b->K, KP, (int)b->n_seg, s->nsp, s->alpha_mid, T, s->segp,
+                                         s->dmax, s->umax);
+    count_launch();
+    e = cudaGetLastError();
   }
-  free_segparams(b->sp);
-  const int KP = pick_kp(b->K);
-  TFS_CHECK(KP > 0, TFS_ERR_INVALID_ARG, "basis size K=%d exceeds 32", b->K);
-  SegParams s;
-  s.T = T;
-  s.KP = KP;
-  s.nsp = ((KP + 3) / 4) * 4;
-  s.alpha_mid = (int)(b->n_seg / 2);
-  TFS_CUDA(cudaMalloc(&s.segp, (size_t)b->n_seg * s.nsp * sizeof(float)));
-  TFS_CUDA(cudaMalloc(&s.dmax, 32 * sizeof(float)));
-  TFS_CUDA(cudaMalloc(&s.umax, 32 * sizeof(float)));
-  TFS_CUDA(cudaMemsetAsync(s.segp, 0, (size_t)b->n_seg * s.nsp * sizeof(float), st));
-  segparams_kernel<<<KP, 256, 0, st>>>(b->U, b->K, KP, (int)b->n_seg, s.nsp, s.alpha_mid, T, s.segp, s.dmax,
-                                       s.umax);
-  count_launch();
-  TFS_CUDA(cudaGetLastError());
-  TFS_CUDA(cudaStreamSynchronize(st));  // one-off per (basis, T): later calls may use other streams
-  b->sp = s;
-  *out = &b->sp;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // one-off per (basis, T, KP): later calls may use other streams
+  if (e != cudaSuccess) {
+    free_segparams(s);
+    return cuda_fail(e, "segment parameters");
+  }
+  b->sps.push_back(s);
+  *out = s;
   return TFS_OK;
 }
 
 int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
-  switch (L.table->dtype) {
+  if (L.n_jobs <= 0) return TFS_OK;
+  switch (L.jobs[0].table->dtype) {
     case TFS_F32: return launch_eval_f32(L, tune, st);
     case TFS_BF16: return launch_eval_bf16(L, tune, st);
     case TFS_F16: return launch_eval_f16(L, tune, st);
@@ -271,9 +279,7 @@ int tfs_basis_to_host(const tfs_basis* b, double* U, double* sigma, double* cmin
 int tfs_basis_free(tfs_basis* b) {
   if (!b) return TFS_OK;
   if (b->U) cudaFree(b->U);
-  if (b->sp.segp) cudaFree(b->sp.segp);
-  if (b->sp.dmax) cudaFree(b->sp.dmax);
-  if (b->sp.umax) cudaFree(b->sp.umax);
+  for (SegParams* s : b->sps) free_segparams(s);
   delete b;
   return TFS_OK;
 }
@@ -292,7 +298,7 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   TFS_CHECK(topk >= 0 && topk <= 1024, TFS_ERR_INVALID_ARG, "topk must be in [0, 1024]");
   TFS_CHECK(N == 0 || coeffs, TFS_ERR_INVALID_ARG, "null coeffs");
   TFS_CHECK(stat || topk > 0 || N == 0, TFS_ERR_INVALID_ARG, "need stat or topk > 0");
-  TFS_CHECK(topk == 0 || (top_idx && top_val), TFS_ERR_INVALID_ARG, "null top-k outputs");
+  TFS_CHECK(topk == 0 || N == 0 || (top_idx && top_val), TFS_ERR_INVALID_ARG, "null top-k outputs");
   TFS_CHECK(topk == 0 || N < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "top-k needs N < 2^31");
   TFS_CHECK(!ties || ties->capacity == 0 || (ties->track && ties->seg), TFS_ERR_INVALID_ARG,
             "tie report arrays missing");
@@ -303,7 +309,7 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   const int kk = (int)std::min<int64_t>(topk, N);
 
   SegParams* sp = nullptr;
-  int rc = get_segparams(basis, table->T_sft, st, &sp);
+  int rc = get_segparams(basis, table->T_sft, 0, st, &sp);
   if (rc) return rc;
 
   // one arena for everything this call needs on the device
@@ -337,20 +343,8 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   TFS_CUDA(cudaMemsetAsync(d_tc, 0, sizeof(unsigned long long), st));
   TFS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
 
-  EvalLaunch L;
-  L.table = table;
-  L.basis = basis;
-  L.sp = sp;
-  L.coeffs = d_c;
-  L.f_ref = d_f;
-  L.N = N;
-  L.m = m;
-  L.stat = d_stat;
-  L.tie_count = d_tc;
-  L.tie_track = d_tt;
-  L.tie_seg = d_ts;
-  L.tie_cap = tie_cap;
-  L.status = d_status;
+  EvalJob J{table, basis, sp, d_c, d_f, N, m, d_stat, nullptr};
+  EvalLaunch L{&J, 1, d_tc, d_tt, d_ts, tie_cap, d_status};
 #ifdef TFS_DEBUG_CHECKS
   unsigned long long* d_dbg = nullptr;
   TFS_CUDA(cudaMallocAsync((void**)&d_dbg, 32, st));
@@ -413,7 +407,7 @@ int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis_c, const double
   if (N == 0) return TFS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SegParams* sp = nullptr;
-  int rc = get_segparams(basis, table->T_sft, st, &sp);
+  int rc = get_segparams(basis, table->T_sft, 0, st, &sp);
   if (rc) return rc;
   const bool host = mem == TFS_MEM_HOST;
   const int K = basis->K;
@@ -444,21 +438,8 @@ int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis_c, const double
   }
   TFS_CUDA(cudaMemsetAsync(d_tc, 0, 8, st));
   TFS_CUDA(cudaMemsetAsync(d_status, 0, 4, st));
-  EvalLaunch L;
-  L.table = table;
-  L.basis = basis;
-  L.sp = sp;
-  L.coeffs = d_c;
-  L.f_ref = d_f;
-  L.N = N;
-  L.m = m;
-  L.stat = d_stat;
-  L.tie_count = d_tc;
-  L.tie_track = d_tt;
-  L.tie_seg = d_ts;
-  L.tie_cap = 0;
-  L.status = d_status;
-  L.bins_out = d_b;
+  EvalJob J{table, basis, sp, d_c, d_f, N, m, d_stat, d_b};
+  EvalLaunch L{&J, 1, d_tc, d_tt, d_ts, 0, d_status};
   rc = launch_eval(L, EvalTuning(), st);
   if (rc) return rc;
   if (host) TFS_CUDA(cudaMemcpyAsync(bins, d_b, nb * 4, cudaMemcpyDeviceToHost, st));
@@ -466,6 +447,97 @@ int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis_c, const double
   TFS_CUDA(cudaMemcpyAsync(&h_status, d_status, 4, cudaMemcpyDeviceToHost, st));
   TFS_CUDA(cudaStreamSynchronize(st));
   TFS_CHECK(h_status == 0, TFS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", h_status);
+  return TFS_OK;
+}
+
+int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* stream) {
+  clear_error();
+  TFS_CHECK(jobs && n_jobs >= 1 && n_jobs <= 4096, TFS_ERR_INVALID_ARG, "need 1 <= n_jobs <= 4096 jobs");
+  for (int i = 0; i < n_jobs; ++i) {
+    const tfs_job& j = jobs[i];
+    TFS_CHECK(j.table && j.basis, TFS_ERR_INVALID_ARG, "job %d: null table or basis", i);
+    TFS_CHECK(j.basis->n_seg == j.table->n_seg, TFS_ERR_INVALID_ARG, "job %d: basis and table segment counts differ",
+              i);
+    TFS_CHECK(j.N >= 0 && j.N < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "job %d: N must be in [0, 2^31)", i);
+    TFS_CHECK(j.m >= 0 && j.m <= 64, TFS_ERR_INVALID_ARG, "job %d: m must be in [0, 64]", i);
+    TFS_CHECK(j.topk >= 0 && j.topk <= 1024, TFS_ERR_INVALID_ARG, "job %d: topk must be in [0, 1024]", i);
+    TFS_CHECK(j.N == 0 || j.coeffs, TFS_ERR_INVALID_ARG, "job %d: null coeffs", i);
+    TFS_CHECK(j.stat || j.topk > 0 || j.N == 0, TFS_ERR_INVALID_ARG, "job %d: need stat or topk > 0", i);
+    TFS_CHECK(j.topk == 0 || j.N == 0 || (j.top_idx && j.top_val), TFS_ERR_INVALID_ARG, "job %d: null top-k outputs",
+              i);
+    TFS_CHECK(pick_kp(j.basis->K) > 0, TFS_ERR_INVALID_ARG, "job %d: basis size exceeds 32", i);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // one launch per table dtype, with the widest coefficient slot count among its jobs
+  int kp_of[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n_jobs; ++i) {
+    int& kp = kp_of[jobs[i].table->dtype];
+    kp = std::max(kp, pick_kp(jobs[i].basis->K));
+  }
+  std::vector<SegParams*> sps(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    int rc = get_segparams(const_cast<tfs_basis*>(jobs[i].basis), jobs[i].table->T_sft,
+                           kp_of[jobs[i].table->dtype], st, &sps[i]);
+    if (rc) return rc;
+  }
+  size_t need = round256(8) + round256(4) + round256(8) + round256(4);
+  size_t ws_max = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    if (!jobs[i].stat) need += round256((size_t)jobs[i].N * 4);
+    if (jobs[i].topk > 0 && jobs[i].N > 0) ws_max = std::max(ws_max, topk_workspace_bytes(jobs[i].N));
+  }
+  need += round256(ws_max);
+  Arena ar;
+  int rc = ar.init(need, st);
+  if (rc) return rc;
+  unsigned long long* d_tc = ar.take<unsigned long long>(1);
+  int* d_status = dev_status ? dev_status : ar.take<int>(1);
+  int64_t* d_tt = ar.take<int64_t>(1);
+  int* d_ts = ar.take<int>(1);
+  void* ws = ws_max ? ar.take<char>(ws_max) : nullptr;
+  std::vector<EvalJob> ej(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    const tfs_job& j = jobs[i];
+    float* stat = j.stat ? j.stat : ar.take<float>((size_t)j.N);
+    ej[i] = EvalJob{j.table, j.basis, sps[i], j.coeffs, j.f_ref, j.N, j.m, stat, nullptr};
+  }
+  TFS_CUDA(cudaMemsetAsync(d_tc, 0, 8, st));
+  TFS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  unsigned long long* d_dbg = nullptr;
+#ifdef TFS_DEBUG_CHECKS
+  TFS_CUDA(cudaMallocAsync((void**)&d_dbg, 32, st));
+  TFS_CUDA(cudaMemsetAsync(d_dbg, 0, 32, st));
+#endif
+  for (int dt = 0; dt < 4; ++dt) {
+    if (!kp_of[dt]) continue;
+    std::vector<EvalJob> group;
+    for (int i = 0; i < n_jobs; ++i)
+      if (jobs[i].table->dtype == dt && jobs[i].N > 0) group.push_back(ej[i]);
+    for (size_t g0 = 0; g0 < group.size(); g0 += kMaxJobs) {
+      const int n = (int)std::min<size_t>(kMaxJobs, group.size() - g0);
+      EvalLaunch L{group.data() + g0, n, d_tc, d_tt, d_ts, 0, d_status, d_dbg};
+      rc = launch_eval(L, EvalTuning(), st);
+      if (rc) return rc;
+    }
+  }
+#ifdef TFS_DEBUG_CHECKS
+  TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
+  TFS_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(d_dbg, st);
+#endif
+  // top-k per job, one after another on the stream (they share the scratch)
+  for (int i = 0; i < n_jobs; ++i) {
+    const tfs_job& j = jobs[i];
+    if (j.topk == 0 || j.N == 0) continue;
+    rc = topk_device(ej[i].stat, j.N, (int)std::min<int64_t>(j.topk, j.N), j.top_idx, j.top_val, ws, st);
+    if (rc) return rc;
+  }
+  if (!dev_status) {
+    int h_status = 0;
+    TFS_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TFS_CUDA(cudaStreamSynchronize(st));
+    TFS_CHECK(h_status == 0, TFS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", h_status);
+  }
   return TFS_OK;
 }
 

@@ -74,32 +74,38 @@ struct tfs_basis {
   double* U = nullptr;      // device [K][n_seg]
   std::vector<double> sigma, cmin, cmax;
   std::mutex mu;            // guards the cached segment parameters
-  tfs::SegParams sp;
+  std::vector<tfs::SegParams*> sps;  // one per (T_sft, slot count) used so far; freed with the basis
 };
 
 namespace tfs {
 
 inline int esize_of(int dtype) { return dtype == TFS_F32 ? 4 : (dtype == TFS_F8E4M3 ? 1 : 2); }
 
-// Cached FP32 filter parameters of a basis for a given T_sft (built on first use).
-int get_segparams(tfs_basis* b, double T, cudaStream_t st, SegParams** out);
+// Cached FP32 filter parameters of a basis for a given T_sft, with at least kp_min coefficient
+// slots (built on first use; rebuilt for another T_sft or a wider slot count).
+int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams** out);
+int pick_kp(int K);
 
 // ---------------------------------------------------------------- kernels (host launchers)
-struct EvalLaunch {
+struct EvalJob {          // one dataset's part of a statistic launch
   const tfs_table* table;
   const tfs_basis* basis;
-  const SegParams* sp;
-  const double* coeffs;   // device
-  const double* f_ref;    // device or null
+  const SegParams* sp;    // built with the launch's coefficient slot count
+  const double* coeffs;   // device [N][K]
+  const double* f_ref;    // device [N] or null
   int64_t N;
   int m;
-  float* stat;            // device
+  float* stat;            // device [N]
+  int* bins_out = nullptr;  // device [N][n_seg] or null: the bin of every pair (verification only)
+};
+struct EvalLaunch {
+  const EvalJob* jobs;    // host array
+  int n_jobs;
   unsigned long long* tie_count;  // device
   int64_t* tie_track;     // device [tie_cap]
   int* tie_seg;
   int tie_cap;
   int* status;            // device
-  int* bins_out = nullptr;  // device [N][n_seg] or null: the bin of every pair (verification only)
   unsigned long long* dbg = nullptr;  // self-check record (TFS_DEBUG_CHECKS builds)
 };
 struct EvalTuning {       // launch shape; zeros select defaults
@@ -108,6 +114,7 @@ struct EvalTuning {       // launch shape; zeros select defaults
   int cap = 0;            // staged band capacity per row (elements)
   int qcap = 0;
 };
+constexpr int kMaxJobs = 64;  // jobs per statistic launch (larger batches are split)
 int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st);
 
 // dtype-specific launchers (one translation unit each)

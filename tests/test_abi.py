@@ -63,6 +63,19 @@ def test_host_validation_without_device(L):
     assert b"prime factors" in L.tfs_last_error()
     assert L.tfs_build_basis(ctypes.cast(x, P), 8, 8, 40, 0.0, 0, None, ctypes.byref(out)) == -1
     assert L.tfs_basis_from_host(ctypes.cast(x, P), 0, 8, ctypes.byref(out)) == -1
+    # batched evaluation: job list and per-job handles are checked before any CUDA call
+    assert L.tfs_eval_batch(None, 1, None, None) == -1
+    jobs = (_lib.TfsJob * 2)()
+    assert L.tfs_eval_batch(jobs, 0, None, None) == -1
+    assert L.tfs_eval_batch(jobs, 5000, None, None) == -1
+    assert L.tfs_eval_batch(jobs, 2, None, None) == -1
+    assert b"job 0" in L.tfs_last_error()
+
+
+def test_job_struct_matches_the_header():
+    """struct tfs_job: 8-byte fields except m and topk (int32 each), no padding."""
+    assert ctypes.sizeof(_lib.TfsJob) == 9 * 8
+    assert _lib.TfsJob.m.offset == 40 and _lib.TfsJob.topk.offset == 44 and _lib.TfsJob.stat.offset == 48
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

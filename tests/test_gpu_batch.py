@@ -1,0 +1,203 @@
+"""Batched evaluation (tfs_eval_batch): many datasets of different shapes in one
+persistent launch per table dtype.
+
+Tiles never straddle jobs, so a job's statistic and top-k are bit-identical to
+tfs_eval_stat on the same job alone whenever the launch runs it with the same
+tracks per thread (set by the widest basis of its dtype group: K <= 6, 7-8,
+9-16, 17-32); otherwise the FP32 filter's warp-uniform decision limit and the
+tile's staged band move a few pairs between the FP32 sum and the FP64 fix-up
+sum, and the two results agree within FP32 rounding (relative 1e-5, the
+parity tolerance).  Each job is also checked against the FP64 oracle on the
+same stored table.  The CUDA-graph test captures the call once and replays it
+on new coefficients: a replay equals an uncaptured call bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.tfstat_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_20891_gb300 import build as B
+
+    B.build()
+    import paper_2510_20891_gb300 as pkg
+
+    return pkg
+
+
+def _dataset(T, rng, n_seg, n_bin, Tsft, dtype, K):
+    """Random chi^2_2-like power table and an orthonormal basis [K][n_seg]."""
+    P = rng.exponential(2.0, size=(n_seg, n_bin))
+    P[:, 0] = 0.0
+    table = T.table_from_power(P, Tsft, dtype)
+    U = np.linalg.qr(rng.standard_normal((n_seg, K)))[0].T.copy()
+    return table, T.basis_from_host(U), U
+
+
+def _tracks(rng, N, K, n_seg, n_bin, Tsft, n_ties=0):
+    """f_ref across the band (a few tracks leave the table), coefficients spreading
+    each track over ~5% of the bins; the first n_ties tracks sit exactly on a
+    half-integer x in every segment (c = 0, Tsft a power of two)."""
+    f_ref = rng.uniform(-0.02, 1.02, N) * n_bin / Tsft
+    scale = 0.05 * n_bin / Tsft * math.sqrt(n_seg) / math.sqrt(K)
+    c = rng.uniform(-1.0, 1.0, (N, K)) * scale
+    for t in range(min(n_ties, N)):
+        c[t] = 0.0
+        f_ref[t] = (rng.integers(1, n_bin - 1) + 0.5) / Tsft
+    return c, f_ref
+
+
+SPECS = [
+    # dtype,  n_seg, n_bin,  Tsft,     K,  N,     m, topk, ties
+    ("f32", 17, 300, 4096.0, 3, 5000, 1, 10, 5),
+    ("f32", 365, 2049, 86400.0, 6, 40000, 0, 0, 0),
+    ("bf16", 64, 1001, 1.0e4, 4, 777, 2, 5, 0),
+    ("f32", 100, 500, 2.0e4, 8, 0, 1, 3, 0),
+    ("f16", 33, 8641, 5.0e4, 2, 1, 7, 1, 0),
+    ("f8e4m3", 50, 700, 1.0e5, 13, 3000, 1, 1024, 0),
+    ("f32", 40, 400, 8192.0, 20, 2000, 3, 7, 3),
+    ("f32", 2500, 300, 1024.0, 3, 3000, 1, 0, 2),
+    ("bf16", 7, 64, 512.0, 1, 10000, 0, 16, 4),
+]
+
+
+def _make_jobs(T, torch, specs, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for (dtype, n_seg, n_bin, Tsft, K, N, m, topk, ties) in specs:
+        table, basis, U = _dataset(T, rng, n_seg, n_bin, Tsft, dtype, K)
+        c, f = _tracks(rng, N, K, n_seg, n_bin, Tsft, ties)
+        out.append(dict(table=table, basis=basis, U=U, c=c, f=f, m=m, topk=topk, Tsft=Tsft,
+                        dc=torch.tensor(c.reshape(N, K), device="cuda"),
+                        df=torch.tensor(f, device="cuda")))
+    return out
+
+
+def _alone(T, torch, d):
+    r = T.eval_stat(d["table"], d["basis"], d["dc"], d["df"], m=d["m"], topk=d["topk"])
+    torch.cuda.synchronize()
+    return r
+
+
+def _batch(T, torch, data, dev_status=None):
+    jobs = [T.Job(d["table"], d["basis"], d["dc"], d["df"], m=d["m"], topk=d["topk"],
+                  stat=torch.full((d["dc"].shape[0],), float("nan"), device="cuda")) for d in data]
+    T.eval_batch(jobs, dev_status=dev_status)
+    torch.cuda.synchronize()
+    return jobs
+
+
+def _tile_class(K):
+    return 16 if K <= 6 else (12 if K <= 8 else (8 if K <= 16 else 2))
+
+
+def _launch_class(data, d):
+    """Tracks per thread of the launch that runs job d (the widest basis among its dtype)."""
+    dt = d["table"].dtype
+    return _tile_class(max(e["U"].shape[0] for e in data if e["table"].dtype == dt and e["c"].shape[0] > 0))
+
+
+def _same(torch, job, alone, exact=True):
+    a = alone.stat.cpu().numpy()
+    b = job.stat.cpu().numpy()
+    if exact:
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), np.flatnonzero(a != b)[:5]
+        if job.topk:
+            assert np.array_equal(alone.top_idx.cpu().numpy(), job.top_idx.cpu().numpy())
+            assert np.array_equal(alone.top_val.cpu().numpy().view(np.uint32),
+                                  job.top_val.cpu().numpy().view(np.uint32))
+    else:
+        assert O.stat_relative_error(b.astype(np.float64), a.astype(np.float64)) <= 1e-5
+    if job.topk and b.size:
+        ref_idx, _ = O.topk(b.astype(np.float64), job.topk)
+        assert np.array_equal(job.top_idx.cpu().numpy(), ref_idx)
+
+
+def _check_vs_alone(T, torch, data, jobs):
+    n_exact = 0
+    for d, j in zip(data, jobs):
+        exact = _launch_class(data, d) == _tile_class(d["U"].shape[0]) if d["c"].shape[0] else True
+        n_exact += exact
+        _same(torch, j, _alone(T, torch, d), exact)
+    return n_exact
+
+
+def test_batch_equals_each_job_alone_and_the_oracle(T):
+    torch = pytest.importorskip("torch")
+    data = _make_jobs(T, torch, SPECS, seed=5)
+    jobs = _batch(T, torch, data)
+    assert _check_vs_alone(T, torch, data, jobs) >= 4  # bf16, f16, f8 jobs and the empty one
+    for d, j in zip(data, jobs):
+        if d["c"].shape[0] == 0:
+            continue
+        Pq, _ = d["table"].to_host()
+        S, idx, val, _ = O.eval_stat(Pq, d["U"], d["c"], d["f"], d["Tsft"], d["m"], d["topk"])
+        got = j.stat.cpu().numpy().astype(np.float64)
+        assert O.stat_relative_error(got, S) <= 1e-5
+
+
+def test_batch_larger_than_one_launch(T):
+    """70 jobs: more than one launch's 64, mixed dtypes."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    specs = []
+    for i in range(70):
+        dt = ["f32", "bf16", "f16"][i % 3]
+        specs.append((dt, int(rng.integers(8, 90)), int(rng.integers(40, 900)), float(2 ** rng.integers(8, 14)),
+                      int(rng.integers(1, 9)), int(rng.integers(0, 3000)), int(rng.integers(0, 3)),
+                      int(rng.integers(0, 4)), 1))
+    data = _make_jobs(T, torch, specs, seed=10)
+    jobs = _batch(T, torch, data)
+    _check_vs_alone(T, torch, data, jobs)
+    again = _batch(T, torch, data)  # the same call twice: deterministic
+    for j, k in zip(jobs, again):
+        assert np.array_equal(j.stat.cpu().numpy().view(np.uint32), k.stat.cpu().numpy().view(np.uint32))
+
+
+def test_batch_in_a_cuda_graph(T):
+    """Capture once (after one uncaptured call builds the cached per-segment data), then
+    replay on new coefficients written in place: each replay equals a fresh call."""
+    torch = pytest.importorskip("torch")
+    data = _make_jobs(T, torch, SPECS[:3] + SPECS[5:7], seed=21)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    jobs = [T.Job(d["table"], d["basis"], d["dc"], d["df"], m=d["m"], topk=d["topk"]) for d in data]
+    T.eval_batch(jobs, dev_status=status)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            T.eval_batch(jobs, dev_status=status, stream=s.cuda_stream)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(22)
+    for rep in range(3):
+        for d in data:
+            N, K = d["dc"].shape
+            c, f = _tracks(rng, N, K, d["U"].shape[1], d["table"].n_bin, d["Tsft"], 2)
+            d["dc"].copy_(torch.tensor(c.reshape(N, K)))
+            d["df"].copy_(torch.tensor(f))
+        status.fill_(7)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        fresh = _batch(T, torch, data)
+        for j, k in zip(jobs, fresh):
+            _same(torch, j, _AsResult(k), exact=True)
+        _check_vs_alone(T, torch, data, jobs)
+
+
+class _AsResult:
+    """A batch Job seen through the result fields that _same reads."""
+
+    def __init__(self, job):
+        self.stat, self.top_idx, self.top_val = job.stat, job.top_idx, job.top_val
