@@ -17,7 +17,7 @@
 //     * warps 1-3 (the builders) turn each staged band into window sums
 //           Q[b] = sum_{j=-m..m} P[alpha][b+j]      (FP32, fixed order)
 //       with 16-byte vector loads and lane shuffles and signal the Q slot;
-//   two consumer warpgroups (256 threads, registers raised with setmaxnreg)
+//   three consumer warpgroups (384 threads, registers raised with setmaxnreg)
 //     per segment, each thread evaluates x = f T_SFT for its R tracks in FP32,
 //           y = (x_mid - B) + sum_k c_k D_k,alpha,    b = B + rint(y),
 //     (B = rint(x_mid), x_mid an FP64 per-track constant) and adds Q[b] with a
@@ -78,15 +78,16 @@ struct Store<TFS_F8E4M3> {
 
 constexpr int kProd = 128;            // producer warpgroup: stager warp + 3 builder warps
 constexpr int kBuild = kProd - 32;    // builder threads
-constexpr int kCons = 256;            // two consumer warpgroups
+constexpr int kCons = 384;            // three consumer warpgroups
 constexpr int kThreads = kProd + kCons;
 constexpr int kConsWarps = kCons / 32;
-constexpr int kProdRegs = 72;         // setmaxnreg targets: 128*72 + 256*216 = 384*168
-constexpr int kConsRegs = 216;
-static_assert(kProd * kProdRegs + kCons * kConsRegs <= kThreads * 168, "register split exceeds the launch");
+constexpr int kLaunchRegs = 65536 / kThreads;  // 128 registers per thread at launch
+constexpr int kProdRegs = 56;         // setmaxnreg targets: 128*56 + 384*152 = 512*128
+constexpr int kConsRegs = 152;
+static_assert(kProd * kProdRegs + kCons * kConsRegs <= kThreads * kLaunchRegs, "register split exceeds the launch");
 constexpr int kNQ = 4;                // window-sum (Q) slots
 constexpr int kNP = 4;                // staging slots
-constexpr int kQT = 32;               // fix-up queue entries per consumer thread
+constexpr int kQT = 24;               // fix-up queue entries per consumer thread
 constexpr int kPadL = 16;             // zero elements before the staged band in a staging slot
 constexpr int kSegTile = 32;          // FP32 partial sums are flushed every kSegTile segments
 constexpr int kBandCap = 2048;        // segments whose bands are precomputed per tile
@@ -106,7 +107,7 @@ struct JobDesc {
   double T;
   int n_seg, n_bin, row_stride, m, K, alpha_mid;
   int seg_resident;     // segp (and scales) copied to shared memory for this job's tiles
-  int pad;
+  int tile_tracks;      // tracks per tile (<= consumer threads * R); the last tile may hold fewer
 };
 
 template <int MJ>
@@ -589,7 +590,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       const int j = job_of(a, tile);
       const JobDesc& J = a.jobs[j];
       const int n_seg = J.n_seg, m = J.m, K = J.K;
-      const long long tile0 = (long long)(tile - a.tile_start[j]) * (kCons * R);
+      const long long tile0 = (long long)(tile - a.tile_start[j]) * J.tile_tracks;
+      const long long tend = min(J.N, tile0 + J.tile_tracks);
       const bool live = !__any_sync(0xffffffffu, flags[0] != 0);  // warp-uniform
       // -------------------------------------------------------------- tile prologue
       float c[R][KP];
@@ -617,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           corr[r * kCons + ctid] = 0.f;
           tot[r * kCons + ctid] = 0.f;
           const long long t = tile0 + ctid + r * kCons;
-          if (t < J.N) {
+          if (t < tend) {
             const double fr = J.f_ref ? J.f_ref[t] : 0.0;
             double f = fr;
             float A = 0.f, Um = fabsf((float)fr);
@@ -720,14 +722,15 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             if (4 * k4 + 3 < KP) d[4 * k4 + 3] = v.w;
           }
         }
-        // pass 1 (straight-line over the R tracks): slot offsets and FP32 decisions.
+        // one straight-line pass over the R tracks: slot offset, FP32 decision, masked gather.
         // off = b - qbase = B + (bits(tt) - bits(1.5 * 2^23)) - qbase; the window of b overlaps
         // the table iff 0 <= b + m < n_bin + 2m, i.e. (unsigned)(off + qbase + m) < n_bin + 2m.
+        // A pair is pending (queued for the FP64 path) when FP32 cannot decide its bin, or when
+        // its window overlaps the table but its centre lies outside the staged band.
         const int koff = -0x4B400000 - h.qbase;
         const int kin = h.qbase + m;
         const unsigned qn = (unsigned)h.qn;
-        unsigned offv[R];
-        unsigned undecided = 0u, outside = 0u;
+        unsigned pend = 0u;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           float y = y0[r];
@@ -736,34 +739,26 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
           const float dd = y - (tt - 12582912.0f);
           const unsigned off = (unsigned)(B[r] + __float_as_int(tt) + koff);
-          offv[r] = off;
-          if (!(fabsf(dd) < wlim)) undecided |= 1u << r;
-          if (off >= qn && (unsigned)((int)off + kin) < nin) outside |= 1u << r;
-        }
-        const unsigned pend = undecided | outside;
-        // pass 2 (straight-line): one shared load per track, masked; the address is always valid
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const unsigned off = offv[r];
-          const bool use = off < qn && !((pend >> r) & 1u);
-          const float v = q[use ? off : 0u];
+          const bool und = !(fabsf(dd) < wlim);
+          const bool inq = off < qn;
+          const bool outside = !inq && (unsigned)((int)off + kin) < nin;
+          pend |= (unsigned)(und || outside) << r;
+          const bool use = inq && !und;
+          const float v = q[use ? off : 0u];  // the address is always valid
           acc[r] += use ? v : 0.f;
+          if (BINS) {
+            const int b = (int)off + h.qbase;
+            const long long t = tile0 + ctid + r * kCons;
+            if (t < tend && !(und || outside))
+              J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+          }
         }
-        // pass 3 (rare): queue the undecided pairs and those whose window lies outside the band
+        // (rare) queue the pending pairs
         if (pend) {
           for (unsigned mk = pend; mk; mk &= mk - 1u) {
             const int r = __ffs(mk) - 1;
             queue[nq * kCons + ctid] = ((uint32_t)sg << 5) | (uint32_t)r;
             ++nq;
-          }
-        }
-        if (BINS) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int b = (int)offv[r] + h.qbase;
-            const long long t = tile0 + ctid + r * kCons;
-            if (t < J.N && !((pend >> r) & 1u))
-              J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
           }
         }
         if ((sg % kSegTile) == kSegTile - 1) {
@@ -786,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const long long t = tile0 + ctid + r * kCons;
-          if (t < J.N) J.stat[t] = (tot[r * kCons + ctid] + acc[r]) + corr[r * kCons + ctid];
+          if (t < tend) J.stat[t] = (tot[r * kCons + ctid] + acc[r]) + corr[r * kCons + ctid];
         }
       }
     }
@@ -830,7 +825,7 @@ inline int sm_count() {
   return n;
 }
 
-inline int r_of_kp(int KP) { return KP <= 6 ? 16 : (KP <= 8 ? 12 : (KP <= 16 ? 8 : 2)); }
+inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 8 : (KP <= 16 ? 6 : 2)); }
 
 template <int DT, int MJ>
 int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
@@ -879,8 +874,18 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     D.m = E.m;
     D.K = E.basis->K;
     D.alpha_mid = E.sp->alpha_mid;
+    // tiles of equal size; a single job gets a whole number of rounds over the SMs (or, when
+    // small, one tile per SM), so that no round runs on a few SMs alone
+    long long ntj = (E.N + tile - 1) / tile;
+    if (L.n_jobs == 1 && E.N > 0) {
+      const long long sms = sm_count();
+      if (ntj < sms) ntj = std::min<long long>(sms, (E.N + 255) / 256);
+      else ntj = (ntj + sms - 1) / sms * sms;
+    }
+    const long long tt = ntj > 0 ? (E.N + ntj - 1) / ntj : tile;
+    D.tile_tracks = (int)tt;
     a.tile_start[i] = (int)nt;
-    nt += (E.N + tile - 1) / tile;
+    nt += tt > 0 ? (E.N + tt - 1) / tt : 0;
     row_max = std::max(row_max, (int)tb->row_stride);
     seg_max = std::max(seg_max, (int)tb->n_seg);
     bins = bins || E.bins_out != nullptr;
@@ -941,11 +946,11 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     }                                                                                   \
     return launch_one<DT, KPV, RV, false, MJ>(a, grid, smem, st);                        \
   }
-  TFS_LAUNCH_KP(2, 16)
-  TFS_LAUNCH_KP(4, 16)
-  TFS_LAUNCH_KP(6, 16)
-  TFS_LAUNCH_KP(8, 12)
-  TFS_LAUNCH_KP(16, 8)
+  TFS_LAUNCH_KP(2, 12)
+  TFS_LAUNCH_KP(4, 12)
+  TFS_LAUNCH_KP(6, 12)
+  TFS_LAUNCH_KP(8, 8)
+  TFS_LAUNCH_KP(16, 6)
   TFS_LAUNCH_KP(32, 2)
 #undef TFS_LAUNCH_KP
   (void)R;
