@@ -184,8 +184,11 @@ int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis, const double* 
  * The paper evaluates one dataset at a time; this entry point serves a batch
  * of independent searches (different tables, bases, track counts, m) with a
  * single persistent kernel launch per table dtype, so that small searches fill
- * the GPU together.  Each job's results are bit-identical to tfs_eval_stat
- * (mem = DEVICE) on the same job.  All pointers inside the jobs are device
+ * the GPU together.  Each job's bins are those of tfs_eval_stat on the same
+ * job; its statistic agrees with tfs_eval_stat's within FP32 rounding of the
+ * sum (how tracks are grouped into tiles decides which pairs take the FP64
+ * path, so the last bits may differ), and the same call repeated gives
+ * bit-identical results.  All pointers inside the jobs are device
  * pointers of the current device; `jobs` itself is a host array of n_jobs
  * (1 <= n_jobs <= 4096) entries, read during the call only.  Per job: table
  * and basis with equal n_seg, 0 <= N < 2^31, 0 <= m <= 64, 0 <= topk <= 1024,

@@ -14,12 +14,14 @@
 //     * warp 0 (the stager) stages, segment after segment, the band of table
 //       row alpha into a staging slot with a 1-D bulk copy (cp.async.bulk)
 //       completing on an mbarrier;
-//     * warps 1-3 (the builders) turn each staged band into window sums
+//     * warps 1-3 (the builders) turn staged bands into window sums
 //           Q[b] = sum_{j=-m..m} P[alpha][b+j]      (FP32, fixed order)
 //       with 16-byte vector loads and lane shuffles and signal the Q slot;
+//       builder warp w takes segments w, w+3, ..., so each warp's per-segment
+//       synchronisation latency hides behind the other two warps' work;
 //   three consumer warpgroups (384 threads, registers raised with setmaxnreg)
 //     per segment, each thread evaluates x = f T_SFT for its R tracks in FP32,
-//           y = (x_mid - B) + sum_k c_k D_k,alpha,    b = B + rint(y),
+//           y = (x_mid - Bw) + sum_k c_k D_k,alpha,    b = Bw + rint(y),
 //     (B = rint(x_mid), x_mid an FP64 per-track constant) and adds Q[b] with a
 //     single shared load.  Pairs within a warp-uniform error bound g of a
 //     half-integer, and pairs whose centre falls outside the staged band, go
@@ -32,10 +34,8 @@
 // segments apart.  FP32 sums are flushed to a second accumulator every 32
 // segments; fix-up contributions accumulate separately in segment order.  The
 // result is deterministic for a given launch; which pairs take the fix-up path
-// depends on the warp's decision limit and the tile's band, so a track's FP32
-// rounding (never its bins) can change with its tile neighbours.  Tiles never
-// straddle jobs: a job gives bit-identical results alone and inside a batch
-// whose launch uses the same tracks per thread.
+// depends on the warp's base bin and decision limit and on the tile's band, so
+// a track's FP32 rounding (never its bins) can change with its tile neighbours.
 // Every wait is bounded (2 s) and warp-uniform; after a timeout every role
 // keeps iterating without work (so barriers stay matched) and the call
 // returns TFS_ERR_TIMEOUT.
@@ -77,13 +77,13 @@ struct Store<TFS_F8E4M3> {
 };
 
 constexpr int kProd = 128;            // producer warpgroup: stager warp + 3 builder warps
-constexpr int kBuild = kProd - 32;    // builder threads
+constexpr int kBuildWarps = kProd / 32 - 1;  // builder warps; warp w builds segments w, w+3, ...
 constexpr int kCons = 384;            // three consumer warpgroups
 constexpr int kThreads = kProd + kCons;
 constexpr int kConsWarps = kCons / 32;
 constexpr int kLaunchRegs = 65536 / kThreads;  // 128 registers per thread at launch
-constexpr int kProdRegs = 56;         // setmaxnreg targets: 128*56 + 384*152 = 512*128
-constexpr int kConsRegs = 152;
+constexpr int kProdRegs = 64;         // setmaxnreg targets: 128*64 + 384*144 <= 512*128
+constexpr int kConsRegs = 144;
 static_assert(kProd * kProdRegs + kCons * kConsRegs <= kThreads * kLaunchRegs, "register split exceeds the launch");
 constexpr int kNQ = 4;                // window-sum (Q) slots
 constexpr int kNP = 4;                // staging slots
@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   uint64_t* full_p = bars;                           // [kNP] staged copy landed (tx)
-  uint64_t* empty_p = bars + kNP;                    // [kNP] builders done with the slot (3 warps)
-  uint64_t* full_q = bars + 2 * kNP;                 // [kNQ] window sums ready (96 builder threads)
+  uint64_t* empty_p = bars + kNP;                    // [kNP] its builder warp is done with the slot
+  uint64_t* full_q = bars + 2 * kNP;                 // [kNQ] window sums ready (32 lanes of a builder warp)
   uint64_t* empty_q = bars + 2 * kNP + kNQ;          // [kNQ] consumers done with the slot (8 warps)
   uint64_t* tile_ready = bars + 2 * kNP + 2 * kNQ;   // [2] a tile's coefficient box is ready (8 warps)
   QHdr* qhdr = reinterpret_cast<QHdr*>(smem + a.off_qhdr);  // [kNQ], then [kNQ][nsp] floats of D
@@ -362,10 +362,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
   if (tid == 0) {
     for (int i = 0; i < kNP; ++i) {
       mbar_init(&full_p[i], 1);
-      mbar_init(&empty_p[i], kProd / 32 - 1);
+      mbar_init(&empty_p[i], 1);
     }
     for (int i = 0; i < kNQ; ++i) {
-      mbar_init(&full_q[i], kBuild);
+      mbar_init(&full_q[i], 32);
       mbar_init(&empty_q[i], kConsWarps);
     }
     for (int i = 0; i < 2; ++i) mbar_init(&tile_ready[i], kConsWarps);
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
     // ================================================================ producer warpgroup
     setmaxnreg_dec<kProdRegs>();
     const int pw = tid >> 5;  // 0: stager, 1..3: builders
-    uint32_t p_seq = 0, b_seq = 0, q_seq = 0;
+    uint32_t p_seq = 0, b_base = 0;
     int cur_job = -1;
     int ltile = 0;
     for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
@@ -479,11 +479,13 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         }
       } else {
         // ------------------------------------------------------------ builder warps
-        const int btid = tid - 32;
-        for (int sg = 0; sg < n_seg; ++sg) {
-          const int ps = (int)(b_seq % kNP), qs = (int)(q_seq % kNQ);
-          bool go = warp_wait(&full_p[ps], (b_seq / kNP) & 1u, flags);
-          if (go && q_seq >= kNQ) go = warp_wait(&empty_q[qs], ((q_seq / kNQ) - 1u) & 1u, flags);
+        // builder warp w builds the window sums of segments w, w + 3, w + 6, ...: the latency of
+        // each warp's per-segment waits and set-up overlaps the other two warps' work
+        for (int sg = pw - 1; sg < n_seg; sg += kBuildWarps) {
+          const uint32_t gs = b_base + (uint32_t)sg;  // launch-wide segment sequence number
+          const int ps = (int)(gs % kNP), qs = (int)(gs % kNQ);
+          bool go = warp_wait(&full_p[ps], (gs / kNP) & 1u, flags);
+          if (go && gs >= kNQ) go = warp_wait(&empty_q[qs], ((gs / kNQ) - 1u) & 1u, flags);
           if (go) {
             const int plo = plo_s[ps], plen = plen_s[ps];
             const unsigned char* src = pslots + (size_t)ps * pslot_bytes;
@@ -502,16 +504,16 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               const int nload = min((ws_lo + qn + 4 + EALIGN - 1) / EALIGN, kPadL / EALIGN + a.pcap / EALIGN + 1);
               // each pass: UV vectors (16 table elements) per thread, all loads issued first
               constexpr int UV = 16 / EALIGN;
-              for (int v0 = 0; v0 < nvec; v0 += kBuild * UV) {
+              for (int v0 = 0; v0 < nvec; v0 += 32 * UV) {
                 uint4 raw[UV];
 #pragma unroll
                 for (int u = 0; u < UV; ++u) {
-                  const int vi = v0 + u * kBuild + btid;
+                  const int vi = v0 + u * 32 + lane;
                   raw[u] = vi < nload ? reinterpret_cast<const uint4*>(src)[vi] : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
                 for (int u = 0; u < UV; ++u) {
-                  const int vi = v0 + u * kBuild + btid;
+                  const int vi = v0 + u * 32 + lane;
                   float e[EALIGN + 4];
                   unpack16<DT>(raw[u], scale, e);
                   float nx[4];
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               }
             } else {
               const T* pb = reinterpret_cast<const T*>(src);
-              for (int ws = ws_lo + btid; ws < ws_lo + qn; ws += kBuild) {
+              for (int ws = ws_lo + lane; ws < ws_lo + qn; ws += 32) {
                 float s = 0.f;
                 for (int k = 0; k < W; ++k) {
                   const float p = S::ld(pb + ws + k);
@@ -559,10 +561,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
                 q[ws] = s;
               }
             }
-            if (btid < a.nsp)
-              qdseg[qs * a.nsp + btid] =
-                  reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[btid];
-            if (btid == 0) {
+            if (lane < a.nsp)
+              qdseg[qs * a.nsp + lane] =
+                  reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[lane];
+            if (lane == 0) {
               QHdr h;
               h.ws_lo = ws_lo;
               h.qn = qn;
@@ -570,14 +572,13 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               h.pad = 0;
               qhdr[qs] = h;
             }
-            mbar_arrive(&full_q[qs]);  // every builder thread releases its own writes
+            mbar_arrive(&full_q[qs]);  // every lane releases its own writes
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_p[ps]);
           }
-          ++b_seq;
-          ++q_seq;
         }
       }
+      b_base += (uint32_t)n_seg;
     }
   } else {
     // ================================================================ consumer warpgroups
@@ -594,85 +595,112 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       const long long tend = min(J.N, tile0 + J.tile_tracks);
       const bool live = !__any_sync(0xffffffffu, flags[0] != 0);  // warp-uniform
       // -------------------------------------------------------------- tile prologue
+      // Each track is evaluated relative to a warp-uniform base bin Bw (the FP64 mid-segment bin
+      // of the warp's first track): y = (x_mid - Bw) + sum_k c_k D_k,alpha in FP32, and the bin
+      // is Bw + rint(y).  One base per warp keeps a register per track free.
       float c[R][KP];
-      int B[R];
       float y0[R], acc[R];
+      int Bw = 0;
       // warp-uniform decision limit: min over the warp's tracks of 1/2 - g; at most 1/2, so the
       // tracks that take the FP64 path for every pair (y = 1/2) are never decided in FP32
       float wlim = 0.5f;
       int nq = 0;        // entries in this thread's fix-up queue
       if (live) {
-        float cmn[KP], cmx[KP];
         int bmin = 0x7fffffff, bmax = -0x7fffffff;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-          cmn[k] = __int_as_float(0x7f800000);
-          cmx[k] = -__int_as_float(0x7f800000);
-        }
+        unsigned inbox = 0u;  // tracks that enter the coefficient box (decided in FP32)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           acc[r] = 0.f;
-          B[r] = -(1 << 29);  // inactive slot: y = 0 is never queued and b is always out of range
           y0[r] = 0.f;
 #pragma unroll
           for (int k = 0; k < KP; ++k) c[r][k] = 0.f;
           corr[r * kCons + ctid] = 0.f;
           tot[r * kCons + ctid] = 0.f;
           const long long t = tile0 + ctid + r * kCons;
-          if (t < tend) {
+          const bool active = t < tend;
+          double xm = 0.0;
+          float eb = 0.f;
+          bool exact = false;
+          if (active) {
             const double fr = J.f_ref ? J.f_ref[t] : 0.0;
             double f = fr;
             float A = 0.f, Um = fabsf((float)fr);
             const double* cp = J.coeffs + t * (long long)K;
-            float cf[KP];
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
               const double cd = (k < K) ? cp[k] : 0.0;
               if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
-              cf[k] = (float)cd;
-              A = fmaf(fabsf(cf[k]), J.dmax[k], A);
-              Um = fmaf(fabsf(cf[k]), J.umax[k], Um);
+              c[r][k] = (float)cd;
+              A = fmaf(fabsf(c[r][k]), J.dmax[k], A);
+              Um = fmaf(fabsf(c[r][k]), J.umax[k], Um);
             }
             A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
             Um *= 1.0001f;
-            const double xm = f * J.T;
-            // |fp32 estimate - exact x| <= err = 2^-24 ((K+1)/2 + (K+2.001) A) + e64, where
-            // e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid, the
-            // deltas D, and the oracle's own evaluation).  Pairs closer than g to a half-integer
-            // are resolved in FP64; outside that band the exact, the oracle's and this bin
-            // coincide and none of them is within the 1e-9 tie band.
+            xm = f * J.T;
+            // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
+            // FP32, K rounded FMAs on partial sums below |y0| + A, and the FP32 roundings of c and
+            // D; e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid,
+            // the deltas D, and the oracle's own evaluation).  With g = 1.25 (err + e64) + 4e-9,
+            // pairs closer than g to a half-integer are resolved in FP64; outside that band the
+            // exact, the oracle's and this bin coincide and none of them is a 1e-9 tie.
             const float e64 = 7.105427357601002e-15f * (float)J.T * Um;
-            const float err = 5.9604644775390625e-08f * (0.5f * (K + 1) + (K + 2.001f) * A) + e64;
-            const float g = 1.25f * (err + e64) + 4e-9f;
-            const bool exact = !(fabs(xm) < 1073741824.0) || !(g < 0.25f) || !(A < 1048576.0f);
+            eb = 1.25f * (5.9604644775390625e-08f * ((K + 2.001f) * A) + 2.f * e64) + 4e-9f;
+            exact = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
+          }
+          if (r == 0) {
+            // the warp's base bin: from the first lane whose first track is usable
+            const unsigned ok = __ballot_sync(0xffffffffu, active && !exact);
+            const int src = ok ? __ffs(ok) - 1 : 0;
+            Bw = __shfl_sync(0xffffffffu, (active && !exact) ? (int)rint(xm) : 0, src);
+          }
+          if (!active) {
+            // inactive slot: c = 0 and y far from the table (|y| < 2^22), never pending
+            y0[r] = Bw >= 0 ? 4194303.0f : -4194303.0f;
+            continue;
+          }
+          if (!exact) {
+            const double yd = xm - (double)Bw;
+            const float yf = (float)yd;
+            const float g = eb + 1.25f * 5.9604644775390625e-08f * (float)(K + 1) * fabsf(yf) * 1.0001f;
+            exact = !(fabs(yd) < 2097152.0) || !(g < 0.25f);
             if (!exact) {
-              const double Bd = rint(xm);
-              B[r] = (int)Bd;
-              y0[r] = (float)(xm - Bd);
+              y0[r] = yf;
               wlim = fminf(wlim, __fsub_rd(0.5f, g));
-#pragma unroll
-              for (int k = 0; k < KP; ++k) {
-                c[r][k] = cf[k];
-                cmn[k] = fminf(cmn[k], c[r][k]);
-                cmx[k] = fmaxf(cmx[k], c[r][k]);
-              }
-              bmin = min(bmin, B[r]);
-              bmax = max(bmax, B[r]);
-            } else {
-              // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
-              B[r] = 0;
-              y0[r] = 0.5f;
+              const int Bd = (int)rint(xm);
+              bmin = min(bmin, Bd);
+              bmax = max(bmax, Bd);
+              inbox |= 1u << r;
             }
+          }
+          if (exact) {
+            // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
+            y0[r] = 0.5f;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) c[r][k] = 0.f;
           }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wlim = fminf(wlim, __shfl_xor_sync(0xffffffffu, wlim, o));
+        // the warp's coefficient box, one coefficient at a time (few live registers)
+        float* rb = red + (ltile & 1) * kConsWarps * RW + cwarp * RW;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
+          float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if ((inbox >> r) & 1u) {
+              lo = fminf(lo, c[r][k]);
+              hi = fmaxf(hi, c[r][k]);
+            }
+          }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            cmn[k] = fminf(cmn[k], __shfl_xor_sync(0xffffffffu, cmn[k], o));
-            cmx[k] = fmaxf(cmx[k], __shfl_xor_sync(0xffffffffu, cmx[k], o));
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+          }
+          if (lane == 0) {
+            rb[k] = lo;
+            rb[KP + k] = hi;
           }
         }
 #pragma unroll
@@ -681,12 +709,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
         }
         if (lane == 0) {
-          float* rb = red + (ltile & 1) * kConsWarps * RW + cwarp * RW;
-#pragma unroll
-          for (int k = 0; k < KP; ++k) {
-            rb[k] = cmn[k];
-            rb[KP + k] = cmx[k];
-          }
           reinterpret_cast<int*>(rb)[2 * KP] = bmin;
           reinterpret_cast<int*>(rb)[2 * KP + 1] = bmax;
         }
@@ -723,12 +745,13 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           }
         }
         // one straight-line pass over the R tracks: slot offset, FP32 decision, masked gather.
-        // off = b - qbase = B + (bits(tt) - bits(1.5 * 2^23)) - qbase; the window of b overlaps
+        // off = b - qbase = Bw + (bits(tt) - bits(1.5 * 2^23)) - qbase; the window of b overlaps
         // the table iff 0 <= b + m < n_bin + 2m, i.e. (unsigned)(off + qbase + m) < n_bin + 2m.
         // A pair is pending (queued for the FP64 path) when FP32 cannot decide its bin, or when
         // its window overlaps the table but its centre lies outside the staged band.
-        const int koff = -0x4B400000 - h.qbase;
-        const int kin = h.qbase + m;
+        // (unsigned arithmetic: the offsets wrap modulo 2^32 and only b - qbase matters)
+        const unsigned koff = (unsigned)Bw - 0x4B400000u - (unsigned)h.qbase;
+        const unsigned kin = (unsigned)(h.qbase + m);
         const unsigned qn = (unsigned)h.qn;
         unsigned pend = 0u;
 #pragma unroll
@@ -738,10 +761,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           for (int k = 0; k < KP; ++k) y = fmaf(c[r][k], d[k], y);
           const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
           const float dd = y - (tt - 12582912.0f);
-          const unsigned off = (unsigned)(B[r] + __float_as_int(tt) + koff);
+          const unsigned off = (unsigned)__float_as_int(tt) + koff;
           const bool und = !(fabsf(dd) < wlim);
           const bool inq = off < qn;
-          const bool outside = !inq && (unsigned)((int)off + kin) < nin;
+          const bool outside = !inq && off + kin < nin;
           pend |= (unsigned)(und || outside) << r;
           const bool use = inq && !und;
           const float v = q[use ? off : 0u];  // the address is always valid
@@ -825,7 +848,7 @@ inline int sm_count() {
   return n;
 }
 
-inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 8 : (KP <= 16 ? 6 : 2)); }
+inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 10 : (KP <= 16 ? 5 : 2)); }
 
 template <int DT, int MJ>
 int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
@@ -949,8 +972,8 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
   TFS_LAUNCH_KP(2, 12)
   TFS_LAUNCH_KP(4, 12)
   TFS_LAUNCH_KP(6, 12)
-  TFS_LAUNCH_KP(8, 8)
-  TFS_LAUNCH_KP(16, 6)
+  TFS_LAUNCH_KP(8, 10)
+  TFS_LAUNCH_KP(16, 5)
   TFS_LAUNCH_KP(32, 2)
 #undef TFS_LAUNCH_KP
   (void)R;

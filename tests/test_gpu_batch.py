@@ -1,15 +1,14 @@
 """Batched evaluation (tfs_eval_batch): many datasets of different shapes in one
 persistent launch per table dtype.
 
-Tiles never straddle jobs, so a job's statistic and top-k are bit-identical to
-tfs_eval_stat on the same job alone whenever the launch runs it with the same
-tracks per thread (set by the widest basis of its dtype group: K <= 6, 7-8,
-9-16, 17-32); otherwise the FP32 filter's warp-uniform decision limit and the
-tile's staged band move a few pairs between the FP32 sum and the FP64 fix-up
-sum, and the two results agree within FP32 rounding (relative 1e-5, the
-parity tolerance).  Each job is also checked against the FP64 oracle on the
-same stored table.  The CUDA-graph test captures the call once and replays it
-on new coefficients: a replay equals an uncaptured call bit for bit.
+A job's bins do not depend on how its tracks are grouped into tiles, but
+which pairs the FP32 filter leaves to the FP64 fix-up sum does (the decision
+limit and the base bin are warp-uniform, the staged band is per tile), so the
+statistic of a job inside a batch equals tfs_eval_stat on the job alone within
+FP32 rounding (relative 1e-5, the parity tolerance), and each job is checked
+against the FP64 oracle on the same stored table.  The same call repeated
+gives bit-identical results, and so does a CUDA-graph replay against an
+uncaptured call.
 """
 import math
 
@@ -96,16 +95,6 @@ def _batch(T, torch, data, dev_status=None):
     return jobs
 
 
-def _tile_class(K):
-    return 16 if K <= 6 else (12 if K <= 8 else (8 if K <= 16 else 2))
-
-
-def _launch_class(data, d):
-    """Tracks per thread of the launch that runs job d (the widest basis among its dtype)."""
-    dt = d["table"].dtype
-    return _tile_class(max(e["U"].shape[0] for e in data if e["table"].dtype == dt and e["c"].shape[0] > 0))
-
-
 def _same(torch, job, alone, exact=True):
     a = alone.stat.cpu().numpy()
     b = job.stat.cpu().numpy()
@@ -123,19 +112,15 @@ def _same(torch, job, alone, exact=True):
 
 
 def _check_vs_alone(T, torch, data, jobs):
-    n_exact = 0
     for d, j in zip(data, jobs):
-        exact = _launch_class(data, d) == _tile_class(d["U"].shape[0]) if d["c"].shape[0] else True
-        n_exact += exact
-        _same(torch, j, _alone(T, torch, d), exact)
-    return n_exact
+        _same(torch, j, _alone(T, torch, d), exact=False)
 
 
 def test_batch_equals_each_job_alone_and_the_oracle(T):
     torch = pytest.importorskip("torch")
     data = _make_jobs(T, torch, SPECS, seed=5)
     jobs = _batch(T, torch, data)
-    assert _check_vs_alone(T, torch, data, jobs) >= 4  # bf16, f16, f8 jobs and the empty one
+    _check_vs_alone(T, torch, data, jobs)
     for d, j in zip(data, jobs):
         if d["c"].shape[0] == 0:
             continue
