@@ -81,7 +81,7 @@ constexpr int kBuildWarps = kProd / 32 - 1;  // builder warps; warp w builds seg
 constexpr int kCons = 384;            // three consumer warpgroups
 constexpr int kThreads = kProd + kCons;
 constexpr int kConsWarps = kCons / 32;
-constexpr int kLaunchRegs = 65536 / kThreads;  // 128 registers per thread at launch
+constexpr int kLaunchRegs = (65536 / kThreads) & ~7;  // 128 registers per thread at launch
 constexpr int kProdRegs = 64;         // setmaxnreg targets: 128*64 + 384*144 <= 512*128
 constexpr int kConsRegs = 144;
 static_assert(kProd * kProdRegs + kCons * kConsRegs <= kThreads * kLaunchRegs, "register split exceeds the launch");
@@ -91,6 +91,7 @@ constexpr int kQT = 24;               // fix-up queue entries per consumer threa
 constexpr int kPadL = 16;             // zero elements before the staged band in a staging slot
 constexpr int kSegTile = 32;          // FP32 partial sums are flushed every kSegTile segments
 constexpr int kBandCap = 2048;        // segments whose bands are precomputed per tile
+constexpr int kTrunc = 1 << 30;       // flag in a band length: the band was cut to the slot capacity
 
 struct JobDesc {
   const void* table;
@@ -131,10 +132,10 @@ struct EvalArgs {
 };
 
 struct QHdr {
-  int qbase;  // window centre held at q[ws_lo]
-  int qn;     // valid centres from there on
-  int ws_lo;  // first valid window start in the slot
-  int pad;
+  int qbase;     // window centre held at q[ws_lo]
+  int qn;        // valid centres from there on; q[ws_lo + qn] holds 0
+  int ws_lo;     // first valid window start in the slot
+  int complete;  // every reachable centre whose window overlaps the table has its sum in Q
 };
 
 #ifdef TFS_DEBUG_CHECKS
@@ -298,6 +299,7 @@ __device__ __forceinline__ int job_of(const EvalArgs<MJ>& a, int tile) {
 // Band of staged table elements [blo, blo + blen) for segment row d of a tile whose
 // coefficient box is [lo_k, hi_k] and base bins [bm, bx] (FP32 with a margin covering
 // its rounding: the band only steers staging, bins outside it take the exact path).
+// blen carries kTrunc when the band had to be cut to pcap elements.
 template <int KP, int EALIGN>
 __device__ __forceinline__ void band_of(const float* d, const float* blo_k, const float* bhi_k, int bm, int bx,
                                         int m, int n_bin, int row_stride, int pcap, int* out_lo, int* out_len) {
@@ -319,7 +321,7 @@ __device__ __forceinline__ void band_of(const float* d, const float* blo_k, cons
       int ih = ((int)bh + EALIGN) & ~(EALIGN - 1);
       ih = min(ih, row_stride);
       blo = il;
-      blen = min(ih - il, pcap);
+      blen = ih - il > pcap ? (pcap | kTrunc) : ih - il;
     }
   }
   *out_lo = blo;
@@ -452,6 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             }
             plo_s[ps] = blo;
             plen_s[ps] = blen;
+            blen &= kTrunc - 1;
             unsigned char* dst = pslots + (size_t)ps * pslot_bytes;
             uint32_t dbytes = (uint32_t)blen * S::esize;
             {
@@ -487,14 +490,22 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           bool go = warp_wait(&full_p[ps], (gs / kNP) & 1u, flags);
           if (go && gs >= kNQ) go = warp_wait(&empty_q[qs], ((gs / kNQ) - 1u) & 1u, flags);
           if (go) {
-            const int plo = plo_s[ps], plen = plen_s[ps];
+            const int plo = plo_s[ps], plv = plen_s[ps];
+            const int plen = plv & (kTrunc - 1);
             const unsigned char* src = pslots + (size_t)ps * pslot_bytes;
-            // valid window starts (slot coordinates): wholly inside the staged band, or in the zero
-            // pad when the band starts at bin 0 (windows reaching further below bin 0 than the pad
-            // covers are left to the FP64 queue)
-            const int ws_lo = plo == 0 ? max(kPadL - m, 0) : kPadL;
-            const int ws_hi = kPadL + plen - (W - 1);
+            // Window starts (slot coordinates) with a sum in Q: inside the staged band, plus the
+            // windows that reach beyond the table, whose missing elements count as 0: into the
+            // zero pad when the band starts at bin 0 (centres down to -m if 2m <= kPadL), and past
+            // the band's end when it reaches the end of the table (centres up to n_bin - 1 + m).
+            // Elements past the band always read as 0.  The band is "complete" when every centre
+            // whose window overlaps the table and that the tile's tracks can reach has its sum in
+            // Q; then a centre outside Q always has a window wholly outside the table.
+            const bool at_end = plo + plen >= J.n_bin;
+            const int ws_lo = plo == 0 ? max(kPadL - 2 * m, 0) : kPadL;
+            const int ws_hi = kPadL + plen - (W - 1) + (at_end ? 2 * m : 0);
             const int qn = plen == 0 ? 0 : max(0, min(ws_hi, a.qcap - EALIGN) - ws_lo);
+            const bool complete = !(plv & kTrunc) && (plo > 0 || 2 * m <= kPadL) && ws_hi <= a.qcap - EALIGN;
+            const int nband = (kPadL + plen) / EALIGN;  // vectors of pad + band (plen is a multiple of EALIGN)
             float* q = qslots + (size_t)qs * a.qcap;
             const float scale = S::scaled ? sscales[sg] : 1.f;
             if (m <= 2) {
@@ -509,7 +520,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 #pragma unroll
                 for (int u = 0; u < UV; ++u) {
                   const int vi = v0 + u * 32 + lane;
-                  raw[u] = vi < nload ? reinterpret_cast<const uint4*>(src)[vi] : make_uint4(0u, 0u, 0u, 0u);
+                  raw[u] = vi < nload && vi < nband ? reinterpret_cast<const uint4*>(src)[vi]
+                                                    : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
                 for (int u = 0; u < UV; ++u) {
@@ -519,11 +531,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
                   float nx[4];
 #pragma unroll
                   for (int k = 0; k < 4; ++k) nx[k] = __shfl_down_sync(0xffffffffu, e[k], 1);
-                  if (lane == 31 && vi < nvec) {
-                    const T* tail = reinterpret_cast<const T*>(src) + (size_t)(vi + 1) * EALIGN;
+                  if (lane == 31) {
+                    // the next vector belongs to the next pass: read it from shared memory, or
+                    // take zeros past the band (the shuffle above returned this lane's own values)
+                    const bool in_band = vi < nvec && vi + 1 < nband;
+                    const T* tail = reinterpret_cast<const T*>(src) + (size_t)(in_band ? vi + 1 : 0) * EALIGN;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                      const float p = S::ld(tail + k);
+                      const float p = in_band ? S::ld(tail + k) : 0.f;
                       nx[k] = S::scaled ? p * scale : p;
                     }
                   }
@@ -555,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               for (int ws = ws_lo + lane; ws < ws_lo + qn; ws += 32) {
                 float s = 0.f;
                 for (int k = 0; k < W; ++k) {
-                  const float p = S::ld(pb + ws + k);
+                  const float p = ws + k < kPadL + plen ? S::ld(pb + ws + k) : 0.f;
                   s += S::scaled ? p * scale : p;
                 }
                 q[ws] = s;
@@ -564,12 +579,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             if (lane < a.nsp)
               qdseg[qs * a.nsp + lane] =
                   reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[lane];
+            __syncwarp();
             if (lane == 0) {
+              q[ws_lo + qn] = 0.f;  // the sum every centre outside Q reads in the complete case
               QHdr h;
               h.ws_lo = ws_lo;
               h.qn = qn;
               h.qbase = plo - kPadL + ws_lo + m;  // centre of the window starting at ws_lo
-              h.pad = 0;
+              h.complete = complete ? 1 : 0;
               qhdr[qs] = h;
             }
             mbar_arrive(&full_q[qs]);  // every lane releases its own writes
@@ -754,26 +771,52 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         const unsigned kin = (unsigned)(h.qbase + m);
         const unsigned qn = (unsigned)h.qn;
         unsigned pend = 0u;
+        if (h.complete) {
+          // complete band: a centre outside Q reads the 0 at q[qn]; only FP32-undecided pairs
+          // are pending
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float y = y0[r];
+          for (int r = 0; r < R; ++r) {
+            float y = y0[r];
 #pragma unroll
-          for (int k = 0; k < KP; ++k) y = fmaf(c[r][k], d[k], y);
-          const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
-          const float dd = y - (tt - 12582912.0f);
-          const unsigned off = (unsigned)__float_as_int(tt) + koff;
-          const bool und = !(fabsf(dd) < wlim);
-          const bool inq = off < qn;
-          const bool outside = !inq && off + kin < nin;
-          pend |= (unsigned)(und || outside) << r;
-          const bool use = inq && !und;
-          const float v = q[use ? off : 0u];  // the address is always valid
-          acc[r] += use ? v : 0.f;
-          if (BINS) {
-            const int b = (int)off + h.qbase;
-            const long long t = tile0 + ctid + r * kCons;
-            if (t < tend && !(und || outside))
-              J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+            for (int k = 0; k < KP; ++k) y = fmaf(c[r][k], d[k], y);
+            const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
+            const float dd = y - (tt - 12582912.0f);
+            const unsigned off = (unsigned)__float_as_int(tt) + koff;
+            const bool und = !(fabsf(dd) < wlim);
+            const float v = q[min(off, qn)];
+            acc[r] += und ? 0.f : v;
+            pend |= (unsigned)und << r;
+            if (BINS) {
+              const int b = (int)off + h.qbase;
+              const long long t = tile0 + ctid + r * kCons;
+              if (t < tend && !und)
+                J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+            }
+          }
+        } else {
+          // incomplete band (cut to the slot, or m too wide for the pad): pairs whose window
+          // overlaps the table but whose centre lies outside Q are pending too
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float y = y0[r];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) y = fmaf(c[r][k], d[k], y);
+            const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
+            const float dd = y - (tt - 12582912.0f);
+            const unsigned off = (unsigned)__float_as_int(tt) + koff;
+            const bool und = !(fabsf(dd) < wlim);
+            const bool inq = off < qn;
+            const bool outside = !inq && off + kin < nin;
+            pend |= (unsigned)(und || outside) << r;
+            const bool use = inq && !und;
+            const float v = q[use ? off : 0u];  // the address is always valid
+            acc[r] += use ? v : 0.f;
+            if (BINS) {
+              const int b = (int)off + h.qbase;
+              const long long t = tile0 + ctid + r * kCons;
+              if (t < tend && !(und || outside))
+                J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+            }
           }
         }
         // (rare) queue the pending pairs
@@ -848,7 +891,7 @@ inline int sm_count() {
   return n;
 }
 
-inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 10 : (KP <= 16 ? 5 : 2)); }
+inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 5 : 2)); }
 
 template <int DT, int MJ>
 int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
@@ -972,7 +1015,7 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
   TFS_LAUNCH_KP(2, 12)
   TFS_LAUNCH_KP(4, 12)
   TFS_LAUNCH_KP(6, 12)
-  TFS_LAUNCH_KP(8, 10)
+  TFS_LAUNCH_KP(8, 9)
   TFS_LAUNCH_KP(16, 5)
   TFS_LAUNCH_KP(32, 2)
 #undef TFS_LAUNCH_KP

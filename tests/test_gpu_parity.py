@@ -304,6 +304,26 @@ def test_eval_stat_track_counts(T, N):
     _eval_and_check(T, P, V, c, f, 4096.0, 1, "f32", topk=min(N, 7))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f8e4m3"])
+@pytest.mark.parametrize("m", [1, 2, 3, 8, 9])
+@pytest.mark.parametrize("n_bin", [64, 700, 1001, 1016, 1024, 1025])
+def test_eval_stat_table_edges(T, dtype, m, n_bin):
+    """Tracks crowding both ends of the table, many leaving it: the windows that
+    reach past bin 0 or past the last bin (window sums built with zeros outside
+    the table), for band ends at every position of the builders' 16-byte vectors
+    and of a warp's lanes, widths that fit the left zero pad (2m <= 16) and
+    widths that do not."""
+    rng = np.random.default_rng(1000 * m + n_bin)
+    n_seg, K, N, Tsft = 24, 3, 3000, 4096.0
+    P = rng.exponential(2.0, (n_seg, n_bin))
+    V = np.linalg.qr(rng.standard_normal((n_seg, K)))[0].T.copy()
+    side = rng.integers(0, 2, N)
+    f_ref = np.where(side == 0, rng.uniform(-3.0 * m - 4, 3.0 * m + 4, N),
+                     n_bin + rng.uniform(-3.0 * m - 4, 3.0 * m + 4, N)) / Tsft
+    c = rng.uniform(-1.0, 1.0, (N, K)) * 3.0 / Tsft
+    _eval_and_check(T, P, V, c, f_ref, Tsft, m, dtype, topk=5)
+
+
 def test_eval_stat_exact_ties_everywhere(T):
     """Every pair lands exactly on a half-integer: all pairs take the FP64 path,
     the per-segment queues overflow and the tie report lists every pair."""
