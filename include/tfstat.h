@@ -216,6 +216,57 @@ typedef struct tfs_job {
 
 int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* stream);
 
+/* ---- serving: many resident datasets, requests batched as they arrive -------
+ * The paper evaluates walker populations in batches (Sec. II.D); serving many
+ * independent searches at once has no counterpart in the paper.  A server keeps
+ * datasets' tables on the current device under a byte budget and evaluates
+ * submitted requests (a dataset, a batch of tracks) with continuous batching:
+ * one worker thread keeps up to two tfs_eval_batch launches in flight on two
+ * streams and admits queued requests (first come, first served) as soon as
+ * their buffers, plus their table if it was evicted, fit under the budget.
+ * Idle tables are evicted least recently used first; their bytes stay in host
+ * memory and return on the next use (an eviction waits for the device).
+ * Thread-safe: submit and wait may be called from any threads. */
+typedef struct tfs_server tfs_server;
+
+typedef struct tfs_server_stats {
+  int64_t submitted, completed, failed, tracks_completed;
+  int64_t evictions, loads, batches;
+  int64_t used_bytes, resident_bytes, budget_bytes;
+  double mean_jobs_per_batch;
+  double p50_ms, p99_ms, mean_ms; /* latency: submit to the return of tfs_server_wait */
+} tfs_server_stats;
+
+/* budget_bytes > 0 bounds resident tables plus admitted requests' device
+ * buffers (approximately: per-call scratch of tfs_eval_batch is not counted);
+ * 1 <= max_batch_jobs <= 4096 requests per launch.  Binds the current device. */
+int tfs_server_create(int64_t budget_bytes, int max_batch_jobs, tfs_server** out);
+
+/* The server takes ownership of `table` (freed by tfs_server_free; do not free
+ * it yourself) and borrows `basis` (it must outlive the server).  ds_id
+ * receives the dataset's id (0, 1, ...). */
+int tfs_server_add_dataset(tfs_server* s, tfs_table* table, const tfs_basis* basis, int* ds_id);
+
+/* Queue a request: coeffs [N][K] and f_ref [N] (or NULL) are HOST arrays that
+ * must stay valid until tfs_server_wait returns for the ticket (they are read
+ * when the request is admitted).  1 <= N < 2^31, 0 <= m <= 64, 0 <= topk <= 1024.
+ * Returns TFS_ERR_OOM if the request and its table alone exceed the budget,
+ * TFS_ERR_NOT_FOUND for an unknown dataset.  Does not wait. */
+int tfs_server_submit(tfs_server* s, int ds_id, const double* coeffs, const double* f_ref, int64_t N, int m,
+                      int topk, int64_t* ticket);
+
+/* Wait for a ticket (timeout_ms < 0: no limit) and copy its results to host
+ * stat [N], top_idx / top_val [min(topk, N)] (any may be NULL).  The statistic
+ * is the one tfs_eval_stat gives within FP32 rounding (the bins are identical).
+ * TFS_ERR_TIMEOUT leaves the ticket valid; any other return consumes it. */
+int tfs_server_wait(tfs_server* s, int64_t ticket, int timeout_ms, float* stat, int64_t* top_idx, float* top_val);
+
+int tfs_server_get_stats(tfs_server* s, tfs_server_stats* out);
+
+/* Stops the worker after the queued requests ran, frees the server's tables
+ * and buffers.  Tickets not yet waited for are dropped. */
+int tfs_server_free(tfs_server* s);
+
 /* Number of kernels this library has launched in this process (all devices). */
 long long tfs_kernel_launches(void);
 

@@ -9,6 +9,8 @@ marshals arguments.  Functions keep the C names without the ``tfs_`` prefix:
 * ``build_basis(tracks, K=0, tol=1e-7)`` -> ``Basis``;  ``basis_from_host(U)`` -> ``Basis``
 * ``eval_stat(table, basis, coeffs, f_ref=None, m=0, topk=0, ...)`` -> ``EvalResult``
 * ``eval_batch([Job(table, basis, coeffs, ...), ...], dev_status=None)`` -> the jobs, outputs filled
+* ``Server(budget_bytes)``: ``add_dataset(table, basis)``, ``submit(ds, coeffs, ...)`` -> ticket,
+  ``wait(ticket)`` -> (stat, top_idx, top_val), ``stats()``
 * ``topk(values, k)`` -> (idx, val)
 
 Array arguments are numpy arrays (host memory: the call copies in and out
@@ -263,6 +265,72 @@ def eval_batch(jobs, dev_status=None, stream=None):
     check(lib().tfs_eval_batch(arr, len(jobs), _ptr(dev_status) if dev_status is not None else None,
                                _stream_ptr(stream)))
     return jobs
+
+
+class Server:
+    """Serving runtime (tfs_server_*): resident datasets under a device-memory budget,
+    requests batched as they arrive.  Thread-safe; submit() returns a ticket, wait()
+    returns (stat, top_idx, top_val) as numpy arrays."""
+
+    def __init__(self, budget_bytes: int, max_batch_jobs: int = 64):
+        self._h = ctypes.c_void_p()
+        check(lib().tfs_server_create(int(budget_bytes), int(max_batch_jobs), ctypes.byref(self._h)))
+        self._bases = []      # bases must outlive the server
+        self._inputs = {}     # host inputs must stay alive until their ticket is waited for
+        self._shape = {}
+        self._lock = __import__("threading").Lock()
+
+    def add_dataset(self, table: Table, basis: Basis) -> int:
+        """Hand `table` over to the server (it frees it) and return the dataset id."""
+        ds = ctypes.c_int()
+        check(lib().tfs_server_add_dataset(self._h, table.handle, basis.handle, ctypes.byref(ds)))
+        table._h = None
+        self._bases.append(basis)
+        return ds.value
+
+    def submit(self, ds: int, coeffs, f_ref=None, m: int = 0, topk: int = 0) -> int:
+        c = _f64(coeffs)
+        fr = _f64(f_ref) if f_ref is not None else None
+        N = c.shape[0]
+        t = ctypes.c_int64()
+        check(lib().tfs_server_submit(self._h, int(ds), _ptr(c), _ptr(fr) if fr is not None else None, N, int(m),
+                                      int(topk), ctypes.byref(t)))
+        with self._lock:
+            self._inputs[t.value] = (c, fr)
+            self._shape[t.value] = (N, min(int(topk), N))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        with self._lock:
+            N, kk = self._shape[ticket]
+        stat = np.empty(N, dtype=np.float32)
+        ti = np.empty(kk, dtype=np.int64)
+        tv = np.empty(kk, dtype=np.float32)
+        rc = lib().tfs_server_wait(self._h, int(ticket), int(timeout_ms), _ptr(stat), _ptr(ti) if kk else None,
+                                   _ptr(tv) if kk else None)
+        if rc != -4:  # TIMEOUT keeps the ticket
+            with self._lock:
+                self._inputs.pop(ticket, None)
+                self._shape.pop(ticket, None)
+        check(rc)
+        return stat, ti, tv
+
+    def stats(self) -> dict:
+        st = _lib.TfsServerStats()
+        check(lib().tfs_server_get_stats(self._h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in st._fields_}
+
+    def close(self):
+        if self._h:
+            lib().tfs_server_free(self._h)
+            self._h = None
+            self._inputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def topk(values, k: int, stream=None):

@@ -36,7 +36,21 @@ SIGNATURES = {
     "tfs_kernel_launches": (ctypes.c_longlong, []),
     "tfs_topk_noalloc": (I, [P, I64, I, P, P, P]),
     "tfs_eval_batch": (I, [P, I, P, P]),
+    "tfs_server_create": (I, [I64, I, P]),
+    "tfs_server_add_dataset": (I, [P, P, P, P]),
+    "tfs_server_submit": (I, [P, I, P, P, I64, I, I, P]),
+    "tfs_server_wait": (I, [P, I64, I, P, P, P]),
+    "tfs_server_get_stats": (I, [P, P]),
+    "tfs_server_free": (I, [P]),
 }
+
+
+class TfsServerStats(ctypes.Structure):
+    """struct tfs_server_stats (include/tfstat.h)."""
+
+    _fields_ = [(n, I64) for n in ("submitted", "completed", "failed", "tracks_completed", "evictions", "loads",
+                                   "batches", "used_bytes", "resident_bytes", "budget_bytes")] + \
+               [(n, ctypes.c_double) for n in ("mean_jobs_per_batch", "p50_ms", "p99_ms", "mean_ms")]
 
 
 class TfsJob(ctypes.Structure):

@@ -72,6 +72,21 @@ def test_host_validation_without_device(L):
     assert b"job 0" in L.tfs_last_error()
 
 
+def test_server_validation_without_device(L):
+    out = ctypes.c_void_p()
+    assert L.tfs_server_create(0, 64, ctypes.byref(out)) == -1
+    assert L.tfs_server_create(1 << 30, 0, ctypes.byref(out)) == -1
+    t = ctypes.c_int64()
+    assert L.tfs_server_submit(None, 0, None, None, 10, 0, 0, ctypes.byref(t)) == -1
+    assert L.tfs_server_wait(None, 1, 0, None, None, None) == -1
+    assert L.tfs_server_get_stats(None, None) == -1
+    assert L.tfs_server_free(None) == 0
+
+
+def test_server_stats_struct_matches_the_header():
+    assert ctypes.sizeof(_lib.TfsServerStats) == 10 * 8 + 4 * 8
+
+
 def test_job_struct_matches_the_header():
     """struct tfs_job: 8-byte fields except m and topk (int32 each), no padding."""
     assert ctypes.sizeof(_lib.TfsJob) == 9 * 8
