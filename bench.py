@@ -51,6 +51,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
+    ap.add_argument("--stat-error", type=int, default=0,
+                    help="also report the statistic's error against the FP64 oracle on the exact table, "
+                         "over this many sampled tracks")
+    ap.add_argument("--batch-jobs", type=int, default=64, help="datasets of the batched workload")
+    ap.add_argument("--requests", type=int, default=1000, help="requests of the served workload")
+    ap.add_argument("--rate", type=float, default=200.0, help="request arrival rate (Hz) of the served workload")
+    ap.add_argument("--datasets", type=int, default=32, help="resident datasets of the served workload")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="device-memory budget of the served workload")
     return ap.parse_args()
 
 
@@ -351,6 +359,19 @@ def run_ours(args):
         cpu = {"value": cpu_val, "unit": UNIT, "cores": ncores, "kind": "oracle",
                "sample": f"FP64 SFT of the full strain ({t_sft:.2f} s, 1 process) + statistic of {sample} tracks "
                          f"on {ncores} processes ({t_eval:.2f} s), scaled to {N} tracks per step"}
+    stat_err = None
+    if rank == 0 and args.stat_error > 0:
+        import oracle.tfstat_oracle as O
+
+        n_s = min(args.stat_error, N)
+        P64 = O.power_table(x, w.dt, w.T_sft, psd)
+        T.check(L.tfs_eval_stat(table.handle, basis.handle, coeffs_d.data_ptr(), None, N, w.m, 0,
+                                stat.data_ptr(), None, None, None, 1, sp))
+        got = stat[:n_s].double().cpu().numpy()
+        ref, *_ = O.eval_stat(P64, U, coeffs_h[:n_s], np.zeros(n_s), w.T_sft, w.m, 0)
+        rel = np.abs(got - ref) / np.abs(ref)
+        stat_err = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "tracks": n_s,
+                    "against": "FP64 oracle statistic of the exact FP64 table (no quantisation)"}
     if rank != 0:
         return
     clocks = clk.summary()
@@ -372,15 +393,249 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "cpu_baseline": cpu}
+    if stat_err is not None:
+        line["stat_error"] = stat_err
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- batched datasets
+def run_batched(args):
+    """64 uneven datasets (durations, T_SFT, K, track counts) evaluated by one persistent
+    launch per step, replayed from a CUDA graph; compared with one tfs_eval_stat per dataset."""
+    from concurrent.futures import ProcessPoolExecutor
+
+    items = synth.batched_workloads(args.batch_jobs)
+    ncores = os.cpu_count() or 1
+    with ProcessPoolExecutor(ncores, mp_context=mp.get_context("spawn")) as ex:  # before any CUDA call
+        data = list(ex.map(synth.make_batched_inputs, items))
+    import torch
+    from paper_2510_20891_gb300 import build as B
+
+    B.build()
+    import paper_2510_20891_gb300 as T
+
+    L = T.lib()
+    stream = torch.cuda.current_stream()
+    jobs, keep = [], []
+    for (w, snr), (x, psd, F) in zip(items, data):
+        x_d = torch.from_numpy(x).cuda()
+        table = T.build_sfts(x_d, w.dt, w.T_sft, psd, "hann", args.dtype)
+        del x_d
+        basis = T.build_basis(F, w.K)
+        U, sig, cmin, cmax = basis.to_host()
+        c = torch.from_numpy(synth.uniform_coeffs(w.n_tracks, cmin, cmax, np.random.default_rng(1000 + w.seed))).cuda()
+        jobs.append(T.Job(table, basis, c, None, m=w.m, topk=min(args.topk, w.n_tracks)))
+        keep.append((table, basis))
+    n_tracks = sum(w.n_tracks for w, _ in items)
+    pairs = sum(w.n_tracks * w.n_seg for w, _ in items)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    T.eval_batch(jobs, dev_status=status)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            T.eval_batch(jobs, dev_status=status, stream=side.cuda_stream)
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    launches0 = L.tfs_kernel_launches()
+    with ClockSampler(0) as clk:
+        ms = timed(g.replay, args.steps)
+    assert int(status.item()) == 0
+    # graph launches do not pass through the library's counter: count one replay's kernels
+    k0 = L.tfs_kernel_launches()
+    T.eval_batch(jobs, dev_status=status)
+    torch.cuda.synchronize()
+    per_batch = L.tfs_kernel_launches() - k0
+    ms_uncaptured = timed(lambda: T.eval_batch(jobs, dev_status=status), max(3, args.steps // 4))
+
+    def sequential():
+        for j in jobs:
+            T.eval_stat(j.table, j.basis, j.coeffs, None, m=j.m, topk=j.topk, stat=j.stat, top_idx=j.top_idx,
+                        top_val=j.top_val)
+
+    ms_seq = timed(sequential, max(3, args.steps // 4))
+    del launches0
+    esize = {"f32": 4, "bf16": 2, "f16": 2, "f8e4m3": 1}[args.dtype]
+    bytes_all = sum(w.n_tracks * (w.n_seg * (2 * w.m + 1) * esize + w.K * 8 + 4) for w, _ in items)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_all / (ms / 1e3) / 1e9
+    value = n_tracks / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": f"batched{args.batch_jobs}", "datasets": len(items), "tracks": n_tracks,
+                       "pairs": pairs, "T_sft_s": sorted({w.T_sft for w, _ in items}),
+                       "K": sorted({w.K for w, _ in items}), "n_seg_range": [min(w.n_seg for w, _ in items),
+                                                                            max(w.n_seg for w, _ in items)],
+                       "m": 1, "topk_per_dataset": args.topk, "table_dtype": args.dtype,
+                       "launch": "one tfs_eval_batch per step (one persistent launch per table dtype, "
+                                 "per-dataset top-k), replayed from a CUDA graph",
+                       "l2": "coefficients %.0f MB per step (larger than L2)" % (n_tracks * 6 * 8 / 1e6)},
+            "uncaptured_ms_per_step": ms_uncaptured,
+            "sequential_ms_per_step": ms_seq,
+            "sequential_value": n_tracks / (ms_seq / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": "eval_stat_kernel (all datasets)"},
+            "e2e": None,
+            "gpu_launches": int(per_batch) * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- served requests
+def run_served(args):
+    """Poisson requests (a dataset and 10^3-10^6 tracks, BF16 or FP32 table) against resident
+    datasets of the 1577 x 20001 shape, served with continuous batching under a budget;
+    compared with the plain FP32 path that runs one request at a time."""
+    import threading
+
+    import torch
+    from paper_2510_20891_gb300 import build as B
+
+    B.build()
+    import paper_2510_20891_gb300 as T
+
+    w = synth.WORKLOADS["oneyear_fine_1577x20001"]
+    rng = np.random.default_rng(0)
+    basis = T.build_basis(synth.make_training_tracks(w, rng), w.K)
+    U, sig, cmin, cmax = basis.to_host()
+    reqs = synth.served_requests(args.requests, args.rate, args.datasets, seed=0)
+    bank = synth.uniform_coeffs(int(max(r[2] for r in reqs)), cmin, cmax, np.random.default_rng(1))
+    offs = np.random.default_rng(2).integers(0, 1 << 20, len(reqs))
+    budget = int(args.budget_gb * (1 << 30))
+    srv = T.Server(budget, max_batch_jobs=64)
+    ids, f32_tables = {}, []
+    for d in range(args.datasets):
+        P = synth.noise_power_table(w.n_seg, w.n_bin, np.random.default_rng(100 + d))
+        for dt in ("f32", "bf16"):
+            ids[(d, dt)] = srv.add_dataset(T.table_from_power(P, w.T_sft, dt), basis)
+        f32_tables.append(T.table_from_power(P, w.T_sft, "f32") if d < 4 else None)
+    torch.cuda.synchronize()
+
+    def coeffs_of(i):
+        N = reqs[i][2]
+        o = int(offs[i]) % max(1, bank.shape[0] - N + 1)
+        return bank[o:o + N]
+
+    # warm-up: one request per dtype (builds the cached per-segment data)
+    for dt in ("f32", "bf16"):
+        srv.wait(srv.submit(ids[(0, dt)], coeffs_of(0)[:1000], None, m=w.m, topk=16))
+    s0 = srv.stats()
+    tickets = [None] * len(reqs)
+    done_t = [0.0] * len(reqs)
+    t_start = time.perf_counter()
+
+    def collect(k, n_threads):
+        for i in range(k, len(reqs), n_threads):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            srv.wait(tickets[i], 600000)
+            done_t[i] = time.perf_counter()
+
+    n_coll = 16
+    coll = [threading.Thread(target=collect, args=(k, n_coll)) for k in range(n_coll)]
+    for t in coll:
+        t.start()
+    with ClockSampler(0) as clk:
+        for i, (ta, d, N, dt) in enumerate(reqs):
+            now = time.perf_counter() - t_start
+            if ta > now:
+                time.sleep(ta - now)
+            tickets[i] = srv.submit(ids[(d, dt)], coeffs_of(i), None, m=w.m, topk=16)
+        for t in coll:
+            t.join()
+    t_end = max(done_t)
+    st = srv.stats()
+    n_tracks = sum(r[2] for r in reqs)
+    served_lat = st["p50_ms"], st["p99_ms"]
+    value = n_tracks / (t_end - t_start)
+
+    # saturation: every request submitted at once (no pacing): the server's throughput
+    t_sat0 = time.perf_counter()
+    sat = [srv.submit(ids[(d, dt)], coeffs_of(i), None, m=w.m, topk=16) for i, (ta, d, N, dt) in enumerate(reqs)]
+    for tk in sat:
+        srv.wait(tk, 600000)
+    sat_s = time.perf_counter() - t_sat0
+    st_sat = srv.stats()
+
+    # accuracy of the BF16 path against FP32 on the same tracks (a few requests)
+    errs = []
+    for i in range(4):
+        c = coeffs_of(i)[:20000]
+        a = srv.wait(srv.submit(ids[(i, "bf16")], c, None, m=w.m))[0].astype(np.float64)
+        b = T.eval_stat(f32_tables[i], basis, c, None, m=w.m).stat.astype(np.float64)
+        errs.append(float(np.max(np.abs(a - b) / np.abs(b))))
+    srv.close()
+
+    # the plain FP32 path: one request at a time, in arrival order, through tfs_eval_stat
+    t_b0 = time.perf_counter()
+    for i, (ta, d, N, dt) in enumerate(reqs):
+        T.eval_stat(f32_tables[d % 4], basis, coeffs_of(i), None, m=w.m, topk=16)
+    base_sat_s = time.perf_counter() - t_b0
+    lat = []
+    t0 = time.perf_counter()
+    for i, (ta, d, N, dt) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tb = f32_tables[d % 4]
+        T.eval_stat(tb, basis, coeffs_of(i), None, m=w.m, topk=16)
+        lat.append((time.perf_counter() - t0 - ta) * 1e3)
+    t1 = time.perf_counter() - t0
+    lat.sort()
+    base = {"value": n_tracks / t1, "saturated_value": n_tracks / base_sat_s, "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "path": "tfs_eval_stat on FP32 tables, host buffers, one request at a time in arrival order"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 2,
+            "ms_per_step": (t_end - t_start) * 1e3 / len(reqs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": f"served{args.datasets}", "requests": len(reqs), "rate_hz": args.rate,
+                       "tracks": n_tracks, "tracks_per_request": "log-uniform 1e3..1e6", "n_seg": w.n_seg,
+                       "n_bin": w.n_bin, "K": w.K, "m": w.m, "topk": 16, "tables": "BF16 or FP32 per request",
+                       "budget_gb": args.budget_gb},
+            "served": {"p50_ms": served_lat[0], "p99_ms": served_lat[1], "mean_ms": st["mean_ms"],
+                       "batches": st["batches"] - s0["batches"], "mean_jobs_per_batch": st["mean_jobs_per_batch"],
+                       "evictions": st["evictions"], "loads": st["loads"], "failed": st["failed"],
+                       "bf16_vs_f32_max_rel_err": max(errs),
+                       "saturated_value": n_tracks / sat_s,
+                       "saturated_mean_jobs_per_batch": (st_sat["mean_jobs_per_batch"] * st_sat["batches"] -
+                                                         st["mean_jobs_per_batch"] * st["batches"]) /
+                                                        max(1, st_sat["batches"] - st["batches"])},
+            "baseline_fp32_one_at_a_time": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(n_tracks * w.K * 8 / len(reqs)),
+                    "d2h_bytes_per_step": int(n_tracks * 4 / len(reqs))},
+            "gpu_launches": None,
+            "clocks": clk.summary(),
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -166,6 +166,7 @@ class Workload:
     family: str          # "quad" or "powerlaw"
     psd: str             # "white" or "oneyear"
     seed: int = 0
+    tau_yr: tuple = (1.5, 5.0)  # power-law family: tau range (years); tau must exceed the duration
 
     @property
     def L(self):
@@ -207,7 +208,7 @@ def make_strain(w: Workload, rng: np.random.Generator, snr: float | None = None,
             x = x + chirp_signal(n, dt, inj["f0"], inj["fdot"], inj["amp"])
         return x, inj
     x = coloured_noise(n, dt, psd_oneyear, rng)
-    f0, tau, p = powerlaw_params(1, rng)
+    f0, tau, p = powerlaw_params(1, rng, tau_yr=w.tau_yr)
     inj = dict(kind="powerlaw", f0=float(f0[0]), tau=float(tau[0]), p=float(p[0]), snr=30.0 if snr is None else snr)
     if inject:
         a0 = powerlaw_amplitude_for_snr(n, dt, inj["f0"], inj["tau"], inj["p"], inj["snr"], psd_oneyear)
@@ -221,4 +222,66 @@ def make_training_tracks(w: Workload, rng: np.random.Generator, M: int | None = 
     M = w.n_train if M is None else M
     if w.family == "quad":
         return quad_chirp_tracks(M, t, rng)
-    return powerlaw_tracks(M, t, rng)
+    return powerlaw_tracks(M, t, rng, tau_yr=w.tau_yr)
+
+
+# --------------------------------------------------------------------------
+# Batched datasets and served datasets
+# --------------------------------------------------------------------------
+def batched_workloads(n: int = 64, seed0: int = 1):
+    """Independent datasets of the one-year family for one batched launch: durations
+    U[0.25, 2] yr at dt = 5 s, T_sft drawn from {1e4, 2e4, 5e4, 1e5} s, the one-year PSD,
+    one power-law harmonic injected at SNR U[15, 40], K drawn from {4, 6, 8}, 10^U[4,6]
+    candidate tracks, +-1-bin neighbours.  The family's tau is drawn from
+    U[max(1.5, 1.25 D), max(5, that + 1)] yr for a dataset of D years, so that its
+    frequency stays finite over the whole dataset.  Dataset i uses seed seed0 + i for every draw.
+    Returns a list of (Workload, snr)."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed0 + i)
+        dur = rng.uniform(0.25, 2.0) * YEAR_S
+        T = float(rng.choice([1e4, 2e4, 5e4, 1e5]))
+        K = int(rng.choice([4, 6, 8]))
+        N = int(round(10.0 ** rng.uniform(4.0, 6.0)))
+        snr = float(rng.uniform(15.0, 40.0))
+        L = int(round(T / 5.0))
+        n_seg = max(1, int(dur // T))
+        # the family's frequency diverges at t = tau: keep tau beyond the dataset's span
+        tau_lo = max(1.5, 1.25 * dur / YEAR_S)
+        out.append((Workload(f"batch{seed0 + i}", 5.0, n_seg * L, T, K, N, 1, 2000, "powerlaw", "oneyear",
+                             seed0 + i, (tau_lo, max(5.0, tau_lo + 1.0))), snr))
+    return out
+
+
+def make_batched_inputs(item):
+    """Strain, PSD bins and training tracks of one batched dataset (picklable: for a
+    process pool).  ``item`` is one entry of ``batched_workloads``."""
+    w, snr = item
+    rng = np.random.default_rng(w.seed)
+    x, inj = make_strain(w, rng, snr=snr)
+    psd = psd_bins(w.psd_fn(), w.n_bin, w.T_sft)
+    F = make_training_tracks(w, rng)
+    return x, psd, F
+
+
+def noise_power_table(n_seg: int, n_bin: int, rng: np.random.Generator):
+    """A normalised power table of stationary Gaussian noise without its window's bin
+    correlations: every P[alpha][k] is chi^2_2 (exponential with mean 2), P[alpha][0] = 0.
+    Stands in for tables built from strain where only their shape and value distribution
+    matter (serving throughput)."""
+    P = rng.exponential(2.0, (n_seg, n_bin))
+    P[:, 0] = 0.0
+    return P
+
+
+def served_requests(n: int, rate_hz: float, n_datasets: int, seed: int = 0,
+                    tracks=(1e3, 1e6), dtypes=("bf16", "f32")):
+    """Poisson arrivals: (arrival time s, dataset index, track count, table dtype) per request,
+    exponential inter-arrival times at ``rate_hz``, track counts log-uniform in ``tracks``."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    ds = rng.integers(0, n_datasets, n)
+    N = np.round(10.0 ** rng.uniform(math.log10(tracks[0]), math.log10(tracks[1]), n)).astype(np.int64)
+    dt = rng.integers(0, len(dtypes), n)
+    return [(float(t[i]), int(ds[i]), int(N[i]), dtypes[int(dt[i])]) for i in range(n)]
+
