@@ -55,6 +55,7 @@ def parse():
                     help="also report the statistic's error against the FP64 oracle on the exact table, "
                          "over this many sampled tracks")
     ap.add_argument("--batch-jobs", type=int, default=64, help="datasets of the batched workload")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default launch shape")
     ap.add_argument("--requests", type=int, default=1000, help="requests of the served workload")
     ap.add_argument("--rate", type=float, default=200.0, help="request arrival rate (Hz) of the served workload")
     ap.add_argument("--datasets", type=int, default=32, help="resident datasets of the served workload")
@@ -433,6 +434,17 @@ def run_batched(args):
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     T.eval_batch(jobs, dev_status=status)
     torch.cuda.synchronize()
+    ms_default = None
+    tuned = None
+    if not args.no_autotune:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            T.eval_batch(jobs, dev_status=status)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_default = e0.elapsed_time(e1) / 3
+        tuned, _ = T.autotune(jobs, reps=3)   # untimed: picks the launch shape used below
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -488,6 +500,7 @@ def run_batched(args):
                                  "per-dataset top-k), replayed from a CUDA graph",
                        "l2": "coefficients %.0f MB per step (larger than L2)" % (n_tracks * 6 * 8 / 1e6)},
             "uncaptured_ms_per_step": ms_uncaptured,
+            "autotuned_shape": tuned, "default_shape_ms_per_step": ms_default,
             "sequential_ms_per_step": ms_seq,
             "sequential_value": n_tracks / (ms_seq / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -216,6 +216,28 @@ typedef struct tfs_job {
 
 int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* stream);
 
+/* ---- launch-shape autotuning ---------------------------------------------
+ * Not part of the paper's method: it picks how the statistic kernel is laid
+ * out for a kind of workload.  pcap is the number of table elements of one
+ * segment's band staged per tile (wide bands beyond it take a slower path),
+ * tile_div divides the tracks per tile (smaller tiles: more of them, better
+ * balance for small jobs).  tfs_autotune_batch evaluates `jobs` (as
+ * tfs_eval_batch, overwriting their outputs) under every candidate shape,
+ * `reps` times each, and keeps the fastest for every launch of this kind
+ * (table dtype, coefficient slots, widest row and longest job in powers of
+ * two, single job or batch); later tfs_eval_stat / tfs_eval_batch calls of
+ * that kind use it.  Synchronous.  The choices live in the process; save and
+ * load them as a small JSON object {"key": [pcap, tile_div], ...}. */
+typedef struct tfs_tuning {
+  int32_t pcap;
+  int32_t tile_div;
+} tfs_tuning;
+
+int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms, void* stream);
+int tfs_tuning_save(const char* path);
+int tfs_tuning_load(const char* path);
+int tfs_tuning_clear(void);
+
 /* ---- serving: many resident datasets, requests batched as they arrive -------
  * The paper evaluates walker populations in batches (Sec. II.D); serving many
  * independent searches at once has no counterpart in the paper.  A server keeps

@@ -11,6 +11,7 @@ marshals arguments.  Functions keep the C names without the ``tfs_`` prefix:
 * ``eval_batch([Job(table, basis, coeffs, ...), ...], dev_status=None)`` -> the jobs, outputs filled
 * ``Server(budget_bytes)``: ``add_dataset(table, basis)``, ``submit(ds, coeffs, ...)`` -> ticket,
   ``wait(ticket)`` -> (stat, top_idx, top_val), ``stats()``
+* ``autotune(jobs)`` -> (launch shape, ms); ``tuning_save(path)`` / ``tuning_load(path)``
 * ``topk(values, k)`` -> (idx, val)
 
 Array arguments are numpy arrays (host memory: the call copies in and out
@@ -247,6 +248,13 @@ def eval_batch(jobs, dev_status=None, stream=None):
     Outputs missing from a Job (stat, top-k) are allocated here and set on it.  With a device int32
     `dev_status` the call is asynchronous and capturable into a CUDA graph; without one it waits.
     """
+    arr = _job_array(jobs)
+    check(lib().tfs_eval_batch(arr, len(jobs), _ptr(dev_status) if dev_status is not None else None,
+                               _stream_ptr(stream)))
+    return jobs
+
+
+def _job_array(jobs):
     torch = _torch()
     arr = (_lib.TfsJob * len(jobs))()
     for i, j in enumerate(jobs):
@@ -260,11 +268,28 @@ def eval_batch(jobs, dev_status=None, stream=None):
             j.top_val = torch.empty(kk, dtype=torch.float32, device=dev)
         arr[i] = _lib.TfsJob(j.table.handle, j.basis.handle, _ptr(j.coeffs),
                              _ptr(j.f_ref) if j.f_ref is not None else None, N, j.m, j.topk,
-                             _ptr(j.stat) if j.stat is not None else None,
-                             _ptr(j.top_idx) if j.topk else None, _ptr(j.top_val) if j.topk else None)
-    check(lib().tfs_eval_batch(arr, len(jobs), _ptr(dev_status) if dev_status is not None else None,
-                               _stream_ptr(stream)))
-    return jobs
+                             _ptr(j.stat), _ptr(j.top_idx) if j.topk else None,
+                             _ptr(j.top_val) if j.topk else None)
+    return arr
+
+
+def autotune(jobs, reps: int = 3, stream=None):
+    """Time every candidate launch shape on `jobs` and keep the fastest for launches of
+    this kind (tfs_autotune_batch); returns ({"pcap": .., "tile_div": ..}, ms per batch)."""
+    arr = _job_array(jobs)
+    best = _lib.TfsTuning()
+    ms = ctypes.c_double()
+    check(lib().tfs_autotune_batch(arr, len(jobs), int(reps), ctypes.byref(best), ctypes.byref(ms),
+                                   _stream_ptr(stream)))
+    return {"pcap": best.pcap, "tile_div": best.tile_div}, ms.value
+
+
+def tuning_save(path: str):
+    check(lib().tfs_tuning_save(path.encode()))
+
+
+def tuning_load(path: str):
+    check(lib().tfs_tuning_load(path.encode()))
 
 
 class Server:

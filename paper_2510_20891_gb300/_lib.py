@@ -36,6 +36,10 @@ SIGNATURES = {
     "tfs_kernel_launches": (ctypes.c_longlong, []),
     "tfs_topk_noalloc": (I, [P, I64, I, P, P, P]),
     "tfs_eval_batch": (I, [P, I, P, P]),
+    "tfs_autotune_batch": (I, [P, I, I, P, P, P]),
+    "tfs_tuning_save": (I, [ctypes.c_char_p]),
+    "tfs_tuning_load": (I, [ctypes.c_char_p]),
+    "tfs_tuning_clear": (I, []),
     "tfs_server_create": (I, [I64, I, P]),
     "tfs_server_add_dataset": (I, [P, P, P, P]),
     "tfs_server_submit": (I, [P, I, P, P, I64, I, I, P]),
@@ -43,6 +47,12 @@ SIGNATURES = {
     "tfs_server_get_stats": (I, [P, P]),
     "tfs_server_free": (I, [P]),
 }
+
+
+class TfsTuning(ctypes.Structure):
+    """struct tfs_tuning (include/tfstat.h)."""
+
+    _fields_ = [("pcap", ctypes.c_int32), ("tile_div", ctypes.c_int32)]
 
 
 class TfsServerStats(ctypes.Structure):

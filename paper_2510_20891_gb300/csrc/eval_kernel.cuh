@@ -910,7 +910,7 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
   a.status = L.status;
   a.dbg = L.dbg;
   a.nsp = nsp;
-  const long long tile = (long long)kCons * R;
+  const long long tile = (long long)kCons * R / std::max(1, std::min(tune.tile_div, 8));
   long long nt = 0;
   int row_max = 0, seg_max = 0;
   bool bins = false;

@@ -7,6 +7,9 @@
 #include <cstring>
 #include <atomic>
 
+#include <map>
+#include <string>
+
 #include "tfs_internal.cuh"
 
 namespace tfs {
@@ -153,8 +156,53 @@ int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams
   return TFS_OK;
 }
 
-int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
+// ---------------------------------------------------------------- launch tuning
+// Launch shapes chosen by tfs_autotune_batch, keyed by what decides them: table dtype,
+// coefficient slots, the widest row and the longest job (powers of two), single job or batch.
+static std::mutex g_tune_mu;
+static std::map<std::string, tfs_tuning> g_tune;
+thread_local const EvalTuning* g_force_tuning = nullptr;  // set while the tuner times a candidate
+
+static int ceil_log2(int64_t x) {
+  int k = 0;
+  while (((int64_t)1 << k) < x) ++k;
+  return k;
+}
+
+static std::string tuning_key(int dtype, int KP, int64_t row_max, int64_t seg_max, bool multi) {
+  char buf[96];
+  snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d", dtype, KP, ceil_log2(row_max), ceil_log2(seg_max), multi ? 1 : 0);
+  return buf;
+}
+
+static std::string launch_key(const EvalLaunch& L) {
+  int KP = 0;
+  int64_t row_max = 1, seg_max = 1;
+  for (int i = 0; i < L.n_jobs; ++i) {
+    KP = std::max(KP, L.jobs[i].sp->KP);
+    row_max = std::max<int64_t>(row_max, L.jobs[i].table->row_stride);
+    seg_max = std::max<int64_t>(seg_max, L.jobs[i].table->n_seg);
+  }
+  return tuning_key(L.jobs[0].table->dtype, KP, row_max, seg_max, L.n_jobs > 1);
+}
+
+static std::vector<std::string> g_last_keys;  // keys of the launches of the last tfs_eval_batch (tuner only)
+
+int launch_eval(const EvalLaunch& L, const EvalTuning& tune_in, cudaStream_t st) {
   if (L.n_jobs <= 0) return TFS_OK;
+  EvalTuning tune = tune_in;
+  const std::string key = launch_key(L);
+  if (g_force_tuning) {
+    tune = *g_force_tuning;
+    g_last_keys.push_back(key);
+  } else if (tune.cap == 0 && tune.tile_div == 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      tune.cap = it->second.pcap;
+      tune.tile_div = it->second.tile_div;
+    }
+  }
   switch (L.jobs[0].table->dtype) {
     case TFS_F32: return launch_eval_f32(L, tune, st);
     case TFS_BF16: return launch_eval_bf16(L, tune, st);
@@ -538,6 +586,124 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
     TFS_CUDA(cudaStreamSynchronize(st));
     TFS_CHECK(h_status == 0, TFS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", h_status);
   }
+  return TFS_OK;
+}
+
+int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms, void* stream) {
+  clear_error();
+  TFS_CHECK(best && reps >= 1 && reps <= 100, TFS_ERR_INVALID_ARG, "need best and 1 <= reps <= 100");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* d_status = nullptr;
+  TFS_CUDA(cudaMalloc(&d_status, sizeof(int)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // validation, per-segment data and a warm start with the current choice
+  int rc = tfs_eval_batch(jobs, n_jobs, d_status, stream);
+  if (rc == TFS_OK) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "autotune warm-up");
+  }
+  double best_t = 1e300;
+  tfs_tuning win{0, 0};
+  std::vector<std::string> keys;
+  const int caps[] = {512, 1024, 2048, 3072, 4096};
+  const int divs[] = {1, 2};
+  for (int ci = 0; ci < 5 && rc == TFS_OK; ++ci) {
+    for (int di = 0; di < 2 && rc == TFS_OK; ++di) {
+      EvalTuning t;
+      t.cap = caps[ci];
+      t.tile_div = divs[di];
+      g_force_tuning = &t;
+      g_last_keys.clear();
+      int r = tfs_eval_batch(jobs, n_jobs, d_status, stream);  // shape check (shared memory), warm
+      if (r == TFS_OK) {
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && r == TFS_OK; ++k) r = tfs_eval_batch(jobs, n_jobs, d_status, stream);
+        cudaEventRecord(e1, st);
+      }
+      g_force_tuning = nullptr;
+      if (r != TFS_OK) {
+        clear_error();
+        continue;  // this shape does not fit (e.g. shared memory): skip it
+      }
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "autotune timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = (double)ms / reps;
+      if (per < best_t) {
+        best_t = per;
+        win = tfs_tuning{t.cap, t.tile_div};
+        keys = g_last_keys;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_status);
+  if (rc != TFS_OK) return rc;
+  TFS_CHECK(best_t < 1e300, TFS_ERR_INVALID_ARG, "no launch shape fits these jobs");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const std::string& k : keys) g_tune[k] = win;
+  }
+  *best = win;
+  if (best_ms) *best_ms = best_t;
+  return TFS_OK;
+}
+
+int tfs_tuning_save(const char* path) {
+  clear_error();
+  TFS_CHECK(path, TFS_ERR_INVALID_ARG, "null path");
+  FILE* f = fopen(path, "w");
+  TFS_CHECK(f, TFS_ERR_INVALID_ARG, "cannot write %s", path);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : g_tune)
+    fprintf(f, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.pcap, kv.second.tile_div,
+            ++i < g_tune.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
+  return TFS_OK;
+}
+
+int tfs_tuning_load(const char* path) {
+  clear_error();
+  TFS_CHECK(path, TFS_ERR_INVALID_ARG, "null path");
+  FILE* f = fopen(path, "r");
+  TFS_CHECK(f, TFS_ERR_NOT_FOUND, "cannot read %s", path);
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+  fclose(f);
+  std::map<std::string, tfs_tuning> got;
+  size_t pos = 0;
+  while ((pos = txt.find('"', pos)) != std::string::npos) {
+    const size_t end = txt.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    const std::string key = txt.substr(pos + 1, end - pos - 1);
+    int cap = 0, div = 0;
+    if (sscanf(txt.c_str() + end + 1, " : [%d , %d]", &cap, &div) != 2 || cap < 0 || cap > (1 << 20) || div < 0 ||
+        div > 8) {
+      set_error("malformed tuning entry for %s", key.c_str());
+      return TFS_ERR_INVALID_ARG;
+    }
+    got[key] = tfs_tuning{cap, div};
+    pos = end + 1;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : got) g_tune[kv.first] = kv.second;
+  return TFS_OK;
+}
+
+int tfs_tuning_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
   return TFS_OK;
 }
 

@@ -113,6 +113,7 @@ struct EvalTuning {       // launch shape; zeros select defaults
   int stages = 0;
   int cap = 0;            // staged band capacity per row (elements)
   int qcap = 0;
+  int tile_div = 0;       // tiles of (consumer threads x R) / tile_div tracks at most
 };
 constexpr int kMaxJobs = 64;  // jobs per statistic launch (larger batches are split)
 int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st);

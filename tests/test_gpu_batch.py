@@ -186,3 +186,20 @@ class _AsResult:
 
     def __init__(self, job):
         self.stat, self.top_idx, self.top_val = job.stat, job.top_idx, job.top_val
+
+
+def test_autotuned_launch_shape(T):
+    """The tuner returns a shape that fits, later calls of that kind use it, and the results
+    stay within the parity tolerance of the oracle."""
+    torch = pytest.importorskip("torch")
+    data = _make_jobs(T, torch, SPECS[:3] + SPECS[5:6], seed=31)
+    jobs = [T.Job(d["table"], d["basis"], d["dc"], d["df"], m=d["m"], topk=d["topk"]) for d in data]
+    shape, ms = T.autotune(jobs, reps=2)
+    assert shape["pcap"] in (512, 1024, 2048, 3072, 4096) and shape["tile_div"] in (1, 2) and ms > 0
+    jobs2 = _batch(T, torch, data)
+    for d, j in zip(data, jobs2):
+        Pq, _ = d["table"].to_host()
+        S, *_ = O.eval_stat(Pq, d["U"], d["c"], d["f"], d["Tsft"], d["m"], 0)
+        assert O.stat_relative_error(j.stat.cpu().numpy().astype(np.float64), S) <= 1e-5
+    T.lib().tfs_tuning_clear()
+
