@@ -138,6 +138,33 @@ struct QHdr {
   int complete;  // every reachable centre whose window overlaps the table has its sum in Q
 };
 
+// Packed pairs of FP32 values (two tracks at once): each lane of fma/add/sub.rn.f32x2 is one
+// IEEE round-to-nearest operation, the same as the scalar instruction on that value.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2pack(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2split(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2add(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2sub(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 #ifdef TFS_DEBUG_CHECKS
 __device__ __forceinline__ bool dbg_ok(unsigned long long* dbg, bool cond, int where, long long i0, long long i1) {
   if (!cond && dbg) {
@@ -615,8 +642,29 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       // Each track is evaluated relative to a warp-uniform base bin Bw (the FP64 mid-segment bin
       // of the warp's first track): y = (x_mid - Bw) + sum_k c_k D_k,alpha in FP32, and the bin
       // is Bw + rint(y).  One base per warp keeps a register per track free.
-      float c[R][KP];
-      float y0[R], acc[R];
+      // tracks in pairs for the packed FP32x2 arithmetic (an odd R gets an inactive partner):
+      // track r is half (r & 1) of c2[r / 2][k] and y02[r / 2]
+      constexpr int R2 = (R + 1) / 2;
+      f32x2 c2[R2][KP];
+      f32x2 y02[R2];
+      float acc[R];
+#pragma unroll
+      for (int p = 0; p < R2; ++p) {
+        y02[p] = f2pack(4194303.0f, 4194303.0f);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) c2[p][k] = f2pack(0.f, 0.f);
+      }
+      // set half (r & 1) of a packed pair (r is a compile-time index after unrolling)
+      auto put = [](f32x2& v, int half, float x) {
+        float lo, hi;
+        f2split(v, lo, hi);
+        v = half ? f2pack(lo, x) : f2pack(x, hi);
+      };
+      auto get = [](f32x2 v, int half) {
+        float lo, hi;
+        f2split(v, lo, hi);
+        return half ? hi : lo;
+      };
       int Bw = 0;
       // warp-uniform decision limit: min over the warp's tracks of 1/2 - g; at most 1/2, so the
       // tracks that take the FP64 path for every pair (y = 1/2) are never decided in FP32
@@ -628,9 +676,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           acc[r] = 0.f;
-          y0[r] = 0.f;
-#pragma unroll
-          for (int k = 0; k < KP; ++k) c[r][k] = 0.f;
+          put(y02[r / 2], r & 1, 0.f);
           corr[r * kCons + ctid] = 0.f;
           tot[r * kCons + ctid] = 0.f;
           const long long t = tile0 + ctid + r * kCons;
@@ -647,9 +693,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             for (int k = 0; k < KP; ++k) {
               const double cd = (k < K) ? cp[k] : 0.0;
               if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
-              c[r][k] = (float)cd;
-              A = fmaf(fabsf(c[r][k]), J.dmax[k], A);
-              Um = fmaf(fabsf(c[r][k]), J.umax[k], Um);
+              const float cf = (float)cd;
+              put(c2[r / 2][k], r & 1, cf);
+              A = fmaf(fabsf(cf), J.dmax[k], A);
+              Um = fmaf(fabsf(cf), J.umax[k], Um);
             }
             A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
             Um *= 1.0001f;
@@ -672,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           }
           if (!active) {
             // inactive slot: c = 0 and y far from the table (|y| < 2^22), never pending
-            y0[r] = Bw >= 0 ? 4194303.0f : -4194303.0f;
+            put(y02[r / 2], r & 1, Bw >= 0 ? 4194303.0f : -4194303.0f);
             continue;
           }
           if (!exact) {
@@ -681,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             const float g = eb + 1.25f * 5.9604644775390625e-08f * (float)(K + 1) * fabsf(yf) * 1.0001f;
             exact = !(fabs(yd) < 2097152.0) || !(g < 0.25f);
             if (!exact) {
-              y0[r] = yf;
+              put(y02[r / 2], r & 1, yf);
               wlim = fminf(wlim, __fsub_rd(0.5f, g));
               const int Bd = (int)rint(xm);
               bmin = min(bmin, Bd);
@@ -691,9 +738,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           }
           if (exact) {
             // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
-            y0[r] = 0.5f;
+            put(y02[r / 2], r & 1, 0.5f);
 #pragma unroll
-            for (int k = 0; k < KP; ++k) c[r][k] = 0.f;
+            for (int k = 0; k < KP; ++k) put(c2[r / 2][k], r & 1, 0.f);
           }
         }
 #pragma unroll
@@ -706,8 +753,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             if ((inbox >> r) & 1u) {
-              lo = fminf(lo, c[r][k]);
-              hi = fmaxf(hi, c[r][k]);
+              lo = fminf(lo, get(c2[r / 2][k], r & 1));
+              hi = fmaxf(hi, get(c2[r / 2][k], r & 1));
             }
           }
 #pragma unroll
@@ -732,6 +779,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         __syncwarp();
         if (lane == 0) mbar_arrive(&tile_ready[ltile & 1]);
       }
+      const f32x2 kC2 = f2pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23 in both lanes
       // -------------------------------------------------------------- segments
       const unsigned nin = (unsigned)(J.n_bin + 2 * m);
       for (int sg = 0; sg < n_seg; ++sg) {
@@ -770,39 +818,61 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         const unsigned koff = (unsigned)Bw - 0x4B400000u - (unsigned)h.qbase;
         const unsigned kin = (unsigned)(h.qbase + m);
         const unsigned qn = (unsigned)h.qn;
+        f32x2 d2[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) d2[k] = f2pack(d[k], d[k]);
         unsigned pend = 0u;
         if (h.complete) {
           // complete band: a centre outside Q reads the 0 at q[qn]; only FP32-undecided pairs
           // are pending
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            float y = y0[r];
+          for (int p = 0; p < R2; ++p) {
+            // y for the pair (2p, 2p + 1); tt = y + 1.5 * 2^23 rounds y to an integer
+            // (|y| < 2^22); dd = y - rint(y), exact
+            f32x2 y2 = y02[p];
 #pragma unroll
-            for (int k = 0; k < KP; ++k) y = fmaf(c[r][k], d[k], y);
-            const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
-            const float dd = y - (tt - 12582912.0f);
-            const unsigned off = (unsigned)__float_as_int(tt) + koff;
-            const bool und = !(fabsf(dd) < wlim);
-            const float v = q[min(off, qn)];
-            acc[r] += und ? 0.f : v;
-            pend |= (unsigned)und << r;
-            if (BINS) {
-              const int b = (int)off + h.qbase;
-              const long long t = tile0 + ctid + r * kCons;
-              if (t < tend && !und)
-                J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+            for (int k = 0; k < KP; ++k) y2 = f2fma(c2[p][k], d2[k], y2);
+            const f32x2 tt2 = f2add(y2, kC2);
+            const f32x2 dd2 = f2sub(y2, f2sub(tt2, kC2));
+            float tts[2], dds[2];
+            f2split(tt2, tts[0], tts[1]);
+            f2split(dd2, dds[0], dds[1]);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const int r = 2 * p + hh;
+              if (r >= R) continue;
+              const float tt = tts[hh], dd = dds[hh];
+              const unsigned off = (unsigned)__float_as_int(tt) + koff;
+              const bool und = !(fabsf(dd) < wlim);
+              const float v = q[min(off, qn)];
+              acc[r] += und ? 0.f : v;
+              pend |= (unsigned)und << r;
+              if (BINS) {
+                const int b = (int)off + h.qbase;
+                const long long t = tile0 + ctid + r * kCons;
+                if (t < tend && !und)
+                  J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+              }
             }
           }
         } else {
           // incomplete band (cut to the slot, or m too wide for the pad): pairs whose window
           // overlaps the table but whose centre lies outside Q are pending too
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            float y = y0[r];
+          for (int p = 0; p < R2; ++p) {
+            f32x2 y2 = y02[p];
 #pragma unroll
-            for (int k = 0; k < KP; ++k) y = fmaf(c[r][k], d[k], y);
-            const float tt = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer (|y| < 2^22)
-            const float dd = y - (tt - 12582912.0f);
+            for (int k = 0; k < KP; ++k) y2 = f2fma(c2[p][k], d2[k], y2);
+            const f32x2 tt2 = f2add(y2, kC2);
+            const f32x2 dd2 = f2sub(y2, f2sub(tt2, kC2));
+            float tts[2], dds[2];
+            f2split(tt2, tts[0], tts[1]);
+            f2split(dd2, dds[0], dds[1]);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+            const int r = 2 * p + hh;
+            if (r >= R) continue;
+            const float tt = tts[hh], dd = dds[hh];
             const unsigned off = (unsigned)__float_as_int(tt) + koff;
             const bool und = !(fabsf(dd) < wlim);
             const bool inq = off < qn;
@@ -816,6 +886,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               const long long t = tile0 + ctid + r * kCons;
               if (t < tend && !(und || outside))
                 J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+            }
             }
           }
         }
@@ -891,7 +962,7 @@ inline int sm_count() {
   return n;
 }
 
-inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 5 : 2)); }
+inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 4 : 2)); }
 
 template <int DT, int MJ>
 int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
@@ -1016,7 +1087,7 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
   TFS_LAUNCH_KP(4, 12)
   TFS_LAUNCH_KP(6, 12)
   TFS_LAUNCH_KP(8, 9)
-  TFS_LAUNCH_KP(16, 5)
+  TFS_LAUNCH_KP(16, 4)
   TFS_LAUNCH_KP(32, 2)
 #undef TFS_LAUNCH_KP
   (void)R;
