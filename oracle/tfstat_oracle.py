@@ -19,6 +19,11 @@ What it computes, step by step, each in the plainest form:
 * ``statistic``: S~ = sum_alpha S_alpha, here with the nearest-bin reading of
   S_alpha plus an optional +-m neighbour sum (Sec. II.B, Eq. det_stat).
 * ``topk``: keep the best k tracks (Sec. II.D keeps the best 512 of 1024).
+* ``track_freqs`` / ``segment_validity`` / ``statistic_masked``: the per-segment
+  exclusions of the search: S_alpha = 0 where the track's second-order
+  evolution breaks the linear model, fddot_alpha T_SFT^3 / 6 > 1 (Sec. II.B,
+  the T_SFT discussion), and where the track's frequency is below 10^-3.5 Hz
+  or its frequency derivative below 1e-13 Hz/s (Sec. II.D).
 
 Readings where the paper is silent (window, normalisation constant, DC bin,
 rounding rule, tie band, out-of-range bins, segment times, quantised
@@ -305,6 +310,84 @@ def statistic_loop(P, b, m: int):
                     s += float(P[a][k])
         out.append(s)
     return np.array(out)
+
+
+# --------------------------------------------------------------------------
+# Segment exclusions (Sec. II.B validity cut on the second-order evolution;
+# Sec. II.D low-frequency and low-derivative exclusions)
+# --------------------------------------------------------------------------
+F_LOW_HZ = 10.0 ** -3.5    # frequencies below this contribute nothing (Sec. II.D)
+FDOT_LOW = 1e-13           # nor do frequency derivatives below this (Hz/s)
+
+
+def track_freqs(V, coeffs, f_ref):
+    """f_{t,alpha} = f_ref[t] + sum_k c[t,k] V[k,alpha] in FP64, the sum left to right with
+    each product and sum rounded separately (the order of ``track_x`` before the T_SFT factor)."""
+    V = np.asarray(V, dtype=np.float64)
+    c = np.asarray(coeffs, dtype=np.float64)
+    f = np.array(np.asarray(f_ref, dtype=np.float64)[:, None] * np.ones((1, V.shape[1])))
+    for k in range(V.shape[0]):
+        f = f + c[:, k : k + 1] * V[k][None, :]
+    return f
+
+
+def segment_validity(F, T_sft: float):
+    """valid[t, alpha]: False where a segment contributes nothing.
+
+    Readings: the derivatives come from finite differences of the track at the segment
+    midpoints (the paper takes them from the track, by numerical differentiation):
+    fdot_alpha = (f_{alpha+1} - f_{alpha-1}) / (2 T_SFT) inside, (f_1 - f_0) / T_SFT and
+    (f_{n-1} - f_{n-2}) / T_SFT at the ends, 0 for one segment; the second-order term
+    z_alpha = fddot_alpha T_SFT^3 / 6 = ((f_{alpha+1} - 2 f_alpha) + f_{alpha-1}) (T_SFT / 6)
+    inside, the nearest inner value at the ends, 0 for fewer than three segments.  A segment
+    is excluded when z > 1, or f < 10^-3.5 Hz, or fdot < 1e-13 Hz/s (either low condition
+    suffices).  Every step is one IEEE FP64 operation in the order written."""
+    F = np.asarray(F, dtype=np.float64)
+    N, n = F.shape
+    T = float(T_sft)
+    fd = np.zeros_like(F)
+    z = np.zeros_like(F)
+    if n >= 2:
+        fd[:, 1:-1] = (F[:, 2:] - F[:, :-2]) / (2.0 * T)
+        fd[:, 0] = (F[:, 1] - F[:, 0]) / T
+        fd[:, -1] = (F[:, -1] - F[:, -2]) / T
+    if n >= 3:
+        z[:, 1:-1] = ((F[:, 2:] - 2.0 * F[:, 1:-1]) + F[:, :-2]) * (T / 6.0)
+        z[:, 0] = z[:, 1]
+        z[:, -1] = z[:, -2]
+    return ~((z > 1.0) | (F < F_LOW_HZ) | (fd < FDOT_LOW))
+
+
+def statistic_masked(P, b, valid, m: int):
+    """The statistic with excluded segments contributing 0."""
+    P = np.asarray(P, dtype=np.float64)
+    n_seg, n_bin = P.shape
+    b = np.asarray(b, dtype=np.int64)
+    S = np.zeros(b.shape[0], dtype=np.float64)
+    rows = np.arange(n_seg)[None, :]
+    for j in range(-m, m + 1):
+        idx = b + j
+        ok = (idx >= 0) & (idx < n_bin) & valid
+        vals = P[rows, np.where((idx >= 0) & (idx < n_bin), idx, 0)]
+        S += np.sum(np.where(ok, vals, 0.0), axis=1)
+    return S
+
+
+def eval_stat_masked(P, V, coeffs, f_ref, T_sft: float, m: int, chunk: int = 4096):
+    """S [N] (FP64) with the segment exclusions, and the validity mask."""
+    coeffs = np.asarray(coeffs, dtype=np.float64)
+    f_ref = np.asarray(f_ref, dtype=np.float64)
+    N = coeffs.shape[0]
+    S = np.empty(N)
+    valid_all = np.empty((N, np.asarray(V).shape[1]), dtype=bool)
+    for s0 in range(0, N, chunk):
+        s1 = min(N, s0 + chunk)
+        F = track_freqs(V, coeffs[s0:s1], f_ref[s0:s1])
+        valid = segment_validity(F, T_sft)
+        b, _ = bins_and_ties(F * T_sft)
+        S[s0:s1] = statistic_masked(P, b, valid, m)
+        valid_all[s0:s1] = valid
+    return S, valid_all
 
 
 # --------------------------------------------------------------------------

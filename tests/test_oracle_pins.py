@@ -361,3 +361,88 @@ def test_injected_track_stands_out():
     S, *_ = O.eval_stat(P, V, c_true, np.zeros(1), w.T_sft, 0)
     # noise alone: mean 2 * 64 = 128, std 16; signal adds about (2/3) SNR_seg^2 per segment
     assert S[0] - 128 > 10 * 16
+
+
+# --------------------------------------------------------------------------
+# Segment exclusions (Sec. II.B second-order cut, Sec. II.D low f / low fdot)
+# --------------------------------------------------------------------------
+def _quad_tracks(a, b, c, n_seg, T):
+    """f(t) = a + b t + c t^2 / 2 at the segment midpoints, one row per (a, b, c)."""
+    t = O.segment_times(n_seg, T)
+    return a[:, None] + b[:, None] * t[None, :] + 0.5 * c[:, None] * t[None, :] ** 2, t
+
+
+def test_segment_validity_second_order_cut_closed_form():
+    """For a quadratic track the second difference is exact: z = fddot T^3 / 6 in every
+    segment (the ends take the inner value), so the cut is all or nothing at c T^3/6 = 1."""
+    T, n_seg = 5.0e4, 40
+    c_cut = 6.0 / T ** 3
+    c = np.array([0.2, 0.5, 0.9, 1.1, 1.5, 3.0]) * c_cut
+    a = np.full(c.size, 5e-3)
+    b = np.full(c.size, 1e-11)   # well above the fdot floor
+    F, t = _quad_tracks(a, b, c, n_seg, T)
+    valid = O.segment_validity(F, T)
+    expect = (c * T ** 3 / 6.0 <= 1.0)
+    assert np.array_equal(valid, np.repeat(expect[:, None], n_seg, axis=1))
+
+
+def test_segment_validity_fdot_closed_form():
+    """Central differences are exact for quadratics: fdot(t_alpha) = b + c t_alpha inside;
+    the end segments use one-sided differences, off by c T / 2."""
+    T, n_seg = 1.0e4, 30
+    a = np.array([4e-3])
+    b = np.array([-1e-13])
+    c = np.array([1e-18])          # fdot crosses 1e-13 Hz/s inside the track
+    F, t = _quad_tracks(a, b, c, n_seg, T)
+    valid = O.segment_validity(F, T)[0]
+    fd = b[0] + c[0] * t
+    fd[0] = fd[0] + c[0] * T / 2.0
+    fd[-1] = fd[-1] - c[0] * T / 2.0
+    far = np.abs(fd - 1e-13) > 1e-16
+    assert np.array_equal(valid[far], (fd >= 1e-13)[far])
+    assert (~valid).any() and valid.any()
+
+
+def test_segment_validity_low_frequency():
+    T, n_seg = 2.0e4, 20
+    f0 = np.array([2e-4, 3.1e-4, 3.2e-4, 1e-3])   # 10^-3.5 = 3.162e-4
+    F, t = _quad_tracks(f0, np.full(4, 1e-12), np.zeros(4), n_seg, T)
+    valid = O.segment_validity(F, T)
+    assert np.array_equal(valid, F >= 10.0 ** -3.5)
+    assert not valid[0].any() and valid[3].all()
+
+
+def test_segment_validity_short_tracks():
+    """One segment: no derivative (0 < 1e-13), so it is excluded; two segments: one-sided
+    differences and no second-order term."""
+    F1 = np.array([[5e-3]])
+    assert not O.segment_validity(F1, 1e4).any()
+    F2 = np.array([[5e-3, 5e-3 + 1e-8]])       # fdot = 1e-12 on both
+    assert O.segment_validity(F2, 1e4).all()
+
+
+def test_statistic_masked_reduces_to_statistic_and_loop():
+    rng = np.random.default_rng(3)
+    P = rng.exponential(2.0, (9, 40))
+    b = rng.integers(-3, 43, (25, 9))
+    ones = np.ones_like(b, dtype=bool)
+    assert np.allclose(O.statistic_masked(P, b, ones, 1), O.statistic(P, b, 1), rtol=0, atol=1e-12)
+    valid = rng.random(b.shape) < 0.6
+    loop = np.array([sum(P[a, k] for a in range(9) for k in range(b[t, a] - 2, b[t, a] + 3)
+                         if 0 <= k < 40 and valid[t, a]) for t in range(25)])
+    assert np.allclose(O.statistic_masked(P, b, valid, 2), loop, rtol=0, atol=1e-12)
+
+
+def test_eval_stat_masked_drops_only_excluded_segments():
+    """A track whose second half is past the cut scores exactly the first half's sum."""
+    T, n_seg, n_bin = 1.0e4, 16, 400
+    P = np.random.default_rng(4).exponential(2.0, (n_seg, n_bin))
+    V = np.eye(n_seg)                       # basis = the track values themselves
+    t = O.segment_times(n_seg, T)
+    f = 5e-3 + 1e-10 * t
+    f[8:] = f[8:] + 0.5 * 1e-9 * (t[8:] - t[7]) ** 2 * 1e3   # strongly curved second half
+    S, valid = O.eval_stat_masked(P, V, f[None, :], np.zeros(1), T, 0)
+    b = np.floor(f * T + 0.5).astype(int)
+    assert valid[0, :7].all() and not valid[0, 9:].all()
+    expect = sum(P[a, b[a]] for a in range(n_seg) if valid[0, a])
+    assert math.isclose(S[0], expect, rel_tol=1e-15)
