@@ -194,6 +194,14 @@ int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis, const double* 
  * and basis with equal n_seg, 0 <= N < 2^31, 0 <= m <= 64, 0 <= topk <= 1024,
  * stat [N] or NULL (then topk > 0), top_idx/top_val [min(topk, N)] when
  * topk > 0.  Ties are not reported.
+ * flags: 0, or TFS_JOB_SEGMENT_CUTS to apply the paper's segment exclusions
+ * (second-order cut Sec. II.B; low frequency and low fdot Sec. II.D): segment alpha of a track contributes 0 when, with the track's
+ * derivatives taken by finite differences at the segment midpoints
+ * (fdot = central difference / (2 T_sft) inside, one-sided at the two ends;
+ * fddot T_sft^3 / 6 = ((f[a+1] - 2 f[a]) + f[a-1]) T_sft / 6 inside, the
+ * nearest inner value at the ends), the second-order term exceeds 1, or
+ * f < 10^-3.5 Hz, or fdot < 1e-13 Hz/s.  Every exclusion is decided as the
+ * FP64 evaluation in that operation order decides it.  reserved must be 0.
  * dev_status: a device int, or NULL.  Given, the call is fully asynchronous
  * and enqueues only stream-ordered work (cudaMallocAsync scratch, kernels,
  * memsets), so it can be captured into a CUDA graph: it zeroes *dev_status,
@@ -212,7 +220,11 @@ typedef struct tfs_job {
   float* stat;          /* [N] or NULL */
   int64_t* top_idx;     /* [min(topk, N)] */
   float* top_val;       /* [min(topk, N)] */
+  int32_t flags;        /* 0 or TFS_JOB_SEGMENT_CUTS */
+  int32_t reserved;     /* 0 */
 } tfs_job;
+
+#define TFS_JOB_SEGMENT_CUTS 1
 
 int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* stream);
 

@@ -240,6 +240,7 @@ class Job:
     stat: object = None
     top_idx: object = None
     top_val: object = None
+    segment_cuts: bool = False  # TFS_JOB_SEGMENT_CUTS: the paper's segment exclusions
 
 
 def eval_batch(jobs, dev_status=None, stream=None):
@@ -269,7 +270,8 @@ def _job_array(jobs):
         arr[i] = _lib.TfsJob(j.table.handle, j.basis.handle, _ptr(j.coeffs),
                              _ptr(j.f_ref) if j.f_ref is not None else None, N, j.m, j.topk,
                              _ptr(j.stat), _ptr(j.top_idx) if j.topk else None,
-                             _ptr(j.top_val) if j.topk else None)
+                             _ptr(j.top_val) if j.topk else None,
+                             _lib.JOB_SEGMENT_CUTS if j.segment_cuts else 0, 0)
     return arr
 
 

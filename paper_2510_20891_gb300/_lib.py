@@ -77,7 +77,12 @@ class TfsJob(ctypes.Structure):
         ("stat", P),
         ("top_idx", P),
         ("top_val", P),
+        ("flags", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
+
+
+JOB_SEGMENT_CUTS = 1  # TFS_JOB_SEGMENT_CUTS
 
 ERR_NAMES = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY", -6: "NOT_FOUND"}
 

@@ -109,7 +109,12 @@ struct JobDesc {
   int n_seg, n_bin, row_stride, m, K, alpha_mid;
   int seg_resident;     // segp (and scales) copied to shared memory for this job's tiles
   int tile_tracks;      // tracks per tile (<= consumer threads * R); the last tile may hold fewer
+  const float* emax;    // [KP] segment-cut launches: max |E_k|, max |G_k| (see SegParams)
+  const float* gmax;
 };
+
+constexpr double kFLowHz = 0x1.4b96be9c2da2cp-12;  // 10^-3.5 Hz, the nearest double
+constexpr double kFdotLow = 1e-13;                 // Hz/s
 
 template <int MJ>
 struct EvalArgs {
@@ -164,6 +169,14 @@ __device__ __forceinline__ f32x2 f2sub(f32x2 a, f32x2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+// Two packed pairs (16 bytes) from shared memory.  The _v form is volatile: it is re-issued
+// at every use instead of being hoisted into registers held across the loop.
+__device__ __forceinline__ void lds_pair2(uint32_t addr, f32x2& lo, f32x2& hi) {
+  asm("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(addr));
+}
+__device__ __forceinline__ void lds_pair2_v(uint32_t addr, f32x2& lo, f32x2& hi) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(addr));
+}
 
 #ifdef TFS_DEBUG_CHECKS
 __device__ __forceinline__ bool dbg_ok(unsigned long long* dbg, bool cond, int where, long long i0, long long i1) {
@@ -204,14 +217,41 @@ __device__ __forceinline__ void report_tie(const EvalArgs<MJ>& a, long long t, i
   }
 }
 
-// FP64 bin of (track t, segment seg) of job J in the oracle's operation order,
-// and its window sum from global memory.
-template <int DT, bool BINS, int MJ>
-__device__ float exact_pair(const EvalArgs<MJ>& a, const JobDesc& J, long long t, int seg) {
-  if (!dbg_ok(a.dbg, t >= 0 && t < J.N && seg >= 0 && seg < J.n_seg, 1, t, seg)) return 0.f;
+// FP64 frequency of track t at segment seg in the oracle's operation order.
+__device__ __forceinline__ double track_freq(const JobDesc& J, long long t, int seg) {
   double f = J.f_ref ? J.f_ref[t] : 0.0;
   const double* c = J.coeffs + t * (long long)J.K;
   for (int k = 0; k < J.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], J.U[(size_t)k * J.n_seg + seg]));
+  return f;
+}
+
+// Segment exclusions of (track t, segment seg) in FP64, in the oracle's operation order
+// (finite differences of the track at the segment midpoints; see segment_validity there).
+static __device__ __noinline__ bool segment_excluded(const JobDesc& J, long long t, int seg, double f) {
+  const int n = J.n_seg;
+  const double T = J.T;
+  double fd = 0.0, z = 0.0;
+  if (n >= 2) {
+    if (seg == 0) fd = __ddiv_rn(__dsub_rn(track_freq(J, t, 1), f), T);
+    else if (seg == n - 1) fd = __ddiv_rn(__dsub_rn(f, track_freq(J, t, n - 2)), T);
+    else fd = __ddiv_rn(__dsub_rn(track_freq(J, t, seg + 1), track_freq(J, t, seg - 1)), __dmul_rn(2.0, T));
+  }
+  if (n >= 3) {
+    const int cc = seg == 0 ? 1 : (seg == n - 1 ? n - 2 : seg);
+    const double fc = cc == seg ? f : track_freq(J, t, cc);
+    const double dd = __dadd_rn(__dsub_rn(track_freq(J, t, cc + 1), __dmul_rn(2.0, fc)), track_freq(J, t, cc - 1));
+    z = __dmul_rn(dd, __ddiv_rn(T, 6.0));
+  }
+  return z > 1.0 || f < kFLowHz || fd < kFdotLow;
+}
+
+// FP64 bin of (track t, segment seg) of job J in the oracle's operation order,
+// and its window sum from global memory (0 for an excluded segment when CUTS).
+template <int DT, bool BINS, bool CUTS, int MJ>
+__device__ float exact_pair(const EvalArgs<MJ>& a, const JobDesc& J, long long t, int seg) {
+  if (!dbg_ok(a.dbg, t >= 0 && t < J.N && seg >= 0 && seg < J.n_seg, 1, t, seg)) return 0.f;
+  const double f = track_freq(J, t, seg);
+  if (CUTS && segment_excluded(J, t, seg, f)) return 0.f;
   const double x = __dmul_rn(f, J.T);
   int* bo = BINS ? J.bins_out + t * (long long)J.n_seg + seg : nullptr;
   if (!isfinite(x)) {
@@ -355,8 +395,9 @@ __device__ __forceinline__ void band_of(const float* d, const float* blo_k, cons
   *out_len = blen;
 }
 
-template <int DT, int KP, int R, bool BINS, int MJ>
+template <int DT, int KP, int R, bool BINS, bool CUTS, int MJ>
 __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_constant__ EvalArgs<MJ> a) {
+  constexpr bool kCutRegs = CUTS && KP <= 8;  // segment-cut forms held in registers
   using S = Store<DT>;
   using T = typename S::T;
   constexpr int EALIGN = 16 / S::esize;  // table elements per 16 bytes (= EPV)
@@ -603,9 +644,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
                 q[ws] = s;
               }
             }
-            if (lane < a.nsp)
-              qdseg[qs * a.nsp + lane] =
-                  reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[lane];
+            for (int i = lane; i < a.nsp; i += 32)
+              qdseg[qs * a.nsp + i] =
+                  reinterpret_cast<const float*>(src + (size_t)(kPadL + a.pcap + EALIGN) * S::esize)[i];
             __syncwarp();
             if (lane == 0) {
               q[ws_lo + qn] = 0.f;  // the sum every centre outside Q reads in the complete case
@@ -669,6 +710,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       // warp-uniform decision limit: min over the warp's tracks of 1/2 - g; at most 1/2, so the
       // tracks that take the FP64 path for every pair (y = 1/2) are never decided in FP32
       float wlim = 0.5f;
+      // segment cuts: warp-uniform margins of the second-order test (mz), the fdot test (mw)
+      // and the low-frequency test (mf, against ylo = 10^-3.5 T_SFT - Bw in bin units)
+      float mz = 0.f, mw = 0.f, mf = 0.f, ylo = 0.f;
+      unsigned cutm = 0u;  // tracks whose cuts are decided in FP32 (the others are always pending)
       int nq = 0;        // entries in this thread's fix-up queue
       if (live) {
         int bmin = 0x7fffffff, bmax = -0x7fffffff;
@@ -682,12 +727,12 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           const long long t = tile0 + ctid + r * kCons;
           const bool active = t < tend;
           double xm = 0.0;
-          float eb = 0.f;
+          float eb = 0.f, ezt = 0.f, ewt = 0.f;
           bool exact = false;
           if (active) {
             const double fr = J.f_ref ? J.f_ref[t] : 0.0;
             double f = fr;
-            float A = 0.f, Um = fabsf((float)fr);
+            float A = 0.f, Um = fabsf((float)fr), Az = 0.f, Aw = 0.f;
             const double* cp = J.coeffs + t * (long long)K;
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
@@ -697,9 +742,24 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               put(c2[r / 2][k], r & 1, cf);
               A = fmaf(fabsf(cf), J.dmax[k], A);
               Um = fmaf(fabsf(cf), J.umax[k], Um);
+              if (CUTS) {
+                Az = fmaf(fabsf(cf), J.emax[k], Az);
+                Aw = fmaf(fabsf(cf), J.gmax[k], Aw);
+              }
             }
             A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
             Um *= 1.0001f;
+            if (CUTS) {
+              // z = fddot T^3/6 and w = fdot are linear in c: z = sum_k c_k E_k, w = sum_k c_k G_k.
+              // |fp32 z - oracle z| <= 2^-24 (K+2) sum|c_k| max|E_k| (c, E and the K FMAs rounded)
+              // + (4K+40) 2^-53 Um T/6 (the oracle's rounded frequencies, its second difference
+              // and the FP64 rounding of E); |fp32 w - oracle w| likewise with G and
+              // (2K+12) 2^-53 Um / T_SFT, plus the FP32 rounding of the 1e-13 threshold
+              ezt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Az * 1.0001f +
+                             (4.f * K + 40.f) * 1.1102230246251565e-16f * Um * (float)(J.T / 6.0)) + 1e-12f;
+              ewt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Aw * 1.0001f +
+                             (2.f * K + 12.f) * 1.1102230246251565e-16f * Um / (float)J.T) + 1e-20f;
+            }
             xm = f * J.T;
             // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
             // FP32, K rounded FMAs on partial sums below |y0| + A, and the FP32 roundings of c and
@@ -730,6 +790,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             if (!exact) {
               put(y02[r / 2], r & 1, yf);
               wlim = fminf(wlim, __fsub_rd(0.5f, g));
+              if (CUTS) {
+                mz = fmaxf(mz, ezt);
+                mw = fmaxf(mw, ewt);
+              }
               const int Bd = (int)rint(xm);
               bmin = min(bmin, Bd);
               bmax = max(bmax, Bd);
@@ -745,6 +809,19 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wlim = fminf(wlim, __shfl_xor_sync(0xffffffffu, wlim, o));
+        if (CUTS) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            mz = fmaxf(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+            mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+          }
+          const double ylo64 = kFLowHz * J.T - (double)Bw;
+          ylo = (float)ylo64;
+          // 1/2 - wlim bounds |y - (f T_SFT - Bw)| for every decided track of the warp; add the
+          // roundings of ylo (FP32, and FP64 below 1e-6 for |10^-3.5 T_SFT| < 2^29)
+          mf = (0.5f - wlim) + fabsf(ylo) * 2.4e-7f + 1e-6f;
+          cutm = inbox;
+        }
         // the warp's coefficient box, one coefficient at a time (few live registers)
         float* rb = red + (ltile & 1) * kConsWarps * RW + cwarp * RW;
 #pragma unroll
@@ -791,7 +868,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           for (int i = 0; i < nq; ++i) {
             const uint32_t e = queue[i * kCons + ctid];
             const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
-            corr[r2 * kCons + ctid] += exact_pair<DT, BINS>(a, J, tile0 + ctid + r2 * kCons, s2);
+            corr[r2 * kCons + ctid] += exact_pair<DT, BINS, CUTS>(a, J, tile0 + ctid + r2 * kCons, s2);
           }
           nq = 0;
         }
@@ -821,6 +898,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         f32x2 d2[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) d2[k] = f2pack(d[k], d[k]);
+        // segment-cut forms, each stored twice (E, E, G, G per coefficient): held in registers
+        // for up to 8 coefficients, re-read from shared memory per pair above that
+        const uint32_t egs = smem_u32(qdseg + (size_t)qs * a.nsp + cut_col(KP));
+        f32x2 e2[kCutRegs ? KP : 1], g2[kCutRegs ? KP : 1];
+        if (kCutRegs) {
+#pragma unroll
+          for (int k = 0; k < KP; ++k) lds_pair2(egs + 16u * k, e2[k], g2[k]);
+        }
         unsigned pend = 0u;
         if (h.complete) {
           // complete band: a centre outside Q reads the 0 at q[qn]; only FP32-undecided pairs
@@ -837,15 +922,42 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             float tts[2], dds[2];
             f2split(tt2, tts[0], tts[1]);
             f2split(dd2, dds[0], dds[1]);
+            float ys[2], zs[2], ws[2];
+            if (CUTS) {
+              f32x2 z2 = f2pack(0.f, 0.f), w2 = f2pack(0.f, 0.f);
+#pragma unroll
+              for (int k = 0; k < KP; ++k) {
+                f32x2 ek, gk;
+                if (kCutRegs) {
+                  ek = e2[k];
+                  gk = g2[k];
+                } else {
+                  lds_pair2_v(egs + 16u * k, ek, gk);
+                }
+                z2 = f2fma(c2[p][k], ek, z2);
+                w2 = f2fma(c2[p][k], gk, w2);
+              }
+              f2split(y2, ys[0], ys[1]);
+              f2split(z2, zs[0], zs[1]);
+              f2split(w2, ws[0], ws[1]);
+            }
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
               const int r = 2 * p + hh;
               if (r >= R) continue;
               const float tt = tts[hh], dd = dds[hh];
               const unsigned off = (unsigned)__float_as_int(tt) + koff;
-              const bool und = !(fabsf(dd) < wlim);
+              bool und = !(fabsf(dd) < wlim);
+              bool excl = false;
+              if (CUTS) {
+                // excluded segment (decided in FP32), or a cut too close to call: FP64 path
+                const float zc = zs[hh] - 1.f, wc = ws[hh] - 1e-13f, fc = ys[hh] - ylo;
+                excl = zc > 0.f || wc < 0.f || fc < 0.f;
+                und = und || (((cutm >> r) & 1u) &&
+                              (!(fabsf(zc) > mz) || !(fabsf(wc) > mw) || !(fabsf(fc) > mf)));
+              }
               const float v = q[min(off, qn)];
-              acc[r] += und ? 0.f : v;
+              acc[r] += (und || excl) ? 0.f : v;
               pend |= (unsigned)und << r;
               if (BINS) {
                 const int b = (int)off + h.qbase;
@@ -868,17 +980,43 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             float tts[2], dds[2];
             f2split(tt2, tts[0], tts[1]);
             f2split(dd2, dds[0], dds[1]);
+            float ys[2], zs[2], ws[2];
+            if (CUTS) {
+              f32x2 z2 = f2pack(0.f, 0.f), w2 = f2pack(0.f, 0.f);
+#pragma unroll
+              for (int k = 0; k < KP; ++k) {
+                f32x2 ek, gk;
+                if (kCutRegs) {
+                  ek = e2[k];
+                  gk = g2[k];
+                } else {
+                  lds_pair2_v(egs + 16u * k, ek, gk);
+                }
+                z2 = f2fma(c2[p][k], ek, z2);
+                w2 = f2fma(c2[p][k], gk, w2);
+              }
+              f2split(y2, ys[0], ys[1]);
+              f2split(z2, zs[0], zs[1]);
+              f2split(w2, ws[0], ws[1]);
+            }
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
             const int r = 2 * p + hh;
             if (r >= R) continue;
             const float tt = tts[hh], dd = dds[hh];
             const unsigned off = (unsigned)__float_as_int(tt) + koff;
-            const bool und = !(fabsf(dd) < wlim);
+            bool und = !(fabsf(dd) < wlim);
+            bool excl = false;
+            if (CUTS) {
+              const float zc = zs[hh] - 1.f, wc = ws[hh] - 1e-13f, fc = ys[hh] - ylo;
+              excl = zc > 0.f || wc < 0.f || fc < 0.f;
+              und = und || (((cutm >> r) & 1u) &&
+                            (!(fabsf(zc) > mz) || !(fabsf(wc) > mw) || !(fabsf(fc) > mf)));
+            }
             const bool inq = off < qn;
-            const bool outside = !inq && off + kin < nin;
+            const bool outside = !inq && off + kin < nin && !excl;
             pend |= (unsigned)(und || outside) << r;
-            const bool use = inq && !und;
+            const bool use = inq && !und && !excl;
             const float v = q[use ? off : 0u];  // the address is always valid
             acc[r] += use ? v : 0.f;
             if (BINS) {
@@ -913,7 +1051,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         for (int i = 0; i < nq; ++i) {
           const uint32_t e = queue[i * kCons + ctid];
           const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
-          corr[r2 * kCons + ctid] += exact_pair<DT, BINS>(a, J, tile0 + ctid + r2 * kCons, s2);
+          corr[r2 * kCons + ctid] += exact_pair<DT, BINS, CUTS>(a, J, tile0 + ctid + r2 * kCons, s2);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -935,9 +1073,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 }
 
 // ---------------------------------------------------------------- host side
-template <int DT, int KP, int R, bool BINS, int MJ>
+template <int DT, int KP, int R, bool BINS, bool CUTS, int MJ>
 int launch_one(const EvalArgs<MJ>& a0, int grid, size_t smem, cudaStream_t st) {
-  auto kern = eval_stat_kernel<DT, KP, R, BINS, MJ>;
+  auto kern = eval_stat_kernel<DT, KP, R, BINS, CUTS, MJ>;
   static int configured = -1;
   if (configured < (int)smem) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -963,6 +1101,8 @@ inline int sm_count() {
 }
 
 inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 4 : 2)); }
+// with segment cuts each track also carries the two cut forms: fewer tracks per thread
+inline int r_of_kp_cuts(int KP) { return KP <= 6 ? 8 : (KP <= 8 ? 6 : 2); }
 
 template <int DT, int MJ>
 int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st) {
@@ -970,8 +1110,9 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
   constexpr int EPV = 16 / esize;
   int KP = 0;
   for (int i = 0; i < L.n_jobs; ++i) KP = std::max(KP, L.jobs[i].sp->KP);
-  const int R = r_of_kp(KP);
-  const int nsp = ((KP + 3) / 4) * 4;
+  const bool cuts = L.jobs[0].cuts != 0;
+  const int R = cuts ? r_of_kp_cuts(KP) : r_of_kp(KP);
+  const int nsp = segrow_floats(KP, cuts);
 
   EvalArgs<MJ> a{};
   a.tie_count = L.tie_count;
@@ -1011,6 +1152,12 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     D.m = E.m;
     D.K = E.basis->K;
     D.alpha_mid = E.sp->alpha_mid;
+    D.emax = E.sp->emax;
+    D.gmax = E.sp->gmax;
+    if ((E.cuts != 0) != cuts || (cuts && !E.sp->cuts)) {
+      set_error("internal: jobs with and without segment cuts in one launch");
+      return TFS_ERR_INVALID_ARG;
+    }
     // tiles of equal size; a single job gets a whole number of rounds over the SMs (or, when
     // small, one tile per SM), so that no round runs on a few SMs alone
     long long ntj = (E.N + tile - 1) / tile;
@@ -1076,19 +1223,20 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
   }
   const int grid = (int)std::min<long long>(nt, (long long)sm_count());
 
-#define TFS_LAUNCH_KP(KPV, RV)                                                          \
+#define TFS_LAUNCH_KP(KPV, RV, RCV)                                                     \
   if (KP == KPV) {                                                                      \
+    if (cuts) return launch_one<DT, KPV, RCV, false, true, MJ>(a, grid, smem, st);       \
     if constexpr (MJ == 1) {                                                            \
-      if (bins) return launch_one<DT, KPV, RV, true, MJ>(a, grid, smem, st);            \
+      if (bins) return launch_one<DT, KPV, RV, true, false, MJ>(a, grid, smem, st);     \
     }                                                                                   \
-    return launch_one<DT, KPV, RV, false, MJ>(a, grid, smem, st);                        \
+    return launch_one<DT, KPV, RV, false, false, MJ>(a, grid, smem, st);                 \
   }
-  TFS_LAUNCH_KP(2, 12)
-  TFS_LAUNCH_KP(4, 12)
-  TFS_LAUNCH_KP(6, 12)
-  TFS_LAUNCH_KP(8, 9)
-  TFS_LAUNCH_KP(16, 4)
-  TFS_LAUNCH_KP(32, 2)
+  TFS_LAUNCH_KP(2, 12, 8)
+  TFS_LAUNCH_KP(4, 12, 8)
+  TFS_LAUNCH_KP(6, 12, 8)
+  TFS_LAUNCH_KP(8, 9, 6)
+  TFS_LAUNCH_KP(16, 4, 2)
+  TFS_LAUNCH_KP(32, 2, 2)
 #undef TFS_LAUNCH_KP
   (void)R;
   set_error("unsupported coefficient slot count %d", KP);

@@ -107,6 +107,57 @@ __global__ void segparams_kernel(const double* __restrict__ U, int K, int KP, in
   }
 }
 
+// Segment-cut forms per (k, alpha): E = (T/6) x the second difference of U_k (the nearest
+// inner value at the ends, 0 below three segments) and G = the first difference of U_k over
+// the segment spacing (central inside, one-sided at the ends, 0 for one segment), both
+// computed in FP64 and stored in FP32 at columns KP + k and 2 KP + k; max |E|, max |G| per k.
+__global__ void cutparams_kernel(const double* __restrict__ U, int K, int KP, int n_seg, int nsp, double T,
+                                 float* __restrict__ segp, float* __restrict__ emax, float* __restrict__ gmax) {
+  const int k = blockIdx.x;
+  __shared__ float se[32], sg[32];
+  float me = 0.f, mg = 0.f;
+  const double* u = U + (size_t)k * n_seg;
+  for (int a = threadIdx.x; a < n_seg; a += blockDim.x) {
+    double e = 0.0, g = 0.0;
+    if (k < K) {
+      if (n_seg >= 3) {
+        const int c = a == 0 ? 1 : (a == n_seg - 1 ? n_seg - 2 : a);
+        e = __dmul_rn(__dadd_rn(__dsub_rn(u[c + 1], __dmul_rn(2.0, u[c])), u[c - 1]), T / 6.0);
+      }
+      if (n_seg >= 2) {
+        if (a == 0) g = __dsub_rn(u[1], u[0]) / T;
+        else if (a == n_seg - 1) g = __dsub_rn(u[n_seg - 1], u[n_seg - 2]) / T;
+        else g = __dsub_rn(u[a + 1], u[a - 1]) / (2.0 * T);
+      }
+    }
+    const float ef = (float)e, gf = (float)g;
+    float* row = segp + (size_t)a * nsp + cut_col(KP) + 4 * k;
+    row[0] = ef;
+    row[1] = ef;
+    row[2] = gf;
+    row[3] = gf;
+    me = fmaxf(me, fabsf(ef));
+    mg = fmaxf(mg, fabsf(gf));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+    mg = fmaxf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    se[threadIdx.x >> 5] = me;
+    sg[threadIdx.x >> 5] = mg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      me = fmaxf(me, se[w]);
+      mg = fmaxf(mg, sg[w]);
+    }
+    emax[k] = me * (1.0f + 1.0f / 1048576.0f);
+    gmax[k] = mg * (1.0f + 1.0f / 1048576.0f);
+  }
+}
+
 int pick_kp(int K) {
   const int opts[] = {2, 4, 6, 8, 16, 32};
   for (int v : opts)
@@ -119,22 +170,26 @@ static void free_segparams(SegParams* s) {
   if (s->segp) cudaFree(s->segp);
   if (s->dmax) cudaFree(s->dmax);
   if (s->umax) cudaFree(s->umax);
+  if (s->emax) cudaFree(s->emax);
+  if (s->gmax) cudaFree(s->gmax);
   delete s;
 }
 
-int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams** out) {
+int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams** out, int cuts) {
   std::lock_guard<std::mutex> lk(b->mu);
   const int KP = pick_kp(std::max(b->K, kp_min));
   TFS_CHECK(KP > 0, TFS_ERR_INVALID_ARG, "basis size K=%d exceeds 32", std::max(b->K, kp_min));
+  cuts = cuts ? 1 : 0;
   for (SegParams* s : b->sps)
-    if (s->T == T && s->KP == KP) {
+    if (s->T == T && s->KP == KP && s->cuts == cuts) {
       *out = s;
       return TFS_OK;
     }
   SegParams* s = new SegParams();
   s->T = T;
   s->KP = KP;
-  s->nsp = ((KP + 3) / 4) * 4;
+  s->cuts = cuts;
+  s->nsp = segrow_floats(KP, cuts != 0);
   s->alpha_mid = (int)(b->n_seg / 2);
   cudaError_t e = cudaMalloc(&s->segp, (size_t)b->n_seg * s->nsp * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->dmax, 32 * sizeof(float));
@@ -145,6 +200,15 @@ int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams
                                          s->dmax, s->umax);
     count_launch();
     e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && cuts) {
+    e = cudaMalloc(&s->emax, 32 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->gmax, 32 * sizeof(float));
+    if (e == cudaSuccess) {
+      cutparams_kernel<<<KP, 256, 0, st>>>(b->U, b->K, KP, (int)b->n_seg, s->nsp, T, s->segp, s->emax, s->gmax);
+      count_launch();
+      e = cudaGetLastError();
+    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // one-off per (basis, T, KP): later calls may use other streams
   if (e != cudaSuccess) {
@@ -183,7 +247,9 @@ static std::string launch_key(const EvalLaunch& L) {
     row_max = std::max<int64_t>(row_max, L.jobs[i].table->row_stride);
     seg_max = std::max<int64_t>(seg_max, L.jobs[i].table->n_seg);
   }
-  return tuning_key(L.jobs[0].table->dtype, KP, row_max, seg_max, L.n_jobs > 1);
+  std::string k = tuning_key(L.jobs[0].table->dtype, KP, row_max, seg_max, L.n_jobs > 1);
+  if (L.jobs[0].cuts) k += ":c";
+  return k;
 }
 
 static std::vector<std::string> g_last_keys;  // keys of the launches of the last tfs_eval_batch (tuner only)
@@ -514,18 +580,21 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
     TFS_CHECK(j.topk == 0 || j.N == 0 || (j.top_idx && j.top_val), TFS_ERR_INVALID_ARG, "job %d: null top-k outputs",
               i);
     TFS_CHECK(pick_kp(j.basis->K) > 0, TFS_ERR_INVALID_ARG, "job %d: basis size exceeds 32", i);
+    TFS_CHECK((j.flags & ~TFS_JOB_SEGMENT_CUTS) == 0 && j.reserved == 0, TFS_ERR_INVALID_ARG,
+              "job %d: unknown flags or nonzero reserved field", i);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // one launch per table dtype, with the widest coefficient slot count among its jobs
-  int kp_of[4] = {0, 0, 0, 0};
+  // one launch per (table dtype, segment cuts), with the widest coefficient slot count among its jobs
+  int kp_of[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  auto cut_of = [&](int i) { return (jobs[i].flags & TFS_JOB_SEGMENT_CUTS) ? 1 : 0; };
   for (int i = 0; i < n_jobs; ++i) {
-    int& kp = kp_of[jobs[i].table->dtype];
+    int& kp = kp_of[jobs[i].table->dtype][cut_of(i)];
     kp = std::max(kp, pick_kp(jobs[i].basis->K));
   }
   std::vector<SegParams*> sps(n_jobs);
   for (int i = 0; i < n_jobs; ++i) {
     int rc = get_segparams(const_cast<tfs_basis*>(jobs[i].basis), jobs[i].table->T_sft,
-                           kp_of[jobs[i].table->dtype], st, &sps[i]);
+                           kp_of[jobs[i].table->dtype][cut_of(i)], st, &sps[i], cut_of(i));
     if (rc) return rc;
   }
   size_t need = round256(8) + round256(4) + round256(8) + round256(4);
@@ -547,7 +616,7 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
   for (int i = 0; i < n_jobs; ++i) {
     const tfs_job& j = jobs[i];
     float* stat = j.stat ? j.stat : ar.take<float>((size_t)j.N);
-    ej[i] = EvalJob{j.table, j.basis, sps[i], j.coeffs, j.f_ref, j.N, j.m, stat, nullptr};
+    ej[i] = EvalJob{j.table, j.basis, sps[i], j.coeffs, j.f_ref, j.N, j.m, stat, nullptr, cut_of(i)};
   }
   TFS_CUDA(cudaMemsetAsync(d_tc, 0, 8, st));
   TFS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
@@ -556,11 +625,12 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
   TFS_CUDA(cudaMallocAsync((void**)&d_dbg, 32, st));
   TFS_CUDA(cudaMemsetAsync(d_dbg, 0, 32, st));
 #endif
-  for (int dt = 0; dt < 4; ++dt) {
-    if (!kp_of[dt]) continue;
+  for (int g = 0; g < 8; ++g) {
+    const int dt = g >> 1, cu = g & 1;
+    if (!kp_of[dt][cu]) continue;
     std::vector<EvalJob> group;
     for (int i = 0; i < n_jobs; ++i)
-      if (jobs[i].table->dtype == dt && jobs[i].N > 0) group.push_back(ej[i]);
+      if (jobs[i].table->dtype == dt && cut_of(i) == cu && jobs[i].N > 0) group.push_back(ej[i]);
     for (size_t g0 = 0; g0 < group.size(); g0 += kMaxJobs) {
       const int n = (int)std::min<size_t>(kMaxJobs, group.size() - g0);
       EvalLaunch L{group.data() + g0, n, d_tc, d_tt, d_ts, 0, d_status, d_dbg};

@@ -43,14 +43,23 @@ void count_launch(int n = 1);
 void free_sft_plan(void* p);
 
 // ---------------------------------------------------------------- handles
+// Floats per segment row of segp, and the first column of the segment-cut forms (16-byte aligned).
+__host__ __device__ constexpr int cut_col(int KP) { return ((KP + 3) / 4) * 4; }
+inline int segrow_floats(int KP, bool cuts) { return cut_col(KP) + (cuts ? 4 * KP : 0); }
+
 struct SegParams {          // per (basis, T_sft) data for the FP32 filter of the track evaluation
   double T = 0.0;
   int KP = 0;               // coefficient slots in the kernel (>= K, zero padded)
   int nsp = 0;              // floats per segment row of `segp` (multiple of 4, >= KP)
   int alpha_mid = 0;
-  float* segp = nullptr;    // device [n_seg][nsp]: D_k,alpha = fl32(T U_k,alpha - T U_k,mid)
+  float* segp = nullptr;    // device [n_seg][nsp]: D_k,alpha = fl32(T U_k,alpha - T U_k,mid) at k;
+                            // with cuts also E, E, G, G (each of E_k,alpha and G_k,alpha twice,
+                            // the operand pair of a packed two-track FMA) from cut_col(KP) + 4k
   float* dmax = nullptr;    // device [KP]: max_alpha |D_k,alpha| (rounded up)
   float* umax = nullptr;    // device [KP]: max_alpha |U_k,alpha| (rounded up)
+  int cuts = 0;             // rows carry the segment-cut forms E (second difference) and G (first)
+  float* emax = nullptr;    // device [KP]: max_alpha |E_k,alpha| (rounded up), cuts only
+  float* gmax = nullptr;    // device [KP]: max_alpha |G_k,alpha| (rounded up), cuts only
 };
 
 }  // namespace tfs
@@ -83,7 +92,7 @@ inline int esize_of(int dtype) { return dtype == TFS_F32 ? 4 : (dtype == TFS_F8E
 
 // Cached FP32 filter parameters of a basis for a given T_sft, with at least kp_min coefficient
 // slots (built on first use; rebuilt for another T_sft or a wider slot count).
-int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams** out);
+int get_segparams(tfs_basis* b, double T, int kp_min, cudaStream_t st, SegParams** out, int cuts = 0);
 int pick_kp(int K);
 
 // ---------------------------------------------------------------- kernels (host launchers)
@@ -97,6 +106,7 @@ struct EvalJob {          // one dataset's part of a statistic launch
   int m;
   float* stat;            // device [N]
   int* bins_out = nullptr;  // device [N][n_seg] or null: the bin of every pair (verification only)
+  int cuts = 0;           // apply the segment exclusions (TFS_JOB_SEGMENT_CUTS)
 };
 struct EvalLaunch {
   const EvalJob* jobs;    // host array

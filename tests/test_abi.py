@@ -108,7 +108,8 @@ def test_server_stats_struct_matches_the_header():
 
 def test_job_struct_matches_the_header():
     """struct tfs_job: 8-byte fields except m and topk (int32 each), no padding."""
-    assert ctypes.sizeof(_lib.TfsJob) == 9 * 8
+    assert ctypes.sizeof(_lib.TfsJob) == 10 * 8
+    assert _lib.TfsJob.flags.offset == 72 and _lib.TfsJob.reserved.offset == 76
     assert _lib.TfsJob.m.offset == 40 and _lib.TfsJob.topk.offset == 44 and _lib.TfsJob.stat.offset == 48
 
 
