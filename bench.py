@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--stat-error", type=int, default=0,
                     help="also report the statistic's error against the FP64 oracle on the exact table, "
                          "over this many sampled tracks")
+    ap.add_argument("--segment-cuts", action="store_true",
+                    help="apply the segment exclusions (second-order, low-frequency and low-fdot cuts)")
     ap.add_argument("--batch-jobs", type=int, default=64, help="datasets of the batched workload")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default launch shape")
     ap.add_argument("--requests", type=int, default=1000, help="requests of the served workload")
@@ -158,14 +160,17 @@ class ClockSampler:
 _W = {}
 
 
-def _oracle_init(P, V, T_sft, m):
-    _W.update(P=P, V=V, T=T_sft, m=m)
+def _oracle_init(P, V, T_sft, m, cuts=False):
+    _W.update(P=P, V=V, T=T_sft, m=m, cuts=cuts)
 
 
 def _oracle_chunk(coeffs):
     import oracle.tfstat_oracle as O
 
-    S, *_ = O.eval_stat(_W["P"], _W["V"], coeffs, np.zeros(len(coeffs)), _W["T"], _W["m"], 0)
+    if _W["cuts"]:
+        S, _ = O.eval_stat_masked(_W["P"], _W["V"], coeffs, np.zeros(len(coeffs)), _W["T"], _W["m"])
+    else:
+        S, *_ = O.eval_stat(_W["P"], _W["V"], coeffs, np.zeros(len(coeffs)), _W["T"], _W["m"], 0)
     return float(S.sum())
 
 
@@ -174,12 +179,13 @@ class OracleArm:
     (one process) plus its statistic of a sample of tracks split over a spawn pool;
     the rate is the batch's tracks over (SFT time + batch x per-track time)."""
 
-    def __init__(self, x, psd, w, V, ncores):
+    def __init__(self, x, psd, w, V, ncores, cuts=False):
         import oracle.tfstat_oracle as O
 
         self.O, self.x, self.psd, self.w, self.V, self.ncores = O, x, psd, w, V, ncores
         P = O.power_table(x, w.dt, w.T_sft, psd)
-        self.pool = mp.get_context("spawn").Pool(ncores, initializer=_oracle_init, initargs=(P, V, w.T_sft, w.m))
+        self.pool = mp.get_context("spawn").Pool(ncores, initializer=_oracle_init,
+                                                 initargs=(P, V, w.T_sft, w.m, cuts))
         self.pool.map(_oracle_chunk, [np.zeros((1, V.shape[0]))] * ncores)   # warm the workers
 
     def step(self, coeffs):
@@ -271,6 +277,18 @@ def run_ours(args):
     kk = min(args.topk, N)
     top_i = torch.empty(kk, dtype=torch.int64, device="cuda")
     top_v = torch.empty(kk, dtype=torch.float32, device="cuda")
+    cut_job = None
+    if args.segment_cuts:
+        # the exclusions are a flag of the batched entry point: one job, asynchronous
+        cut_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cut_job = T.Job(table, basis, coeffs_d, None, m=w.m, stat=stat, segment_cuts=True)
+
+    def eval_call():
+        if cut_job is None:
+            T.check(L.tfs_eval_stat(table.handle, basis.handle, coeffs_d.data_ptr(), None, N, w.m, 0,
+                                    stat.data_ptr(), None, None, None, 1, sp))
+        else:
+            T.eval_batch([cut_job], dev_status=cut_status, stream=stream.cuda_stream)
 
     def step(evs=None):
         if evs is not None:
@@ -278,8 +296,7 @@ def run_ours(args):
         T.check(L.tfs_table_rebuild(table.handle, x_d.data_ptr(), x_d.numel(), 1, sp))
         if evs is not None:
             evs[1].record(stream)
-        T.check(L.tfs_eval_stat(table.handle, basis.handle, coeffs_d.data_ptr(), None, N, w.m, 0,
-                                stat.data_ptr(), None, None, None, 1, sp))
+        eval_call()
         if evs is not None:
             evs[2].record(stream)
         T.check(L.tfs_topk(stat.data_ptr(), N, kk, top_i.data_ptr(), top_v.data_ptr(), 1, sp))
@@ -307,6 +324,8 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches = L.tfs_kernel_launches() - launches0
+    if cut_job is not None:
+        assert int(cut_status.item()) == 0, "a bounded device wait gave up"
     total_ms = start.elapsed_time(end)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -324,10 +343,21 @@ def run_ours(args):
     e_top_i = np.empty(kk, np.int64)
     e_top_v = np.empty(kk, np.float32)
 
+    if cut_job is not None:
+        c_e2e = torch.empty_like(coeffs_d)
+        e2e_job = T.Job(table, basis, c_e2e, None, m=w.m, topk=kk, stat=stat, segment_cuts=True)
+
     def e2e_step():
         T.check(L.tfs_table_rebuild(table.handle, x_pin.data_ptr(), x_pin.numel(), 0, None))
-        T.check(L.tfs_eval_stat(table.handle, basis.handle, c_pin.data_ptr(), None, N, w.m, kk, None,
-                                e_top_i.ctypes.data, e_top_v.ctypes.data, None, 0, None))
+        if cut_job is None:
+            T.check(L.tfs_eval_stat(table.handle, basis.handle, c_pin.data_ptr(), None, N, w.m, kk, None,
+                                    e_top_i.ctypes.data, e_top_v.ctypes.data, None, 0, None))
+        else:
+            # host coefficients uploaded on the stream, the batched entry point, top-k read back
+            c_e2e.copy_(c_pin, non_blocking=True)
+            T.eval_batch([e2e_job], stream=stream.cuda_stream)
+            e_top_i[:] = e2e_job.top_idx.cpu().numpy()
+            e_top_v[:] = e2e_job.top_val.cpu().numpy()
 
     e2e_step()
     if world > 1:
@@ -353,7 +383,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = min(args.cpu_sample, N)
-        arm = OracleArm(x, psd, w, U, ncores)
+        arm = OracleArm(x, psd, w, U, ncores, cuts=args.segment_cuts)
         t_sft, t_eval = arm.step(coeffs_h[:sample])
         arm.close()
         cpu_val = N / (t_sft + N * (t_eval / sample))
@@ -366,13 +396,17 @@ def run_ours(args):
 
         n_s = min(args.stat_error, N)
         P64 = O.power_table(x, w.dt, w.T_sft, psd)
-        T.check(L.tfs_eval_stat(table.handle, basis.handle, coeffs_d.data_ptr(), None, N, w.m, 0,
-                                stat.data_ptr(), None, None, None, 1, sp))
+        eval_call()
         got = stat[:n_s].double().cpu().numpy()
-        ref, *_ = O.eval_stat(P64, U, coeffs_h[:n_s], np.zeros(n_s), w.T_sft, w.m, 0)
-        rel = np.abs(got - ref) / np.abs(ref)
+        if cut_job is None:
+            ref, *_ = O.eval_stat(P64, U, coeffs_h[:n_s], np.zeros(n_s), w.T_sft, w.m, 0)
+        else:
+            ref, valid = O.eval_stat_masked(P64, U, coeffs_h[:n_s], np.zeros(n_s), w.T_sft, w.m)
+        rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
         stat_err = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "tracks": n_s,
                     "against": "FP64 oracle statistic of the exact FP64 table (no quantisation)"}
+        if cut_job is not None:
+            stat_err["excluded_fraction"] = float(1.0 - valid.mean())
     if rank != 0:
         return
     clocks = clk.summary()
@@ -381,6 +415,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": args.workload, "tracks_per_rank": N, "n_seg": w.n_seg, "n_bin": w.n_bin,
                        "K": w.K, "m": w.m, "topk": kk, "table_dtype": args.dtype,
+                       "segment_cuts": bool(args.segment_cuts),
                        "l2": "inputs larger than L2 (coefficients %.0f MB per step); the table itself is reused "
                              "from L2 within a step" % (coeffs_h.nbytes / 1e6),
                        "parallelism": f"tracks sharded over {world} GPU(s)"},

@@ -177,6 +177,11 @@ __device__ __forceinline__ void lds_pair2(uint32_t addr, f32x2& lo, f32x2& hi) {
 __device__ __forceinline__ void lds_pair2_v(uint32_t addr, f32x2& lo, f32x2& hi) {
   asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(addr));
 }
+__device__ __forceinline__ f32x2 lds_pair_v(uint32_t addr) {
+  f32x2 v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
 
 #ifdef TFS_DEBUG_CHECKS
 __device__ __forceinline__ bool dbg_ok(unsigned long long* dbg, bool cond, int where, long long i0, long long i1) {
@@ -713,7 +718,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       // segment cuts: warp-uniform margins of the second-order test (mz), the fdot test (mw)
       // and the low-frequency test (mf, against ylo = 10^-3.5 T_SFT - Bw in bin units)
       float mz = 0.f, mw = 0.f, mf = 0.f, ylo = 0.f;
+      // ... as thresholds: included below zin / above win, fin; excluded above zex / below wex, fex
+      float zin = 0.f, zex = 0.f, win = 0.f, wex = 0.f, fin = 0.f, fex = 0.f;
       unsigned cutm = 0u;  // tracks whose cuts are decided in FP32 (the others are always pending)
+      bool zt = false;     // some track of the warp may reach the second-order cut
       int nq = 0;        // entries in this thread's fix-up queue
       if (live) {
         int bmin = 0x7fffffff, bmax = -0x7fffffff;
@@ -727,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           const long long t = tile0 + ctid + r * kCons;
           const bool active = t < tend;
           double xm = 0.0;
-          float eb = 0.f, ezt = 0.f, ewt = 0.f;
+          float eb = 0.f, ezt = 0.f, ewt = 0.f, zbt = 0.f;
           bool exact = false;
           if (active) {
             const double fr = J.f_ref ? J.f_ref[t] : 0.0;
@@ -759,6 +767,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
                              (4.f * K + 40.f) * 1.1102230246251565e-16f * Um * (float)(J.T / 6.0)) + 1e-12f;
               ewt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Aw * 1.0001f +
                              (2.f * K + 12.f) * 1.1102230246251565e-16f * Um / (float)J.T) + 1e-20f;
+              zbt = Az * 1.0001f + ezt;  // bounds |oracle z| in every segment
             }
             xm = f * J.T;
             // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
@@ -793,6 +802,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               if (CUTS) {
                 mz = fmaxf(mz, ezt);
                 mw = fmaxf(mw, ewt);
+                zt = zt || !(zbt < 1.f);
               }
               const int Bd = (int)rint(xm);
               bmin = min(bmin, Bd);
@@ -821,6 +831,13 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           // roundings of ylo (FP32, and FP64 below 1e-6 for |10^-3.5 T_SFT| < 2^29)
           mf = (0.5f - wlim) + fabsf(ylo) * 2.4e-7f + 1e-6f;
           cutm = inbox;
+          zt = __any_sync(0xffffffffu, zt);
+          zin = __fsub_rd(1.f, mz);
+          zex = __fadd_ru(1.f, mz);
+          win = __fadd_ru(1e-13f, mw);
+          wex = __fsub_rd(1e-13f, mw);
+          fin = __fadd_ru(ylo, mf);
+          fex = __fsub_rd(ylo, mf);
         }
         // the warp's coefficient box, one coefficient at a time (few live registers)
         float* rb = red + (ltile & 1) * kConsWarps * RW + cwarp * RW;
@@ -898,18 +915,24 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         f32x2 d2[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) d2[k] = f2pack(d[k], d[k]);
-        // segment-cut forms, each stored twice (E, E, G, G per coefficient): held in registers
-        // for up to 8 coefficients, re-read from shared memory per pair above that
+        // segment-cut forms, each stored twice (E, E, G, G per coefficient): G held in registers
+        // for up to 8 coefficients; E (used only when a track of the warp may reach the
+        // second-order cut), and G above 8 coefficients, re-read from shared memory per pair
         const uint32_t egs = smem_u32(qdseg + (size_t)qs * a.nsp + cut_col(KP));
-        f32x2 e2[kCutRegs ? KP : 1], g2[kCutRegs ? KP : 1];
+        f32x2 g2[kCutRegs ? KP : 1];
         if (kCutRegs) {
 #pragma unroll
-          for (int k = 0; k < KP; ++k) lds_pair2(egs + 16u * k, e2[k], g2[k]);
+          for (int k = 0; k < KP; ++k) g2[k] = lds_pair_v(egs + 16u * k + 8u);
         }
         unsigned pend = 0u;
-        if (h.complete) {
-          // complete band: a centre outside Q reads the 0 at q[qn]; only FP32-undecided pairs
-          // are pending
+        // one straight-line pass over the track pairs.  COMPLETE: the band holds every reachable
+        // centre (a centre outside Q reads the 0 at q[qn]; only FP32-undecided pairs are
+        // pending); otherwise pairs whose window overlaps the table but whose centre lies outside
+        // Q are pending too.  ZT: evaluate the second-order cut (off when no track of the warp
+        // can reach it).
+        auto pairs = [&](auto complete_c, auto zt_c) {
+          constexpr bool COMPLETE = decltype(complete_c)::value;
+          constexpr bool ZT = CUTS && decltype(zt_c)::value;
 #pragma unroll
           for (int p = 0; p < R2; ++p) {
             // y for the pair (2p, 2p + 1); tt = y + 1.5 * 2^23 rounds y to an integer
@@ -919,22 +942,23 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             for (int k = 0; k < KP; ++k) y2 = f2fma(c2[p][k], d2[k], y2);
             const f32x2 tt2 = f2add(y2, kC2);
             const f32x2 dd2 = f2sub(y2, f2sub(tt2, kC2));
-            float tts[2], dds[2];
+            float tts[2], dds[2], ys[2], zs[2], ws[2];
             f2split(tt2, tts[0], tts[1]);
             f2split(dd2, dds[0], dds[1]);
-            float ys[2], zs[2], ws[2];
             if (CUTS) {
               f32x2 z2 = f2pack(0.f, 0.f), w2 = f2pack(0.f, 0.f);
 #pragma unroll
               for (int k = 0; k < KP; ++k) {
                 f32x2 ek, gk;
                 if (kCutRegs) {
-                  ek = e2[k];
                   gk = g2[k];
-                } else {
+                  if (ZT) ek = lds_pair_v(egs + 16u * k);
+                } else if (ZT) {
                   lds_pair2_v(egs + 16u * k, ek, gk);
+                } else {
+                  gk = lds_pair_v(egs + 16u * k + 8u);
                 }
-                z2 = f2fma(c2[p][k], ek, z2);
+                if (ZT) z2 = f2fma(c2[p][k], ek, z2);
                 w2 = f2fma(c2[p][k], gk, w2);
               }
               f2split(y2, ys[0], ys[1]);
@@ -945,88 +969,53 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             for (int hh = 0; hh < 2; ++hh) {
               const int r = 2 * p + hh;
               if (r >= R) continue;
-              const float tt = tts[hh], dd = dds[hh];
-              const unsigned off = (unsigned)__float_as_int(tt) + koff;
-              bool und = !(fabsf(dd) < wlim);
+              const unsigned off = (unsigned)__float_as_int(tts[hh]) + koff;
+              bool und = !(fabsf(dds[hh]) < wlim);
               bool excl = false;
               if (CUTS) {
-                // excluded segment (decided in FP32), or a cut too close to call: FP64 path
-                const float zc = zs[hh] - 1.f, wc = ws[hh] - 1e-13f, fc = ys[hh] - ylo;
-                excl = zc > 0.f || wc < 0.f || fc < 0.f;
-                und = und || (((cutm >> r) & 1u) &&
-                              (!(fabsf(zc) > mz) || !(fabsf(wc) > mw) || !(fabsf(fc) > mf)));
+                // included when every test clears its margin, excluded when one fails by more
+                // than its margin; anything between is a close call for the FP64 path
+                const bool inc = (!ZT || zs[hh] < zin) && ws[hh] > win && ys[hh] > fin;
+                excl = (ZT && zs[hh] > zex) || ws[hh] < wex || ys[hh] < fex;
+                und = und || (((cutm >> r) & 1u) && !inc && !excl);
               }
-              const float v = q[min(off, qn)];
-              acc[r] += (und || excl) ? 0.f : v;
-              pend |= (unsigned)und << r;
-              if (BINS) {
-                const int b = (int)off + h.qbase;
-                const long long t = tile0 + ctid + r * kCons;
-                if (t < tend && !und)
-                  J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
-              }
-            }
-          }
-        } else {
-          // incomplete band (cut to the slot, or m too wide for the pad): pairs whose window
-          // overlaps the table but whose centre lies outside Q are pending too
-#pragma unroll
-          for (int p = 0; p < R2; ++p) {
-            f32x2 y2 = y02[p];
-#pragma unroll
-            for (int k = 0; k < KP; ++k) y2 = f2fma(c2[p][k], d2[k], y2);
-            const f32x2 tt2 = f2add(y2, kC2);
-            const f32x2 dd2 = f2sub(y2, f2sub(tt2, kC2));
-            float tts[2], dds[2];
-            f2split(tt2, tts[0], tts[1]);
-            f2split(dd2, dds[0], dds[1]);
-            float ys[2], zs[2], ws[2];
-            if (CUTS) {
-              f32x2 z2 = f2pack(0.f, 0.f), w2 = f2pack(0.f, 0.f);
-#pragma unroll
-              for (int k = 0; k < KP; ++k) {
-                f32x2 ek, gk;
-                if (kCutRegs) {
-                  ek = e2[k];
-                  gk = g2[k];
-                } else {
-                  lds_pair2_v(egs + 16u * k, ek, gk);
+              if (COMPLETE) {
+                const float v = q[min(off, qn)];
+                acc[r] += (und || excl) ? 0.f : v;
+                pend |= (unsigned)und << r;
+                if (BINS) {
+                  const int b = (int)off + h.qbase;
+                  const long long t = tile0 + ctid + r * kCons;
+                  if (t < tend && !und)
+                    J.bins_out[t * n_seg + sg] =
+                        (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
                 }
-                z2 = f2fma(c2[p][k], ek, z2);
-                w2 = f2fma(c2[p][k], gk, w2);
+              } else {
+                const bool inq = off < qn;
+                const bool outside = !inq && off + kin < nin && !excl;
+                pend |= (unsigned)(und || outside) << r;
+                const bool use = inq && !und && !excl;
+                const float v = q[use ? off : 0u];  // the address is always valid
+                acc[r] += use ? v : 0.f;
+                if (BINS) {
+                  const int b = (int)off + h.qbase;
+                  const long long t = tile0 + ctid + r * kCons;
+                  if (t < tend && !(und || outside))
+                    J.bins_out[t * n_seg + sg] =
+                        (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
+                }
               }
-              f2split(y2, ys[0], ys[1]);
-              f2split(z2, zs[0], zs[1]);
-              f2split(w2, ws[0], ws[1]);
-            }
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-            const int r = 2 * p + hh;
-            if (r >= R) continue;
-            const float tt = tts[hh], dd = dds[hh];
-            const unsigned off = (unsigned)__float_as_int(tt) + koff;
-            bool und = !(fabsf(dd) < wlim);
-            bool excl = false;
-            if (CUTS) {
-              const float zc = zs[hh] - 1.f, wc = ws[hh] - 1e-13f, fc = ys[hh] - ylo;
-              excl = zc > 0.f || wc < 0.f || fc < 0.f;
-              und = und || (((cutm >> r) & 1u) &&
-                            (!(fabsf(zc) > mz) || !(fabsf(wc) > mw) || !(fabsf(fc) > mf)));
-            }
-            const bool inq = off < qn;
-            const bool outside = !inq && off + kin < nin && !excl;
-            pend |= (unsigned)(und || outside) << r;
-            const bool use = inq && !und && !excl;
-            const float v = q[use ? off : 0u];  // the address is always valid
-            acc[r] += use ? v : 0.f;
-            if (BINS) {
-              const int b = (int)off + h.qbase;
-              const long long t = tile0 + ctid + r * kCons;
-              if (t < tend && !(und || outside))
-                J.bins_out[t * n_seg + sg] = (b + m < 0) ? (int)0x80000000 : (b - m >= J.n_bin ? 0x7fffffff : b);
-            }
             }
           }
+        };
+        using kT = std::true_type;
+        using kF = std::false_type;
+        if (h.complete) {
+          if (!CUTS || zt) pairs(kT{}, kT{});
+          else pairs(kT{}, kF{});
+        } else {
+          if (!CUTS || zt) pairs(kF{}, kT{});
+          else pairs(kF{}, kF{});
         }
         // (rare) queue the pending pairs
         if (pend) {
