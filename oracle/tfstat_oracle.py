@@ -24,6 +24,10 @@ What it computes, step by step, each in the plainest form:
   evolution breaks the linear model, fddot_alpha T_SFT^3 / 6 > 1 (Sec. II.B,
   the T_SFT discussion), and where the track's frequency is below 10^-3.5 Hz
   or its frequency derivative below 1e-13 Hz/s (Sec. II.D).
+* ``chirp_template_sft`` / ``chirp_statistic``: the paper's own S_alpha of
+  Eq. det_stat with the chirping sinusoid of Sec. II.B as the local template:
+  the template's SFT over the 2P + 1 = 201 bins around the track, fdot from
+  the finite differences, |sum d~* h~ / S_n|^2 normalised by <h|h>.
 
 Readings where the paper is silent (window, normalisation constant, DC bin,
 rounding rule, tie band, out-of-range bins, segment times, quantised
@@ -331,17 +335,16 @@ def track_freqs(V, coeffs, f_ref):
     return f
 
 
-def segment_validity(F, T_sft: float):
-    """valid[t, alpha]: False where a segment contributes nothing.
+def finite_differences(F, T_sft: float):
+    """(fdot, z) [t, alpha] of the tracks F [t, alpha] (Hz at the segment midpoints).
 
     Readings: the derivatives come from finite differences of the track at the segment
     midpoints (the paper takes them from the track, by numerical differentiation):
     fdot_alpha = (f_{alpha+1} - f_{alpha-1}) / (2 T_SFT) inside, (f_1 - f_0) / T_SFT and
     (f_{n-1} - f_{n-2}) / T_SFT at the ends, 0 for one segment; the second-order term
     z_alpha = fddot_alpha T_SFT^3 / 6 = ((f_{alpha+1} - 2 f_alpha) + f_{alpha-1}) (T_SFT / 6)
-    inside, the nearest inner value at the ends, 0 for fewer than three segments.  A segment
-    is excluded when z > 1, or f < 10^-3.5 Hz, or fdot < 1e-13 Hz/s (either low condition
-    suffices).  Every step is one IEEE FP64 operation in the order written."""
+    inside, the nearest inner value at the ends, 0 for fewer than three segments.  Every
+    step is one IEEE FP64 operation in the order written."""
     F = np.asarray(F, dtype=np.float64)
     N, n = F.shape
     T = float(T_sft)
@@ -355,6 +358,15 @@ def segment_validity(F, T_sft: float):
         z[:, 1:-1] = ((F[:, 2:] - 2.0 * F[:, 1:-1]) + F[:, :-2]) * (T / 6.0)
         z[:, 0] = z[:, 1]
         z[:, -1] = z[:, -2]
+    return fd, z
+
+
+def segment_validity(F, T_sft: float):
+    """valid[t, alpha]: False where a segment contributes nothing: z > 1, or f < 10^-3.5 Hz,
+    or fdot < 1e-13 Hz/s (either low condition suffices), with fdot and z from
+    ``finite_differences``."""
+    F = np.asarray(F, dtype=np.float64)
+    fd, z = finite_differences(F, T_sft)
     return ~((z > 1.0) | (F < F_LOW_HZ) | (fd < FDOT_LOW))
 
 
@@ -388,6 +400,72 @@ def eval_stat_masked(P, V, coeffs, f_ref, T_sft: float, m: int, chunk: int = 409
         S[s0:s1] = statistic_masked(P, b, valid, m)
         valid_all[s0:s1] = valid
     return S, valid_all
+
+
+# --------------------------------------------------------------------------
+# The linear-chirp statistic (Sec. II.B: S_alpha of Eq. det_stat with the
+# chirping local template, its SFT over the 2P + 1 bins around the track)
+# --------------------------------------------------------------------------
+CHIRP_P = 100   # the paper's band: 2P + 1 = 201 bins (Sec. II.B)
+
+
+def chirp_template_sft(f, fdot, T_sft: float, dt: float, bins, window_kind: str = "hann"):
+    """h~_k for each listed bin k: the SFT (the window, sampling and DFT of ``sft``) of the
+    segment's local waveform exp(i [2 pi f (t - t_a) + pi fdot (t - t_a)^2]), the chirping
+    sinusoid of Sec. II.B with unit amplitude and zero phase; t runs over the segment's
+    samples t = n dt from its start and t_a = T_SFT / 2 is its midpoint.  f, fdot: [N];
+    bins: [N, B] integers in [0, L); returns [N, B] complex."""
+    f = np.asarray(f, dtype=np.float64).reshape(-1)
+    fdot = np.asarray(fdot, dtype=np.float64).reshape(-1)
+    L = int(round(T_sft / dt))
+    u = np.arange(L, dtype=np.float64) * dt - 0.5 * T_sft
+    w = window(L, window_kind)
+    phase = 2.0 * np.pi * f[:, None] * u[None, :] + np.pi * fdot[:, None] * (u * u)[None, :]
+    H = dt * np.fft.fft(w[None, :] * np.exp(1j * phase), axis=1)
+    return np.take_along_axis(H, np.asarray(bins, dtype=np.int64) % L, axis=1)
+
+
+def chirp_statistic(d, psd_bins, dt: float, T_sft: float, F, P: int = CHIRP_P, valid=None,
+                    window_kind: str = "hann"):
+    """S [t] = sum_alpha S_alpha (FP64) with the linear-chirp S_alpha of Eq. det_stat:
+
+        S_alpha = 4 / (dt sum w^2) |sum_k d~*_{alpha,k} h~_{alpha,k} / S_k|^2 / sum_k |h~_{alpha,k}|^2 / S_k
+
+    (the maximised inner product 4 |sum d~* h~ / S_n| Delta f squared over <h|h>, with
+    Delta f = 1 / T_SFT generalised for the window as in ``power_table``), h~ from
+    ``chirp_template_sft`` at f_alpha = F[t, alpha] and fdot_alpha from
+    ``finite_differences``.  Readings: the sum runs over the 2P + 1 bins k = b - P .. b + P
+    around the nearest bin b = floor(f_alpha T_SFT + 1/2) that lie in the table, skipping the
+    DC bin and bins whose S_n is not finite and positive; S_alpha = 0 when no bin is left,
+    and where valid[t, alpha] is False.  d: the complex SFTs [n_seg, n_bin] of ``sft``."""
+    d = np.asarray(d, dtype=np.complex128)
+    n_seg, n_bin = d.shape
+    F = np.asarray(F, dtype=np.float64)
+    N = F.shape[0]
+    L = int(round(T_sft / dt))
+    w = window(L, window_kind)
+    norm = 4.0 / (dt * float(np.sum(w * w)))
+    S = np.asarray(psd_bins, dtype=np.float64)
+    ok = np.isfinite(S) & (S > 0)
+    ok[0] = False
+    inv_S = np.where(ok, 1.0 / np.where(ok, S, 1.0), 0.0)
+    fd, _ = finite_differences(F, T_sft)
+    b, _ = bins_and_ties(F * T_sft)
+    j = np.arange(-P, P + 1, dtype=np.int64)
+    total = np.zeros(N)
+    for a in range(n_seg):
+        k = b[:, a][:, None] + j[None, :]                     # [N, 2P+1]
+        inside = (k >= 0) & (k < n_bin)
+        kk = np.where(inside, k, 0)
+        wgt = np.where(inside, inv_S[kk], 0.0)
+        h = chirp_template_sft(F[:, a], fd[:, a], T_sft, dt, kk, window_kind)
+        num = np.abs(np.sum(np.conj(d[a, kk]) * h * wgt, axis=1)) ** 2
+        den = np.sum((h.real ** 2 + h.imag ** 2) * wgt, axis=1)
+        Sa = np.where(den > 0, norm * num / np.where(den > 0, den, 1.0), 0.0)
+        if valid is not None:
+            Sa = np.where(valid[:, a], Sa, 0.0)
+        total += Sa
+    return total
 
 
 # --------------------------------------------------------------------------
