@@ -301,6 +301,48 @@ int tfs_server_get_stats(tfs_server* s, tfs_server_stats* out);
  * and buffers.  Tickets not yet waited for are dropped. */
 int tfs_server_free(tfs_server* s);
 
+/* ---- the paper's linear-chirp statistic (Sec. II.B, Eq. det_stat) ----------
+ * The full per-segment statistic of the paper: the local waveform of segment
+ * alpha is the chirping sinusoid exp(i [2 pi f_a (t - t_a) + pi fdot_a (t - t_a)^2])
+ * (t_a the segment midpoint, f_a = f_ref + sum_k c_k U_k,alpha, fdot_a its
+ * finite difference: (f_{a+1} - f_{a-1}) / (2 T_sft) inside, one-sided at the
+ * ends, 0 for one segment), maximised over amplitude and phase:
+ *   S_alpha = 4 / (dt sum w^2) |sum_k d~*_{alpha,k} h~_{alpha,k} / S_k|^2 / sum_k |h~_{alpha,k}|^2 / S_k
+ * over the 2P + 1 bins k = b - P .. b + P around the nearest bin
+ * b = floor(f_a T_sft + 1/2) that lie in the table (the DC bin and bins whose
+ * S_n is not finite and positive left out); S_alpha = 0 when b itself lies
+ * outside the table or no bin is left.
+ * d~ is the Hann-windowed SFT of the strain (Sec. II.B); h~ the template's SFT,
+ * evaluated as the Fourier integral of the windowed chirp at 512 points (equal
+ * to the sampled SFT within 1e-7 of its peak for L >= 512, P <= 111 and
+ * |fdot| T_sft^2 <= 100).  The paper uses P = 100 (TFS_CHIRP_P).
+ *
+ * tfs_build_chirp_table: strain [n] (host or device per mem, FP64), dt,
+ * T_sft (L = T_sft/dt an even 2,3,5-smooth integer in [512, 2^20]), psd [L/2+1]
+ * one-sided S_n(k/T_sft).  Builds the device table z [n_seg][n_bin] (complex
+ * FP32: sqrt(4 dt / (sum w^2 S_ref)) X_k S_ref / S_k with X the windowed DFT
+ * and S_ref the median usable S_n) and wt [n_bin] = S_ref / S_k (0 where
+ * unusable).  Synchronous; the handle is freed with tfs_ctable_free.
+ * tfs_ctable_to_host copies z ([n_seg][n_bin][2] floats) and/or wt to host.
+ *
+ * tfs_eval_chirp_stat: coeffs [N][K] (FP64), f_ref [N] or NULL, stat [N]
+ * (FP32) or NULL with topk > 0, top_idx / top_val [min(topk, N)]: device
+ * pointers of the current device.  0 <= N < 2^31, 0 <= P <= 111, flags 0 or
+ * TFS_JOB_SEGMENT_CUTS (the exclusions of tfs_job; an excluded segment
+ * contributes 0), 0 <= topk <= 1024.  The bins b are those of the FP64
+ * oracle, bit for bit.  Stream-ordered and asynchronous on `stream`
+ * (scratch by cudaMallocAsync). */
+typedef struct tfs_ctable tfs_ctable; /* device-resident linear-chirp table */
+#define TFS_CHIRP_P 100
+int tfs_build_chirp_table(const double* strain, int64_t n, double dt, double T_sft, const double* psd, int mem,
+                          void* stream, tfs_ctable** out);
+int tfs_ctable_info(const tfs_ctable* t, int64_t* n_seg, int64_t* n_bin, double* T_sft, double* dt, double* s_ref);
+int tfs_ctable_to_host(const tfs_ctable* t, float* z, float* wt);
+int tfs_ctable_free(tfs_ctable* t);
+int tfs_eval_chirp_stat(const tfs_ctable* ct, const tfs_basis* basis, const double* coeffs, const double* f_ref,
+                        int64_t N, int P, int flags, float* stat, int topk, int64_t* top_idx, float* top_val,
+                        void* stream);
+
 /* Number of kernels this library has launched in this process (all devices). */
 long long tfs_kernel_launches(void);
 

@@ -436,8 +436,10 @@ def chirp_statistic(d, psd_bins, dt: float, T_sft: float, F, P: int = CHIRP_P, v
     ``chirp_template_sft`` at f_alpha = F[t, alpha] and fdot_alpha from
     ``finite_differences``.  Readings: the sum runs over the 2P + 1 bins k = b - P .. b + P
     around the nearest bin b = floor(f_alpha T_SFT + 1/2) that lie in the table, skipping the
-    DC bin and bins whose S_n is not finite and positive; S_alpha = 0 when no bin is left,
-    and where valid[t, alpha] is False.  d: the complex SFTs [n_seg, n_bin] of ``sft``."""
+    DC bin and bins whose S_n is not finite and positive; S_alpha = 0 when the track's own
+    bin b lies outside the table (its frequency is outside the data's band: only the far
+    tails of the template would remain), when no bin is left, and where valid[t, alpha] is
+    False.  d: the complex SFTs [n_seg, n_bin] of ``sft``."""
     d = np.asarray(d, dtype=np.complex128)
     n_seg, n_bin = d.shape
     F = np.asarray(F, dtype=np.float64)
@@ -462,6 +464,7 @@ def chirp_statistic(d, psd_bins, dt: float, T_sft: float, F, P: int = CHIRP_P, v
         num = np.abs(np.sum(np.conj(d[a, kk]) * h * wgt, axis=1)) ** 2
         den = np.sum((h.real ** 2 + h.imag ** 2) * wgt, axis=1)
         Sa = np.where(den > 0, norm * num / np.where(den > 0, den, 1.0), 0.0)
+        Sa = np.where((b[:, a] >= 0) & (b[:, a] < n_bin), Sa, 0.0)
         if valid is not None:
             Sa = np.where(valid[:, a], Sa, 0.0)
         total += Sa

@@ -178,6 +178,82 @@ class _TieReport(ctypes.Structure):
                 ("track", ctypes.c_void_p), ("seg", ctypes.c_void_p)]
 
 
+class ChirpTable:
+    """Device-resident linear-chirp table (scaled complex spectra of a Hann-windowed strain)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        n_seg, n_bin = ctypes.c_int64(), ctypes.c_int64()
+        T, dt, s_ref = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().tfs_ctable_info(self._h, ctypes.byref(n_seg), ctypes.byref(n_bin), ctypes.byref(T),
+                                    ctypes.byref(dt), ctypes.byref(s_ref)))
+        self.n_seg, self.n_bin, self.T_sft, self.dt, self.s_ref = n_seg.value, n_bin.value, T.value, dt.value, s_ref.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def to_host(self):
+        """(z [n_seg, n_bin] complex64, wt [n_bin] float32)."""
+        z = np.empty((self.n_seg, self.n_bin, 2), dtype=np.float32)
+        wt = np.empty(self.n_bin, dtype=np.float32)
+        check(lib().tfs_ctable_to_host(self._h, _ptr(z), _ptr(wt)))
+        return z[..., 0] + 1j * z[..., 1], wt
+
+    def free(self):
+        if self._h:
+            lib().tfs_ctable_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+CHIRP_P = 100  # TFS_CHIRP_P: the paper's 2P + 1 = 201 bins
+
+
+def build_chirp_table(strain, dt: float, T_sft: float, psd, stream=None) -> ChirpTable:
+    """Strain -> linear-chirp table (tfs_build_chirp_table; Hann window)."""
+    h = ctypes.c_void_p()
+    if _is_torch_cuda(strain):
+        torch = _torch()
+        psd_t = psd if _is_torch_cuda(psd) else torch.as_tensor(np.asarray(psd, np.float64), device=strain.device)
+        check(lib().tfs_build_chirp_table(_ptr(strain), strain.numel(), float(dt), float(T_sft), _ptr(psd_t),
+                                          MEM_DEVICE, _stream_ptr(stream), ctypes.byref(h)))
+    else:
+        s, p = _f64(strain), _f64(psd)
+        check(lib().tfs_build_chirp_table(_ptr(s), s.size, float(dt), float(T_sft), _ptr(p), MEM_HOST, None,
+                                          ctypes.byref(h)))
+    return ChirpTable(h)
+
+
+def eval_chirp_stat(ctable: ChirpTable, basis: Basis, coeffs, f_ref=None, P: int = CHIRP_P,
+                    segment_cuts: bool = False, topk: int = 0, stat=None, top_idx=None, top_val=None,
+                    stream=None):
+    """The paper's linear-chirp statistic of a batch of tracks (tfs_eval_chirp_stat).
+
+    coeffs (and f_ref) are CUDA tensors; returns (stat, top_idx, top_val) as CUDA tensors,
+    asynchronous on `stream`."""
+    torch = _torch()
+    N = coeffs.shape[0]
+    dev = coeffs.device
+    if stat is None:
+        stat = torch.empty(N, dtype=torch.float32, device=dev)
+    kk = min(topk, N)
+    if topk > 0 and top_idx is None:
+        top_idx = torch.empty(kk, dtype=torch.int64, device=dev)
+        top_val = torch.empty(kk, dtype=torch.float32, device=dev)
+    check(lib().tfs_eval_chirp_stat(ctable.handle, basis.handle, _ptr(coeffs),
+                                    _ptr(f_ref) if f_ref is not None else None, N, int(P),
+                                    _lib.JOB_SEGMENT_CUTS if segment_cuts else 0, _ptr(stat), int(topk),
+                                    _ptr(top_idx) if topk else None, _ptr(top_val) if topk else None,
+                                    _stream_ptr(stream)))
+    return stat, top_idx, top_val
+
+
 @dataclasses.dataclass
 class EvalResult:
     stat: object            # [N] float32 (numpy, or torch on the device)

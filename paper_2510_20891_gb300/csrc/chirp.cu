@@ -1,0 +1,330 @@
+// The paper's linear-chirp statistic (Sec. II.B, Eq. det_stat with the chirping local template).
+//
+// For every (track, segment) pair the local waveform is the linear chirp
+// exp(i [2 pi f (t - t_a) + pi fdot (t - t_a)^2]) with f the track's frequency at the segment
+// midpoint t_a and fdot its finite difference; S_alpha is |sum_k d~*_k h~_k / S_k|^2 over
+// sum_k |h~_k|^2 / S_k on the 2P + 1 bins around the nearest bin b, times 4 / (dt sum w^2).
+//
+// GB300 layout: one warp per track at a time, segments in order.  The track's frequency,
+// derivatives and bin are evaluated in FP64 in the oracle's operation order, 32 segments at
+// a time with one segment per lane (GB300's FP64 rate is a small fraction of FP32), so b is
+// bit-identical.  The template is the Fourier
+// integral of the Hann-windowed chirp over the segment, sampled at 512 points and
+// transformed by a warp-wide 512-point FFT (16 per lane, a lane-local 16-point DFT, a
+// shared-memory transpose, a second 16-point DFT and one radix-2 exchange between lane
+// pairs): with the Hann window the sampled transform equals the sampled SFT of the
+// template within aliasing of order 1 / (2 pi (512 - P - beta / 2)^3) of its peak.  The
+// scaled complex table (L2-resident) supplies the data bins; sums in FP32, S_alpha summed
+// over segments in FP64.
+#include <cmath>
+#include <cstdint>
+
+#include "tfs_internal.cuh"
+
+namespace tfs {
+namespace {
+
+constexpr int kM = 512;           // template samples per segment
+constexpr int kCW = 8;            // warps per block
+constexpr int kCThreads = 32 * kCW;
+constexpr int kChirpPMax = 111;   // the output mapping covers |j| <= 111
+constexpr double kFLow = 0x1.4b96be9c2da2cp-12;  // 10^-3.5 Hz, the nearest double
+
+struct ChirpArgs {
+  const float2* z;      // [n_seg][n_bin]
+  const float* wt;      // [n_bin]
+  int n_seg, n_bin;
+  const double* U;      // [K][n_seg]
+  int K;
+  const double* coeffs; // [N][K]
+  const double* f_ref;  // [N] or null
+  long long N;
+  double T;
+  int P, cuts;
+  float* stat;          // [N]
+};
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 c_mi(float2 a) { return make_float2(a.y, -a.x); }  // times -i
+
+// e^{-2 pi i e / 16} and e^{-2 pi i k / 32}
+__device__ __forceinline__ float2 w16(int e) {
+  switch (e & 15) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(0.9238795325112867f, -0.3826834323650898f);
+    case 2: return make_float2(0.7071067811865476f, -0.7071067811865475f);
+    case 3: return make_float2(0.38268343236508984f, -0.9238795325112867f);
+    case 4: return make_float2(0.f, -1.f);
+    case 6: return make_float2(-0.7071067811865475f, -0.7071067811865476f);
+    case 9: return make_float2(-0.9238795325112868f, 0.38268343236508967f);
+    default: return make_float2(0.f, 0.f);  // not used by dft16
+  }
+}
+__device__ __forceinline__ float2 w32(int k) {
+  switch (k) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(0.9807852804032304f, -0.19509032201612825f);
+    case 2: return make_float2(0.9238795325112867f, -0.3826834323650898f);
+    case 3: return make_float2(0.8314696123025452f, -0.5555702330196022f);
+    case 4: return make_float2(0.7071067811865476f, -0.7071067811865475f);
+    case 5: return make_float2(0.5555702330196023f, -0.8314696123025452f);
+    case 6: return make_float2(0.38268343236508984f, -0.9238795325112867f);
+    case 9: return make_float2(-0.1950903220161282f, -0.9807852804032304f);
+    case 10: return make_float2(-0.3826834323650897f, -0.9238795325112867f);
+    case 11: return make_float2(-0.555570233019602f, -0.8314696123025455f);
+    case 12: return make_float2(-0.7071067811865475f, -0.7071067811865476f);
+    case 13: return make_float2(-0.8314696123025453f, -0.5555702330196022f);
+    case 14: return make_float2(-0.9238795325112867f, -0.3826834323650899f);
+    case 15: return make_float2(-0.9807852804032304f, -0.1950903220161286f);
+    default: return make_float2(0.f, 0.f);  // 7, 8: not used by the exchange
+  }
+}
+
+// 4-point DFT in place (W4 = -i).
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  const float2 a = c_add(x0, x2), b = c_sub(x0, x2), c = c_add(x1, x3), d = c_mi(c_sub(x1, x3));
+  x0 = c_add(a, c);
+  x2 = c_sub(a, c);
+  x1 = c_add(b, d);
+  x3 = c_sub(b, d);
+}
+
+// 16-point DFT X[k] = sum_n v[n] W16^{nk} by 4 x 4 (n = 4 n1 + n2, k = k1 + 4 k2);
+// X[k1 + 4 k2] ends in v[4 k1 + k2] (read it through at16).
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+#pragma unroll
+  for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = c_mul(v[4 * k1 + n2], w16(n2 * k1));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+}
+__device__ __forceinline__ int at16(int k) { return 4 * (k & 3) + (k >> 2); }
+
+__device__ __forceinline__ double track_f(const ChirpArgs& a, const double* c, double fr, int seg) {
+  double f = fr;
+  for (int k = 0; k < a.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], a.U[(size_t)k * a.n_seg + seg]));
+  return f;
+}
+
+__global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const ChirpArgs a) {
+  __shared__ float s_win[kM];                 // sin^2(pi m / 512)
+  __shared__ float2 s_buf[kCW][16][33];       // per-warp transpose (padded rows)
+  __shared__ double s_c[kCW][32];             // the warp's track coefficients
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int i = tid; i < kM; i += kCThreads) {
+    const float s = sinpif((float)i / (float)kM);
+    s_win[i] = s * s;
+  }
+  // e^{-2 pi i lane j0 / 512}, j0 = 0..15 (exact arguments)
+  float2 tw[16];
+#pragma unroll
+  for (int j0 = 0; j0 < 16; ++j0) {
+    float sn, cs;
+    sincospif(-(float)(2 * lane * j0) / (float)kM, &sn, &cs);
+    tw[j0] = make_float2(cs, sn);
+  }
+  __syncthreads();
+  const int n = a.n_seg;
+  const double T = a.T;
+  const double T6 = __ddiv_rn(T, 6.0);
+  const int h = lane & 1, j0p = lane >> 1;
+  const long long nw = (long long)gridDim.x * kCW;
+  for (long long t = (long long)blockIdx.x * kCW + w; t < a.N; t += nw) {
+    __syncwarp();
+    if (lane < a.K) s_c[w][lane] = a.coeffs[t * a.K + lane];
+    __syncwarp();
+    const double* c = s_c[w];
+    const double fr = a.f_ref ? a.f_ref[t] : 0.0;
+    double sacc = 0.0;
+    for (int al0 = 0; al0 < n; al0 += 32) {
+      // lane s prepares segment al0 + s in FP64, in the oracle's operation order: its frequency
+      // and neighbours, fdot by finite differences (one-sided at the ends), the bin, the cuts,
+      // and the FP32 phase parameters; the warp then takes the segments one by one
+      const int sg = al0 + lane;
+      bool p_skip = true;
+      int p_b = 0;
+      float p_d2 = 0.f, p_bh = 0.f, p_bl = 0.f;
+      if (sg < n) {
+        const double F0 = track_f(a, c, fr, sg);
+        const double Fm = sg > 0 ? track_f(a, c, fr, sg - 1) : 0.0;
+        const double Fp = sg + 1 < n ? track_f(a, c, fr, sg + 1) : 0.0;
+        double fd = 0.0;
+        if (n >= 2) {
+          if (sg == 0) fd = __ddiv_rn(__dsub_rn(Fp, F0), T);
+          else if (sg == n - 1) fd = __ddiv_rn(__dsub_rn(F0, Fm), T);
+          else fd = __ddiv_rn(__dsub_rn(Fp, Fm), __dmul_rn(2.0, T));
+        }
+        const double x = __dmul_rn(F0, T);
+        const double bz = floor(__dadd_rn(x, 0.5));
+        // the track's own bin must lie in the table (else only far template tails would remain)
+        bool skip = !isfinite(x) || bz < 0.0 || bz >= (double)a.n_bin;
+        if (a.cuts && !skip) {
+          double z = 0.0;
+          if (n >= 3) {
+            double fa, fb, fc;  // F at c + 1, c, c - 1 with c the nearest inner segment
+            if (sg == 0) {
+              fa = track_f(a, c, fr, 2);
+              fb = Fp;
+              fc = F0;
+            } else if (sg == n - 1) {
+              fa = F0;
+              fb = Fm;
+              fc = track_f(a, c, fr, n - 3);
+            } else {
+              fa = Fp;
+              fb = F0;
+              fc = Fm;
+            }
+            z = __dmul_rn(__dadd_rn(__dsub_rn(fa, __dmul_rn(2.0, fb)), fc), T6);
+          }
+          skip = z > 1.0 || F0 < kFLow || fd < 1e-13;
+        }
+        if (!skip) {
+          p_b = (int)bz;
+          p_d2 = (float)(2.0 * __dsub_rn(x, bz));  // 2 delta0, delta0 in [-1/2, 1/2]
+          // beta = fdot T^2 split so that beta_hi * y^2 is exact in FP32 (7 + 16 significant bits)
+          const double beta = fd * T * T;
+          double bh64 = 0.0;
+          if (beta != 0.0 && isfinite(beta)) {
+            int e;
+            frexp(beta, &e);
+            bh64 = ldexp(rint(ldexp(beta, 7 - e)), e - 7);
+          }
+          p_bh = (float)bh64;
+          p_bl = (float)(beta - bh64);
+        }
+        p_skip = skip;
+      }
+      const int cnt = min(32, n - al0);
+      for (int sl = 0; sl < cnt; ++sl) {
+        if (__shfl_sync(0xffffffffu, (int)p_skip, sl)) continue;  // warp-uniform
+        const int al = al0 + sl;
+        const int b = __shfl_sync(0xffffffffu, p_b, sl);
+        const float d2 = __shfl_sync(0xffffffffu, p_d2, sl);
+        const float bh = __shfl_sync(0xffffffffu, p_bh, sl);
+        const float bl = __shfl_sync(0xffffffffu, p_bl, sl);
+        // samples m = lane + 32 i of g(y) = w(y) e^{i pi (2 delta0 y + beta y^2)}, y = m / 512 - 1/2
+        float2 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int m = lane + 32 * i;
+          const int mc = m - kM / 2;
+          const float y = (float)mc * (1.f / kM);
+          const float q = (float)(mc * mc) * (1.f / (kM * kM));  // y^2, exact
+          const float p1 = bh * q;                               // exact
+          const float r1 = p1 - 2.f * rintf(0.5f * p1);          // exact reduction modulo 2
+          const float ph = r1 + fmaf(bl, q, d2 * y);
+          float sn, cs;
+          sincospif(ph, &sn, &cs);
+          const float wv = s_win[m];
+          v[i] = make_float2(wv * cs, wv * sn);
+        }
+        // 512 = 16 (lane-local) x 32 (across lanes)
+        dft16(v);
+#pragma unroll
+        for (int j0 = 0; j0 < 16; ++j0) s_buf[w][j0][lane] = c_mul(v[at16(j0)], tw[j0]);
+        __syncwarp();
+#pragma unroll
+        for (int qq = 0; qq < 16; ++qq) v[qq] = s_buf[w][j0p][2 * qq + h];
+        __syncwarp();
+        dft16(v);  // E (even lanes) or O (odd lanes) of the 32-point DFT over the lanes
+        // radix-2 exchange: G[j0 + 16 j1] = E(j1) + W32^j1 O(j1) (j1 < 16), E - W32 O above.
+        // Even lanes produce j1 = 0..6 (j = j0 + 16 j1 <= 111), odd lanes j1 = 25..31 (j - 512 >= -112).
+        float re = 0.f, im = 0.f, nr = 0.f;
+#pragma unroll
+        for (int s = 0; s < 7; ++s) {
+          const float2 lo = v[at16(s)], hi = v[at16(9 + s)];
+          const float2 send = h ? c_mul(w32(s), lo) : hi;
+          const float2 keep = h ? c_mul(w32(9 + s), hi) : lo;
+          float2 recv;
+          recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+          recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+          const float2 G = h ? c_sub(recv, keep) : c_add(keep, recv);
+          const int jj = h ? j0p + 16 * (25 + s) - kM : j0p + 16 * s;
+          const int kb = b + jj;
+          if (jj >= -a.P && jj <= a.P && kb >= 0 && kb < a.n_bin) {
+            const float2 zz = a.z[(size_t)al * a.n_bin + kb];
+            const float wv = a.wt[kb];
+            re = fmaf(zz.x, G.x, fmaf(zz.y, G.y, re));
+            im = fmaf(zz.x, G.y, fmaf(-zz.y, G.x, im));
+            nr = fmaf(wv, fmaf(G.x, G.x, G.y * G.y), nr);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          re += __shfl_xor_sync(0xffffffffu, re, o);
+          im += __shfl_xor_sync(0xffffffffu, im, o);
+          nr += __shfl_xor_sync(0xffffffffu, nr, o);
+        }
+        if (nr > 0.f) sacc += (double)(fmaf(re, re, im * im) / nr);
+      }
+    }
+    if (lane == 0) a.stat[t] = (float)sacc;
+  }
+}
+
+}  // namespace
+}  // namespace tfs
+
+using namespace tfs;
+
+extern "C" int tfs_eval_chirp_stat(const tfs_ctable* ct, const tfs_basis* basis, const double* coeffs,
+                                   const double* f_ref, int64_t N, int P, int flags, float* stat, int topk,
+                                   int64_t* top_idx, float* top_val, void* stream) {
+  clear_error();
+  TFS_CHECK(ct && basis, TFS_ERR_INVALID_ARG, "null table or basis");
+  TFS_CHECK(basis->n_seg == ct->n_seg, TFS_ERR_INVALID_ARG, "basis has %lld segments, table %lld",
+            (long long)basis->n_seg, (long long)ct->n_seg);
+  TFS_CHECK(basis->K >= 1 && basis->K <= 32, TFS_ERR_INVALID_ARG, "basis size must be in [1, 32]");
+  TFS_CHECK(N >= 0 && N < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "N must be in [0, 2^31)");
+  TFS_CHECK(P >= 0 && P <= kChirpPMax, TFS_ERR_INVALID_ARG, "P must be in [0, %d]", kChirpPMax);
+  TFS_CHECK((flags & ~TFS_JOB_SEGMENT_CUTS) == 0, TFS_ERR_INVALID_ARG, "unknown flags");
+  TFS_CHECK(topk >= 0 && topk <= 1024, TFS_ERR_INVALID_ARG, "topk must be in [0, 1024]");
+  TFS_CHECK(N == 0 || coeffs, TFS_ERR_INVALID_ARG, "null coeffs");
+  TFS_CHECK(stat || topk > 0 || N == 0, TFS_ERR_INVALID_ARG, "need stat or topk > 0");
+  TFS_CHECK(topk == 0 || N == 0 || (top_idx && top_val), TFS_ERR_INVALID_ARG, "null top-k outputs");
+  if (N == 0) return TFS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* d_stat = stat;
+  void* ws = nullptr;
+  const int kk = (int)std::min<int64_t>(topk, N);
+  size_t need = (stat ? 0 : (((size_t)N * 4 + 255) & ~(size_t)255)) + (kk ? topk_workspace_bytes(N) : 0);
+  char* scratch = nullptr;
+  if (need) TFS_CUDA(cudaMallocAsync((void**)&scratch, need, st));
+  if (!stat) d_stat = reinterpret_cast<float*>(scratch);
+  if (kk) ws = scratch + (stat ? 0 : (((size_t)N * 4 + 255) & ~(size_t)255));
+  ChirpArgs a;
+  a.z = ct->z;
+  a.wt = ct->wt;
+  a.n_seg = (int)ct->n_seg;
+  a.n_bin = (int)ct->n_bin;
+  a.U = basis->U;
+  a.K = basis->K;
+  a.coeffs = coeffs;
+  a.f_ref = f_ref;
+  a.N = N;
+  a.T = ct->T_sft;
+  a.P = P;
+  a.cuts = (flags & TFS_JOB_SEGMENT_CUTS) ? 1 : 0;
+  a.stat = d_stat;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chirp_stat_kernel, kCThreads, 0);
+  const long long want = (N + kCW - 1) / kCW;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(1, n_sm) * std::max(1, per_sm)));
+  chirp_stat_kernel<<<grid, kCThreads, 0, st>>>(a);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  int rc = e == cudaSuccess ? TFS_OK : cuda_fail(e, "chirp statistic");
+  if (rc == TFS_OK && kk) rc = topk_device(d_stat, N, kk, top_idx, top_val, ws, st);
+  if (scratch) cudaFreeAsync(scratch, st);
+  return rc;
+}

@@ -13,6 +13,7 @@
 // (4, 2, 3, 5) self-sorting Stockham pass sequence in shared memory.  The
 // real spectrum follows from X_k = (Z_k + Z*_{N-k})/2 - i e^{-2 pi i k/L}
 // (Z_k - Z*_{N-k})/2, and P_k = 4 dt |X_k|^2 / (sum w^2 S_n(k/T_SFT)).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -198,6 +199,23 @@ __global__ void sft_power(const double2* __restrict__ Z, int N, const double2* _
   const double2 o = cscale(csub(zk, zn), 0.5);
   const double2 X = cadd(e, mul_mi(cmul(twU[k], o)));
   P[(size_t)seg * (N + 1) + k] = (X.x * X.x + X.y * X.y) * pscale[k];
+}
+
+// Step 3 for the linear-chirp table: the complex spectrum scaled per bin, FP32 pairs
+// z [n_seg][n_bin] = X_k zscale_k.
+__global__ void sft_cspec(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
+                          const double* __restrict__ zscale, float2* __restrict__ zout) {
+  const int seg = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  const double2* z = Z + (size_t)seg * N;
+  const double2 zk = z[k == N ? 0 : k];
+  const double2 zn0 = z[k == 0 ? 0 : N - k];
+  const double2 zn = make_double2(zn0.x, -zn0.y);
+  const double2 e = cscale(cadd(zk, zn), 0.5);
+  const double2 o = cscale(csub(zk, zn), 0.5);
+  const double2 X = cadd(e, mul_mi(cmul(twU[k], o)));
+  zout[(size_t)seg * (N + 1) + k] = make_float2((float)(X.x * zscale[k]), (float)(X.y * zscale[k]));
 }
 
 }  // namespace
@@ -429,6 +447,9 @@ struct SftPlan {
   FftPlan p1{}, p2{};
   double* win = nullptr;      // [L]
   double* pscale = nullptr;   // [n_bin]: 4 dt / (sum w^2 S_n), 0 where unusable
+  double* zscale = nullptr;   // [n_bin]: sqrt(4 dt / (sum w^2 S_ref)) S_ref / S_n, 0 where unusable
+  float* wt = nullptr;        // [n_bin]: S_ref / S_n, 0 where unusable
+  double s_ref = 1.0;         // median of the usable S_n (keeps the chirp table's values near 1)
   double2* tw1 = nullptr;     // [N1]
   double2* tw2 = nullptr;     // [N2]
   double2* twN = nullptr;     // [N] (N2 > 1)
@@ -439,7 +460,8 @@ struct SftPlan {
 void free_sft_plan(void* p) {
   SftPlan* s = static_cast<SftPlan*>(p);
   if (!s) return;
-  for (void* q : {(void*)s->win, (void*)s->pscale, (void*)s->tw1, (void*)s->tw2, (void*)s->twN, (void*)s->twU})
+  for (void* q : {(void*)s->win, (void*)s->pscale, (void*)s->zscale, (void*)s->wt, (void*)s->tw1, (void*)s->tw2,
+                  (void*)s->twN, (void*)s->twU})
     if (q) cudaFree(q);
   delete s;
 }
@@ -468,9 +490,24 @@ static int make_sft_plan(int64_t L, double dt, int window, const double* psd, in
     TFS_CUDA(cudaMemcpy(psd_h.data(), psd, n_bin * 8, cudaMemcpyDeviceToHost));
   else
     for (int64_t k = 0; k < n_bin; ++k) psd_h[k] = psd[k];
+  std::vector<double> usable;
   for (int64_t k = 0; k < n_bin; ++k) {
     const double S = psd_h[k];
-    pscale[k] = (std::isfinite(S) && S > 0 && k > 0) ? 4.0 * dt / (sw2 * S) : 0.0;
+    const bool ok = std::isfinite(S) && S > 0 && k > 0;
+    pscale[k] = ok ? 4.0 * dt / (sw2 * S) : 0.0;
+    if (ok) usable.push_back(S);
+  }
+  double s_ref = 1.0;
+  if (!usable.empty()) {
+    std::nth_element(usable.begin(), usable.begin() + usable.size() / 2, usable.end());
+    s_ref = usable[usable.size() / 2];
+  }
+  std::vector<double> zscale(n_bin);
+  std::vector<float> wt(n_bin);
+  for (int64_t k = 0; k < n_bin; ++k) {
+    const bool ok = pscale[k] > 0.0;
+    zscale[k] = ok ? std::sqrt(4.0 * dt / (sw2 * s_ref)) * (s_ref / psd_h[k]) : 0.0;
+    wt[k] = ok ? (float)(s_ref / psd_h[k]) : 0.f;
   }
   std::vector<double2> tw1, tw2, twN, twU(n_bin);
   twiddles(N1, tw1);
@@ -500,6 +537,9 @@ static int make_sft_plan(int64_t L, double dt, int window, const double* psd, in
   };
   up((void**)&s->win, win.data(), L * 8);
   up((void**)&s->pscale, pscale.data(), n_bin * 8);
+  up((void**)&s->zscale, zscale.data(), n_bin * 8);
+  up((void**)&s->wt, wt.data(), n_bin * 4);
+  s->s_ref = s_ref;
   up((void**)&s->tw1, tw1.data(), (size_t)N1 * 16);
   up((void**)&s->tw2, tw2.data(), (size_t)N2 * 16);
   if (N2 > 1) up((void**)&s->twN, twN.data(), (size_t)N * 16);
@@ -514,6 +554,42 @@ static int make_sft_plan(int64_t L, double dt, int window, const double* psd, in
   }
   *out = s;
   return TFS_OK;
+}
+
+// The column and row FFT passes of every segment: returns the half-length spectra (Y or Z).
+static int run_fft_passes(const SftPlan* p, const double* d_x, int64_t n_seg, double2** Y, double2** Z,
+                          const double2** out, cudaStream_t st) {
+  const size_t nz = (size_t)n_seg * p->N;
+  TFS_CUDA(cudaMallocAsync((void**)Y, nz * 16, st));
+  if (p->N2 > 1) TFS_CUDA(cudaMallocAsync((void**)Z, nz * 16, st));
+  dim3 g1((p->N2 + p->CB - 1) / p->CB, (unsigned)n_seg);
+  sft_cols<<<g1, 256, p->sm1, st>>>(d_x, p->win, (int)p->L, p->N1, p->N2, p->CB, p->p1, p->tw1, p->twN, *Y);
+  count_launch();
+  *out = *Y;
+  if (p->N2 > 1) {
+    dim3 g2((p->N1 + p->RB - 1) / p->RB, (unsigned)n_seg);
+    sft_rows<<<g2, 256, p->sm2, st>>>(*Y, p->N1, p->N2, p->RB, p->p2, p->tw2, *Z);
+    count_launch();
+    *out = *Z;
+  }
+  return TFS_OK;
+}
+
+// Strain -> linear-chirp table (complex spectra scaled per bin) on `st`.
+static int run_sft_complex(const SftPlan* p, const double* d_x, tfs_ctable* t, cudaStream_t st) {
+  double2 *Y = nullptr, *Z = nullptr;
+  const double2* Zp = nullptr;
+  int rc = run_fft_passes(p, d_x, t->n_seg, &Y, &Z, &Zp, st);
+  if (rc == TFS_OK) {
+    dim3 g3((unsigned)((t->n_bin + 255) / 256), (unsigned)t->n_seg);
+    sft_cspec<<<g3, 256, 0, st>>>(Zp, p->N, p->twU, p->zscale, t->z);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "SFT kernels");
+  }
+  if (Y) cudaFreeAsync(Y, st);
+  if (Z) cudaFreeAsync(Z, st);
+  return rc;
 }
 
 // Enqueue the whole strain -> table computation on `st` (device strain; scratch is stream-ordered).
@@ -611,5 +687,90 @@ extern "C" int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, 
   if (tmp) cudaFreeAsync(tmp, st);
   if (rc) return rc;
   if (mem == TFS_MEM_HOST || st == nullptr) TFS_CUDA(cudaStreamSynchronize(st));
+  return TFS_OK;
+}
+
+// ---------------------------------------------------------------- linear-chirp table
+extern "C" int tfs_build_chirp_table(const double* strain, int64_t n, double dt, double T_sft, const double* psd,
+                                     int mem, void* stream, tfs_ctable** out) {
+  clear_error();
+  TFS_CHECK(strain && psd && out, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(dt > 0 && T_sft > 0 && std::isfinite(dt) && std::isfinite(T_sft), TFS_ERR_INVALID_ARG,
+            "dt and T_sft must be positive");
+  TFS_CHECK(mem == TFS_MEM_HOST || mem == TFS_MEM_DEVICE, TFS_ERR_INVALID_ARG, "bad mem kind");
+  const double Lf = T_sft / dt;
+  const int64_t L = (int64_t)std::llround(Lf);
+  TFS_CHECK(L >= 512 && L <= (1 << 20) && std::fabs(Lf - (double)L) <= 1e-9 * Lf, TFS_ERR_INVALID_ARG,
+            "T_sft/dt must be an integer in [512, 2^20]");
+  TFS_CHECK(L % 2 == 0 && smooth235(L), TFS_ERR_INVALID_ARG,
+            "T_sft/dt = %lld must be even with prime factors 2, 3, 5 only", (long long)L);
+  const int64_t n_seg = n / L;
+  TFS_CHECK(n_seg >= 1 && n_seg <= 65535, TFS_ERR_INVALID_ARG, "need 1 <= n/L <= 65535 segments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SftPlan* plan = nullptr;
+  int rc = make_sft_plan(L, dt, TFS_WINDOW_HANN, psd, mem, &plan);
+  if (rc) return rc;
+  tfs_ctable* t = new tfs_ctable();
+  cudaGetDevice(&t->device);
+  t->n_seg = n_seg;
+  t->n_bin = L / 2 + 1;
+  t->T_sft = T_sft;
+  t->dt = dt;
+  t->L = L;
+  t->s_ref = plan->s_ref;
+  t->wt = plan->wt;
+  t->sft_plan = plan;
+  cudaError_t e = cudaMalloc(&t->z, (size_t)n_seg * t->n_bin * sizeof(float2));
+  if (e != cudaSuccess) {
+    tfs_ctable_free(t);
+    return cuda_fail(e, "chirp table");
+  }
+  const double* d_x = strain;
+  double* tmp = nullptr;
+  const size_t xbytes = (size_t)n_seg * L * 8;
+  if (mem == TFS_MEM_HOST) {
+    e = cudaMallocAsync((void**)&tmp, xbytes, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, strain, xbytes, cudaMemcpyHostToDevice, st);
+    d_x = tmp;
+  }
+  rc = e == cudaSuccess ? run_sft_complex(plan, d_x, t, st) : cuda_fail(e, "strain upload");
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (rc == TFS_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "build_chirp_table");
+  }
+  if (rc) {
+    tfs_ctable_free(t);
+    return rc;
+  }
+  *out = t;
+  return TFS_OK;
+}
+
+extern "C" int tfs_ctable_free(tfs_ctable* t) {
+  if (!t) return TFS_OK;
+  if (t->z) cudaFree(t->z);
+  free_sft_plan(t->sft_plan);  // owns wt
+  delete t;
+  return TFS_OK;
+}
+
+extern "C" int tfs_ctable_info(const tfs_ctable* t, int64_t* n_seg, int64_t* n_bin, double* T_sft, double* dt,
+                               double* s_ref) {
+  clear_error();
+  TFS_CHECK(t, TFS_ERR_INVALID_ARG, "null table");
+  if (n_seg) *n_seg = t->n_seg;
+  if (n_bin) *n_bin = t->n_bin;
+  if (T_sft) *T_sft = t->T_sft;
+  if (dt) *dt = t->dt;
+  if (s_ref) *s_ref = t->s_ref;
+  return TFS_OK;
+}
+
+extern "C" int tfs_ctable_to_host(const tfs_ctable* t, float* z, float* wt) {
+  clear_error();
+  TFS_CHECK(t, TFS_ERR_INVALID_ARG, "null table");
+  if (z) TFS_CUDA(cudaMemcpy(z, t->z, (size_t)t->n_seg * t->n_bin * sizeof(float2), cudaMemcpyDeviceToHost));
+  if (wt) TFS_CUDA(cudaMemcpy(wt, t->wt, (size_t)t->n_bin * sizeof(float), cudaMemcpyDeviceToHost));
   return TFS_OK;
 }

@@ -76,6 +76,16 @@ struct tfs_table {
   void* sft_plan = nullptr; // cached SFT plan (window, twiddles, PSD normalisation) when built from strain
 };
 
+struct tfs_ctable {          // linear-chirp table: scaled complex spectra of a Hann-windowed strain
+  int device = 0;
+  int64_t n_seg = 0, n_bin = 0, L = 0;
+  double T_sft = 0.0, dt = 0.0;
+  double s_ref = 1.0;       // reference PSD of the scaling (median of the usable S_n)
+  float2* z = nullptr;      // device [n_seg][n_bin]: sqrt(4 dt / (sum w^2 S_ref)) X_k S_ref / S_k
+  float* wt = nullptr;      // device [n_bin]: S_ref / S_k (owned by the plan)
+  void* sft_plan = nullptr; // the SFT plan (window, twiddles, scales)
+};
+
 struct tfs_basis {
   int device = 0;
   int K = 0;

@@ -70,6 +70,14 @@ def test_host_validation_without_device(L):
     assert L.tfs_eval_batch(jobs, 5000, None, None) == -1
     assert L.tfs_eval_batch(jobs, 2, None, None) == -1
     assert b"job 0" in L.tfs_last_error()
+    # the linear-chirp calls validate before any CUDA call
+    out = P()
+    x = (ctypes.c_double * 1024)()
+    assert L.tfs_build_chirp_table(ctypes.cast(x, P), 1024, 1.0, 256.0, ctypes.cast(x, P), 0, None,
+                                   ctypes.byref(out)) == -1          # L = 256 < 512
+    assert L.tfs_eval_chirp_stat(None, None, None, None, 0, 100, 0, None, 0, None, None, None) == -1
+    assert L.tfs_ctable_info(None, None, None, None, None, None) == -1
+    assert L.tfs_ctable_free(None) == 0
 
 
 def test_tuning_cache_round_trip(L, tmp_path):

@@ -166,6 +166,8 @@ def test_chirp_statistic_brute_force():
             else:
                 fd = (F[t, a + 1] - F[t, a - 1]) / (2 * T)
             b = int(np.floor(F[t, a] * T + 0.5))
+            if b < 0 or b >= nb:
+                continue  # the track's own bin is outside the table
             num, den = 0j, 0.0
             for k in range(b - P, b + P + 1):
                 if k < 1 or k >= nb or not np.isfinite(psd[k]):
