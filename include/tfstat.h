@@ -301,6 +301,22 @@ int tfs_server_get_stats(tfs_server* s, tfs_server_stats* out);
  * and buffers.  Tickets not yet waited for are dropped. */
 int tfs_server_free(tfs_server* s);
 
+/* ---- data chunks and shifted bases (the T_pl search of Sec. II.D) ----------
+ * The paper searches data of growing duration T_obs (0.1 yr, then 12 SFTs more
+ * per chunk, 48 chunks) for a plunge at the end of each chunk, aligning one
+ * precomputed basis (plunge at the end of the year) by an integer time shift.
+ * tfs_table_view: the rows seg0 .. seg0 + n_seg - 1 of a table as a table of
+ * their own, sharing the device memory (no copy; valid while t lives; freeing
+ * the view with tfs_table_free leaves t intact; a view cannot be rebuilt from
+ * strain or handed to a server).  tfs_basis_view: the columns seg0 .. seg0 +
+ * n_seg - 1 of every basis row as a new basis (a device copy of the K x n_seg
+ * slice, with the training statistics copied); for a chunk of n_obs segments
+ * of a year of n_seg, seg0 = n_seg - n_obs puts the basis's plunge at the
+ * chunk's end.  Synchronous.  0 <= seg0, 1 <= n_seg, seg0 + n_seg within the
+ * parent, else INVALID_ARG. */
+int tfs_table_view(const tfs_table* t, int64_t seg0, int64_t n_seg, tfs_table** out);
+int tfs_basis_view(const tfs_basis* b, int64_t seg0, int64_t n_seg, tfs_basis** out);
+
 /* ---- the paper's linear-chirp statistic (Sec. II.B, Eq. det_stat) ----------
  * The full per-segment statistic of the paper: the local waveform of segment
  * alpha is the chirping sinusoid exp(i [2 pi f_a (t - t_a) + pi fdot_a (t - t_a)^2])

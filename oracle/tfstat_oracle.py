@@ -28,6 +28,10 @@ What it computes, step by step, each in the plainest form:
   Eq. det_stat with the chirping sinusoid of Sec. II.B as the local template:
   the template's SFT over the 2P + 1 = 201 bins around the track, fdot from
   the finite differences, |sum d~* h~ / S_n|^2 normalised by <h|h>.
+* ``chunk_layout`` / ``chunk_eval`` / ``noise_moments``: the plunge-time search
+  over data chunks of growing duration with an integer time shift of the
+  basis, and the noise mean and standard deviation that normalise each
+  duration (Sec. II.D).
 
 Readings where the paper is silent (window, normalisation constant, DC bin,
 rounding rule, tie band, out-of-range bins, segment times, quantised
@@ -469,6 +473,49 @@ def chirp_statistic(d, psd_bins, dt: float, T_sft: float, F, P: int = CHIRP_P, v
             Sa = np.where(valid[:, a], Sa, 0.0)
         total += Sa
     return total
+
+
+# --------------------------------------------------------------------------
+# The plunge-time search over data chunks of growing duration (Sec. II.D)
+# --------------------------------------------------------------------------
+JULIAN_YEAR_S = 365.25 * 86400.0
+
+
+def chunk_layout(n_seg: int, T_sft: float, t_min: float = 0.1 * JULIAN_YEAR_S, step: int = 12,
+                 n_chunks: int = 48):
+    """Segments n_obs of each data chunk: the paper starts at 0.1 yr and adds about 7 days
+    (12 SFTs) per chunk, 48 chunks.  Reading: n_obs(c) = floor(t_min / T_SFT) + step c for
+    c = 0 .. n_chunks - 1, a Julian year, chunks longer than the data dropped."""
+    n0 = int(math.floor(t_min / T_sft))
+    return [n0 + step * c for c in range(n_chunks) if 1 <= n0 + step * c <= n_seg]
+
+
+def chunk_eval(P, V, coeffs_list, f_ref_list, n_obs_list, T_sft: float, m: int):
+    """Per chunk c: the statistic (FP64) of its tracks on the data's first n_obs segments,
+    with the basis shifted by an integer number of segments so that its plunge (its last
+    segment) falls at the chunk's end: basis columns n_seg - n_obs .. n_seg - 1."""
+    P = np.asarray(P, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    n_seg = V.shape[1]
+    out = []
+    for c, f, n in zip(coeffs_list, f_ref_list, n_obs_list):
+        S, *_ = eval_stat(P[:n], V[:, n_seg - n:], c, f, T_sft, m, 0)
+        out.append(S)
+    return out
+
+
+def noise_moments(n_a: int, m: int, window_kind: str = "hann"):
+    """(mean, standard deviation) of the nearest-bin statistic over n_a segments of
+    Gaussian noise, the closed form behind the paper's per-duration normalisation
+    (Sec. II.D normalises by the noise mean and standard deviation of each duration).
+    Each P is chi^2_2 (mean 2, variance 4); two bins of one segment covary by
+    4 |rho_d|^2 with rho_d the window's bin correlation at distance d (periodic Hann:
+    |rho_1|^2 = 4/9, |rho_2|^2 = 1/36, none beyond; rectangular: none); segments are
+    independent.  Windows that leave the table are not accounted for."""
+    rho2 = {1: 4.0 / 9.0, 2: 1.0 / 36.0} if window_kind == "hann" else {}
+    W = 2 * m + 1
+    var_seg = 4.0 * (W + 2.0 * sum((W - d) * rho2.get(d, 0.0) for d in range(1, W)))
+    return 2.0 * W * n_a, math.sqrt(var_seg * n_a)
 
 
 # --------------------------------------------------------------------------

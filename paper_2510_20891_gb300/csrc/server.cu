@@ -340,6 +340,7 @@ int tfs_server_add_dataset(tfs_server* s, tfs_table* table, const tfs_basis* bas
   TFS_CHECK(s && table && basis && ds_id, TFS_ERR_INVALID_ARG, "null argument");
   TFS_CHECK(basis->n_seg == table->n_seg, TFS_ERR_INVALID_ARG, "basis and table segment counts differ");
   TFS_CHECK(table->data, TFS_ERR_INVALID_ARG, "table has no device data");
+  TFS_CHECK(table->owns, TFS_ERR_INVALID_ARG, "a table view cannot be handed to a server");
   std::lock_guard<std::mutex> lk(s->mu);
   SrvDataset* d = new SrvDataset();
   d->table = table;

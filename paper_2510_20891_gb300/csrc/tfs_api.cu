@@ -340,9 +340,60 @@ void tfs_debug_last(unsigned long long* out) {
 int tfs_table_free(tfs_table* t) {
   if (!t) return TFS_OK;
   if (t->sft_plan) free_sft_plan(t->sft_plan);
-  if (t->data) cudaFree(t->data);
-  if (t->scales) cudaFree(t->scales);
+  if (t->owns) {
+    if (t->data) cudaFree(t->data);
+    if (t->scales) cudaFree(t->scales);
+  }
   delete t;
+  return TFS_OK;
+}
+
+int tfs_table_view(const tfs_table* t, int64_t seg0, int64_t n_seg, tfs_table** out) {
+  clear_error();
+  TFS_CHECK(t && out, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(t->data, TFS_ERR_INVALID_ARG, "table has no device data");
+  TFS_CHECK(seg0 >= 0 && n_seg >= 1 && seg0 + n_seg <= t->n_seg, TFS_ERR_INVALID_ARG,
+            "rows [%lld, %lld) outside the table's %lld", (long long)seg0, (long long)(seg0 + n_seg),
+            (long long)t->n_seg);
+  tfs_table* v = new tfs_table();
+  v->device = t->device;
+  v->n_seg = n_seg;
+  v->n_bin = t->n_bin;
+  v->row_stride = t->row_stride;
+  v->dtype = t->dtype;
+  v->T_sft = t->T_sft;
+  v->dt = t->dt;
+  v->data = static_cast<char*>(t->data) + (size_t)seg0 * t->row_stride * esize_of(t->dtype);
+  v->scales = t->scales ? t->scales + seg0 : nullptr;
+  v->bytes = 0;
+  v->owns = false;
+  *out = v;
+  return TFS_OK;
+}
+
+int tfs_basis_view(const tfs_basis* b, int64_t seg0, int64_t n_seg, tfs_basis** out) {
+  clear_error();
+  TFS_CHECK(b && out, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(seg0 >= 0 && n_seg >= 1 && seg0 + n_seg <= b->n_seg, TFS_ERR_INVALID_ARG,
+            "segments [%lld, %lld) outside the basis's %lld", (long long)seg0, (long long)(seg0 + n_seg),
+            (long long)b->n_seg);
+  tfs_basis* v = new tfs_basis();
+  v->device = b->device;
+  v->K = b->K;
+  v->n_seg = n_seg;
+  cudaError_t e = cudaMalloc(&v->U, (size_t)b->K * n_seg * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(v->U, (size_t)n_seg * sizeof(double), b->U + seg0, (size_t)b->n_seg * sizeof(double),
+                     (size_t)n_seg * sizeof(double), (size_t)b->K, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    if (v->U) cudaFree(v->U);
+    delete v;
+    return cuda_fail(e, "basis view");
+  }
+  v->sigma = b->sigma;
+  v->cmin = b->cmin;
+  v->cmax = b->cmax;
+  *out = v;
   return TFS_OK;
 }
 

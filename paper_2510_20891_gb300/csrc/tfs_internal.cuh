@@ -74,6 +74,7 @@ struct tfs_table {
   int64_t bytes = 0;
   double dt = 0.0;
   void* sft_plan = nullptr; // cached SFT plan (window, twiddles, PSD normalisation) when built from strain
+  bool owns = true;         // false for a view: data and scales belong to another table
 };
 
 struct tfs_ctable {          // linear-chirp table: scaled complex spectra of a Hann-windowed strain

@@ -207,3 +207,4 @@ def test_chirp_statistic_mask():
     S = O.chirp_statistic(d, psd, dt, T, F, valid=valid)
     assert np.allclose(S, np.sum(np.where(valid, per, 0.0), axis=1), rtol=1e-12)
     assert not np.allclose(full, per)  # fdot matters
+
