@@ -317,6 +317,24 @@ int tfs_server_free(tfs_server* s);
 int tfs_table_view(const tfs_table* t, int64_t seg0, int64_t n_seg, tfs_table** out);
 int tfs_basis_view(const tfs_basis* b, int64_t seg0, int64_t n_seg, tfs_basis** out);
 
+/* ---- differential evolution of a walker population (Sec. II.D, Eq. de_step) --
+ * The paper's track-space DE without crossover: for every walker t,
+ * f_trial = f_t + F_t (f_r1[t] - f_r2[t]), projected back to coefficients by the
+ * basis pseudo-inverse and kept when it lies in the prior and raises the
+ * statistic.  Tracks are linear in the coefficients, so the projection of the
+ * proposal is exactly c_t + F_t (c_r1 - c_r2); both calls work on coefficients.
+ * tfs_de_propose: c [N][K] (FP64), r1, r2 [N] (int32 walker indices into c),
+ * F [N] (float, the paper draws it from U[0.3, 1.5]), lo, hi [K] (the prior
+ * box) -> c_trial [N][K] and in_prior [N] (1 when every coefficient lies in
+ * [lo, hi]).  tfs_de_accept: where in_prior[t] and s_trial[t] > s[t], copies
+ * c_trial[t] into c[t] and s_trial[t] into s[t].  All pointers device pointers
+ * of the current device; random draws are the caller's; stream-ordered and
+ * asynchronous.  N in [0, 2^31), K in [1, 32]. */
+int tfs_de_propose(const double* c, int64_t N, int K, const int32_t* r1, const int32_t* r2, const float* F,
+                   const double* lo, const double* hi, double* c_trial, int32_t* in_prior, void* stream);
+int tfs_de_accept(double* c, float* s, const double* c_trial, const float* s_trial, const int32_t* in_prior,
+                  int64_t N, int K, void* stream);
+
 /* ---- the paper's linear-chirp statistic (Sec. II.B, Eq. det_stat) ----------
  * The full per-segment statistic of the paper: the local waveform of segment
  * alpha is the chirping sinusoid exp(i [2 pi f_a (t - t_a) + pi fdot_a (t - t_a)^2])

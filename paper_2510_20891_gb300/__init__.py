@@ -173,6 +173,22 @@ def basis_from_host(U) -> Basis:
     return Basis(h)
 
 
+def table_view(table: Table, seg0: int, n_seg: int) -> Table:
+    """Rows seg0 .. seg0 + n_seg - 1 of `table`, sharing its device memory (tfs_table_view)."""
+    h = ctypes.c_void_p()
+    check(lib().tfs_table_view(table.handle, int(seg0), int(n_seg), ctypes.byref(h)))
+    v = Table(h)
+    v._parent = table  # the view's memory belongs to the parent
+    return v
+
+
+def basis_view(basis: Basis, seg0: int, n_seg: int) -> Basis:
+    """Columns seg0 .. seg0 + n_seg - 1 of every basis row, as a new basis (tfs_basis_view)."""
+    h = ctypes.c_void_p()
+    check(lib().tfs_basis_view(basis.handle, int(seg0), int(n_seg), ctypes.byref(h)))
+    return Basis(h)
+
+
 class _TieReport(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("n_stored", ctypes.c_int32), ("capacity", ctypes.c_int32),
                 ("track", ctypes.c_void_p), ("seg", ctypes.c_void_p)]

@@ -48,6 +48,8 @@ SIGNATURES = {
     "tfs_server_free": (I, [P]),
     "tfs_table_view": (I, [P, I64, I64, P]),
     "tfs_basis_view": (I, [P, I64, I64, P]),
+    "tfs_de_propose": (I, [P, I64, I, P, P, P, P, P, P, P, P]),
+    "tfs_de_accept": (I, [P, P, P, P, P, I64, I, P]),
     "tfs_build_chirp_table": (I, [P, I64, D, D, P, I, P, P]),
     "tfs_ctable_info": (I, [P, P, P, P, P, P]),
     "tfs_ctable_to_host": (I, [P, P, P]),

@@ -1,0 +1,194 @@
+"""The paper's plunge-time search (Sec. II.D) as a client of the batched statistic.
+
+* ``ChunkSearch``: data chunks of growing duration (0.1 yr, then 12 SFTs more per chunk,
+  48 chunks), each the first n_obs rows of one table (a view, no copy) with the basis
+  shifted by an integer number of segments so that its plunge falls at the chunk's end;
+  the populations of all chunks are evaluated by one ``eval_batch`` call (one persistent
+  launch per table dtype).  ``noise_moments`` gives the mean and standard deviation of the
+  nearest-bin statistic under noise that normalise each duration.
+* ``DESearch``: the population driver: 1024 candidates per chunk drawn uniformly in the
+  prior box with the initial frequency drawn uniformly in [5e-4, 1e-2] Hz, the best 512
+  kept, then iterations of track-space differential evolution without crossover
+  (Eq. de_step, F_DE ~ U[0.3, 1.5]) with greedy acceptance inside the prior, every
+  iteration one batched statistic launch plus the proposal and acceptance kernels.
+  The gradient (Adam) half of the paper's iterations is not reproduced: the nearest-bin
+  statistic is piecewise constant in the coefficients.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import Job, basis_view, check, eval_batch, lib, table_view
+
+JULIAN_YEAR_S = 365.25 * 86400.0
+
+
+def chunk_sizes(n_seg: int, T_sft: float, t_min_yr: float = 0.1, step: int = 12, n_chunks: int = 48):
+    """Segments of each chunk: floor(0.1 yr / T_SFT) + 12 c, c = 0..47, those that fit."""
+    n0 = int(math.floor(t_min_yr * JULIAN_YEAR_S / T_sft))
+    return [n0 + step * c for c in range(n_chunks) if 1 <= n0 + step * c <= n_seg]
+
+
+def noise_moments(n_segments: int, m: int, window: str = "hann"):
+    """(mean, std) of the nearest-bin statistic over n_segments of Gaussian noise: per bin
+    chi^2_2 (mean 2, variance 4), bins of one segment covarying by 4 |rho_d|^2 (periodic
+    Hann: |rho_1|^2 = 4/9, |rho_2|^2 = 1/36; rectangular: 0), segments independent."""
+    corr = (0.0, 4.0 / 9.0, 1.0 / 36.0) if window == "hann" else (0.0, 0.0, 0.0)
+    width = 2 * m + 1
+    var = float(width)
+    for d in range(1, min(width, 3)):
+        var += 2.0 * (width - d) * corr[d]
+    return 2.0 * width * n_segments, math.sqrt(4.0 * var * n_segments)
+
+
+class ChunkSearch:
+    """Chunks of one table (views) with their shifted bases."""
+
+    def __init__(self, table, basis, sizes=None):
+        self.table, self.basis = table, basis
+        self.sizes = list(sizes) if sizes is not None else chunk_sizes(table.n_seg, table.T_sft)
+        self.tables = [table_view(table, 0, n) for n in self.sizes]
+        self.bases = [basis_view(basis, basis.n_seg - n, n) for n in self.sizes]
+
+    def jobs(self, coeffs, f_ref=None, m: int = 0, topk: int = 0, segment_cuts: bool = False, stats=None):
+        """One Job per chunk; coeffs (and f_ref, stats) are per-chunk CUDA tensors."""
+        out = []
+        for i, c in enumerate(coeffs):
+            out.append(Job(self.tables[i], self.bases[i], c, f_ref[i] if f_ref is not None else None, m=m,
+                           topk=topk, stat=stats[i] if stats is not None else None, segment_cuts=segment_cuts))
+        return out
+
+    def evaluate(self, coeffs, f_ref=None, m: int = 0, topk: int = 0, segment_cuts: bool = False, stats=None,
+                 dev_status=None, stream=None):
+        """All chunks' statistics in one eval_batch call; returns the Jobs (their .stat, .top_*)."""
+        jobs = self.jobs(coeffs, f_ref, m, topk, segment_cuts, stats)
+        eval_batch(jobs, dev_status=dev_status, stream=stream)
+        return jobs
+
+    def moments(self, m: int, window: str = "hann"):
+        return [noise_moments(n, m, window) for n in self.sizes]
+
+
+@dataclasses.dataclass
+class DEResult:
+    coeffs: list            # per chunk: best walker's coefficients [K] (numpy)
+    stat: np.ndarray        # per chunk: its statistic
+    normalised: np.ndarray  # per chunk: (stat - mean) / std under noise
+    evaluations: int        # statistic evaluations made
+    seconds: float          # wall time of the whole search (device synchronised)
+
+
+class DESearch:
+    """Differential-evolution population search over the chunks of a ChunkSearch."""
+
+    def __init__(self, search: ChunkSearch, lo, hi, m: int = 0, n_init: int = 1024, n_walkers: int = 512,
+                 f_start=(5e-4, 1e-2), seed: int = 0, graph: bool = True, segment_cuts: bool = False):
+        self.s, self.m = search, m
+        self.lo, self.hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+        self.n_init, self.n_walkers = n_init, n_walkers
+        self.f_start = f_start
+        self.rng = np.random.default_rng(seed)
+        self.K = self.lo.size
+        self.graph = graph
+        self.cuts = segment_cuts  # the paper's exclusions (Sec. II.B, II.D)
+
+    def _initial(self, U_chunk):
+        """n_init candidates uniform in the prior box, each track shifted by a constant so that
+        its first-segment frequency is uniform in f_start, then projected back onto the
+        chunk's basis (least squares)."""
+        c = self.lo + (self.hi - self.lo) * self.rng.random((self.n_init, self.K))
+        f0 = c @ U_chunk[:, 0]
+        target = self.rng.uniform(*self.f_start, self.n_init)
+        ones_c = np.linalg.lstsq(U_chunk.T, np.ones(U_chunk.shape[1]), rcond=None)[0]
+        return c + (target - f0)[:, None] * ones_c[None, :]
+
+    def run(self, n_iter: int = 525, stream=None, U_full=None):
+        import time
+
+        import torch
+
+        s, K, W = self.s, self.K, self.n_walkers
+        n_ch = len(s.sizes)
+        if U_full is None:
+            U_full, *_ = s.basis.to_host()
+        dev = torch.device("cuda")
+        L = lib()
+        t0 = time.perf_counter()
+        # initial population, best n_walkers per chunk
+        init = [torch.tensor(self._initial(U_full[:, U_full.shape[1] - n:]), device=dev) for n in s.sizes]
+        jobs = s.evaluate(init, m=self.m, topk=W, segment_cuts=self.cuts, stream=stream)
+        c = torch.cat([init[i][jobs[i].top_idx] for i in range(n_ch)])          # [n_ch W, K]
+        st = torch.cat([jobs[i].top_val for i in range(n_ch)]).contiguous()
+        evals = n_ch * self.n_init
+        lo = torch.tensor(self.lo, device=dev)
+        hi = torch.tensor(self.hi, device=dev)
+        ct = torch.empty_like(c)
+        s_trial = torch.empty_like(st)
+        inp = torch.empty(n_ch * W, dtype=torch.int32, device=dev)
+        views = [ct[i * W:(i + 1) * W] for i in range(n_ch)]
+        stats = [s_trial[i * W:(i + 1) * W] for i in range(n_ch)]
+        trial_jobs = s.jobs(views, m=self.m, stats=stats, segment_cuts=self.cuts)
+        base = (np.arange(n_ch) * W).repeat(W)
+        # the random draws of every iteration (r1 != r2 != t within the walker's own chunk,
+        # F_DE ~ U[0.3, 1.5]), made up front and uploaded once
+        n = n_ch * W
+        t_loc = np.tile(np.arange(W), n_ch)
+        R1 = np.empty((n_iter, n), np.int32)
+        R2 = np.empty((n_iter, n), np.int32)
+        FF = np.empty((n_iter, n), np.float32)
+        for it in range(n_iter):
+            r1 = (t_loc + self.rng.integers(1, W, n)) % W
+            r2 = (t_loc + self.rng.integers(1, W - 1, n)) % W
+            r2 = np.where(r2 == r1, (r2 + 1) % W, r2)
+            r2 = np.where(r2 == t_loc, (r2 + 1) % W, r2)
+            r2 = np.where(r2 == r1, (r2 + 1) % W, r2)
+            R1[it] = base + r1
+            R2[it] = base + r2
+            FF[it] = self.rng.uniform(0.3, 1.5, n)
+        R1_d, R2_d, FF_d = (torch.tensor(a, device=dev) for a in (R1, R2, FF))
+        r1_b = torch.empty(n, dtype=torch.int32, device=dev)
+        r2_b = torch.empty(n, dtype=torch.int32, device=dev)
+        F_b = torch.empty(n, dtype=torch.float32, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        side = torch.cuda.Stream() if stream is None else stream
+
+        def iteration(strm):
+            sp = strm.cuda_stream
+            check(L.tfs_de_propose(c.data_ptr(), n, K, r1_b.data_ptr(), r2_b.data_ptr(), F_b.data_ptr(),
+                                   lo.data_ptr(), hi.data_ptr(), ct.data_ptr(), inp.data_ptr(), sp))
+            eval_batch(trial_jobs, dev_status=status, stream=sp)
+            check(L.tfs_de_accept(c.data_ptr(), st.data_ptr(), ct.data_ptr(), s_trial.data_ptr(), inp.data_ptr(),
+                                  n, K, sp))
+
+        if n_iter > 0:
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                graph = None
+                if self.graph:
+                    # one propose + batched statistic + accept, captured once and replayed
+                    r1_b.copy_(R1_d[0]); r2_b.copy_(R2_d[0]); F_b.copy_(FF_d[0])
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph, stream=side):
+                        iteration(side)
+                for it in range(n_iter):
+                    r1_b.copy_(R1_d[it]); r2_b.copy_(R2_d[it]); F_b.copy_(FF_d[it])
+                    if graph is not None:
+                        graph.replay()
+                    else:
+                        iteration(side)
+                    evals += n
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            if int(status.item()) != 0:
+                raise RuntimeError("a bounded device wait gave up during the search")
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        st_h = st.cpu().numpy().reshape(n_ch, W)
+        c_h = c.cpu().numpy().reshape(n_ch, W, K)
+        best = st_h.argmax(axis=1)
+        stat = st_h[np.arange(n_ch), best].astype(np.float64)
+        mom = np.array(s.moments(self.m))
+        return DEResult([c_h[i, best[i]] for i in range(n_ch)], stat, (stat - mom[:, 0]) / mom[:, 1], evals, secs)

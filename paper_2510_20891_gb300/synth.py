@@ -42,6 +42,13 @@ def psd_oneyear(f):
     return np.where(f > 0, s, np.inf)
 
 
+def psd_oneyear_hp(f):
+    """psd_oneyear held at its 1e-4 Hz value below 1e-4 Hz (data high-passed at 1e-4 Hz): the
+    f^-4 wall would otherwise leak through the window's sidelobes into the lowest SFT bins."""
+    f = np.asarray(f, dtype=np.float64)
+    return np.where(f > 0, psd_oneyear(np.maximum(f, 1e-4)), np.inf)
+
+
 def psd_bins(psd_fn, n_bin: int, T_sft: float):
     """PSD sampled at the SFT bin frequencies k / T_sft, k = 0..n_bin-1."""
     return psd_fn(np.arange(n_bin, dtype=np.float64) / T_sft)
@@ -183,6 +190,8 @@ class Workload:
     def psd_fn(self):
         if self.psd == "white":
             return lambda f: psd_white(f, 1.0, self.dt)
+        if self.psd == "oneyear_hp":
+            return psd_oneyear_hp
         return psd_oneyear
 
 
@@ -193,6 +202,10 @@ WORKLOADS = {
     "oneyear_daily_fp32": Workload("oneyear_daily_fp32", 5.0, 6_307_200, 86400.0, 6, 10_000_000, 1, 5000,
                                    "powerlaw", "oneyear"),
     # finer resolution: 1577 x 20000-s segments x 20001 bins (sampled at 0.5 s so segments are full).
+    # the plunge-time search of Sec. II.D: one Julian year at 5 s in 631 SFTs of 5e4 s, a K = 6 basis of
+    # tracks that plunge just after the year, the chunks of 0.1 yr + 12 SFTs, +-1-bin neighbours.
+    "oneyear_5e4_631": Workload("oneyear_5e4_631", 5.0, 631 * 10_000, 50_000.0, 6, 48 * 512, 1, 5000,
+                                "powerlaw", "oneyear_hp", tau_yr=(1.0005, 1.05)),
     "oneyear_fine_1577x20001": Workload("oneyear_fine_1577x20001", 0.5, 1577 * 40000, 20000.0, 6,
                                         100_000_000, 1, 5000, "powerlaw", "oneyear"),
 }
@@ -207,11 +220,12 @@ def make_strain(w: Workload, rng: np.random.Generator, snr: float | None = None,
         if inject:
             x = x + chirp_signal(n, dt, inj["f0"], inj["fdot"], inj["amp"])
         return x, inj
-    x = coloured_noise(n, dt, psd_oneyear, rng)
+    psd_fn = w.psd_fn()
+    x = coloured_noise(n, dt, psd_fn, rng)
     f0, tau, p = powerlaw_params(1, rng, tau_yr=w.tau_yr)
     inj = dict(kind="powerlaw", f0=float(f0[0]), tau=float(tau[0]), p=float(p[0]), snr=30.0 if snr is None else snr)
     if inject:
-        a0 = powerlaw_amplitude_for_snr(n, dt, inj["f0"], inj["tau"], inj["p"], inj["snr"], psd_oneyear)
+        a0 = powerlaw_amplitude_for_snr(n, dt, inj["f0"], inj["tau"], inj["p"], inj["snr"], psd_fn)
         inj["a0"] = a0
         x = x + powerlaw_signal(n, dt, inj["f0"], inj["tau"], inj["p"], a0)
     return x, inj
