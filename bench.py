@@ -588,6 +588,11 @@ def run_tpl_search(args):
     U, sig, cmin, cmax = basis.to_host()
     cs = search.ChunkSearch(table, basis)
     n_iter = args.steps
+    W = 512
+    if not args.no_autotune:
+        # launch shape for one iteration's batch (48 chunk jobs of 512 walkers, with the cuts)
+        tune_c = [torch.tensor(cmin + (cmax - cmin) * rng.random((W, w.K)), device="cuda") for _ in cs.sizes]
+        shape, _ = T.autotune(cs.jobs(tune_c, m=w.m, segment_cuts=True), reps=3)
     # warm-up: a short search builds the cached per-chunk data and the graph machinery
     search.DESearch(cs, cmin, cmax, m=w.m, seed=1, segment_cuts=True).run(n_iter=max(1, args.warmup), U_full=U)
     torch.cuda.synchronize()
@@ -596,7 +601,6 @@ def run_tpl_search(args):
         res = search.DESearch(cs, cmin, cmax, m=w.m, seed=2, segment_cuts=True).run(n_iter=n_iter, U_full=U)
     launches = L.tfs_kernel_launches() - launches0
     # device time of one iteration's batched statistic launch (events around an uncaptured call)
-    W = 512
     coeffs = [torch.tensor(cmin + (cmax - cmin) * rng.random((W, w.K)), device="cuda") for _ in cs.sizes]
     stats = [torch.empty(W, device="cuda") for _ in cs.sizes]
     jobs = cs.jobs(coeffs, m=w.m, stats=stats, segment_cuts=True)
@@ -636,6 +640,7 @@ def run_tpl_search(args):
             "config": {"workload": "oneyear_5e4_631 plunge-time search", "n_seg": w.n_seg, "n_bin": w.n_bin,
                        "K": w.K, "m": w.m, "chunks": len(cs.sizes), "chunk_segments": [cs.sizes[0], cs.sizes[-1]],
                        "walkers": W, "initial": 1024, "iterations": n_iter, "table_dtype": args.dtype,
+                       "launch_shape": None if args.no_autotune else shape,
                        "l2": "the 12.6 MB table and every chunk's walkers stay in L2"},
             "search": {"evaluations": res.evaluations, "seconds": res.seconds, "segment_cuts": True,
                        "best_chunk_segments": cs.sizes[best], "best_stat": float(res.stat[best]),

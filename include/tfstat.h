@@ -232,8 +232,8 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
  * Not part of the paper's method: it picks how the statistic kernel is laid
  * out for a kind of workload.  pcap is the number of table elements of one
  * segment's band staged per tile (wide bands beyond it take a slower path),
- * tile_div divides the tracks per tile (smaller tiles: more of them, better
- * balance for small jobs).  tfs_autotune_batch evaluates `jobs` (as
+ * tile_div (1, 2, 4 or 8) divides the tracks per tile (smaller tiles: more of
+ * them, better balance for small jobs).  tfs_autotune_batch evaluates `jobs` (as
  * tfs_eval_batch, overwriting their outputs) under every candidate shape,
  * `reps` times each, and keeps the fastest for every launch of this kind
  * (table dtype, coefficient slots, widest row and longest job in powers of

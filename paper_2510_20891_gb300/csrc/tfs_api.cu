@@ -729,9 +729,9 @@ int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* be
   tfs_tuning win{0, 0};
   std::vector<std::string> keys;
   const int caps[] = {512, 1024, 2048, 3072, 4096};
-  const int divs[] = {1, 2};
+  const int divs[] = {1, 2, 4, 8};
   for (int ci = 0; ci < 5 && rc == TFS_OK; ++ci) {
-    for (int di = 0; di < 2 && rc == TFS_OK; ++di) {
+    for (int di = 0; di < 4 && rc == TFS_OK; ++di) {
       EvalTuning t;
       t.cap = caps[ci];
       t.tile_div = divs[di];

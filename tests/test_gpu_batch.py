@@ -195,7 +195,7 @@ def test_autotuned_launch_shape(T):
     data = _make_jobs(T, torch, SPECS[:3] + SPECS[5:6], seed=31)
     jobs = [T.Job(d["table"], d["basis"], d["dc"], d["df"], m=d["m"], topk=d["topk"]) for d in data]
     shape, ms = T.autotune(jobs, reps=2)
-    assert shape["pcap"] in (512, 1024, 2048, 3072, 4096) and shape["tile_div"] in (1, 2) and ms > 0
+    assert shape["pcap"] in (512, 1024, 2048, 3072, 4096) and shape["tile_div"] in (1, 2, 4, 8) and ms > 0
     jobs2 = _batch(T, torch, data)
     for d, j in zip(data, jobs2):
         Pq, _ = d["table"].to_host()
