@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--stat-error", type=int, default=0,
                     help="also report the statistic's error against the FP64 oracle on the exact table, "
                          "over this many sampled tracks")
+    ap.add_argument("--statistic", default="nearest", choices=["nearest", "chirp"],
+                    help="plunge-time search: the nearest-bin statistic or the paper's linear-chirp statistic")
     ap.add_argument("--segment-cuts", action="store_true",
                     help="apply the segment exclusions (second-order, low-frequency and low-fdot cuts)")
     ap.add_argument("--batch-jobs", type=int, default=64, help="datasets of the batched workload")
@@ -583,42 +585,74 @@ def run_tpl_search(args):
     L = T.lib()
     w = synth.WORKLOADS["oneyear_5e4_631"]
     x, psd, F, inj, rng = make_inputs(w, 0, 0)
-    table = T.build_sfts(torch.from_numpy(x).cuda(), w.dt, w.T_sft, psd, "hann", args.dtype)
+    chirp = args.statistic == "chirp"
+    x_d = torch.from_numpy(x).cuda()
+    table = T.build_sfts(x_d, w.dt, w.T_sft, psd, "hann", args.dtype)
+    ct = T.build_chirp_table(x_d, w.dt, w.T_sft, psd) if chirp else None
     basis = T.build_basis(F, w.K)
     U, sig, cmin, cmax = basis.to_host()
-    cs = search.ChunkSearch(table, basis)
+    cs = search.ChunkSearch(table, basis, chirp_table=ct)
     n_iter = args.steps
     W = 512
-    if not args.no_autotune:
+    shape = None
+    if not args.no_autotune and not chirp:
         # launch shape for one iteration's batch (48 chunk jobs of 512 walkers, with the cuts)
         tune_c = [torch.tensor(cmin + (cmax - cmin) * rng.random((W, w.K)), device="cuda") for _ in cs.sizes]
         shape, _ = T.autotune(cs.jobs(tune_c, m=w.m, segment_cuts=True), reps=3)
     # warm-up: a short search builds the cached per-chunk data and the graph machinery
-    search.DESearch(cs, cmin, cmax, m=w.m, seed=1, segment_cuts=True).run(n_iter=max(1, args.warmup), U_full=U)
+    search.DESearch(cs, cmin, cmax, m=w.m, seed=1, segment_cuts=True,
+                    statistic=args.statistic).run(n_iter=max(1, args.warmup), U_full=U)
     torch.cuda.synchronize()
     launches0 = L.tfs_kernel_launches()
     with ClockSampler(0) as clk:
-        res = search.DESearch(cs, cmin, cmax, m=w.m, seed=2, segment_cuts=True).run(n_iter=n_iter, U_full=U)
+        res = search.DESearch(cs, cmin, cmax, m=w.m, seed=2, segment_cuts=True,
+                              statistic=args.statistic).run(n_iter=n_iter, U_full=U)
     launches = L.tfs_kernel_launches() - launches0
     # device time of one iteration's batched statistic launch (events around an uncaptured call)
     coeffs = [torch.tensor(cmin + (cmax - cmin) * rng.random((W, w.K)), device="cuda") for _ in cs.sizes]
     stats = [torch.empty(W, device="cuda") for _ in cs.sizes]
-    jobs = cs.jobs(coeffs, m=w.m, stats=stats, segment_cuts=True)
+    jobs = cs.jobs(coeffs, m=w.m, stats=stats, segment_cuts=True, statistic=args.statistic)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    T.eval_batch(jobs, dev_status=status)
+    cs.launch(jobs, args.statistic, dev_status=status)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(20):
-        T.eval_batch(jobs, dev_status=status)
+        cs.launch(jobs, args.statistic, dev_status=status)
     e1.record()
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / 20
     pairs = W * sum(cs.sizes)
     bytes_batch = sum(W * (n * (2 * w.m + 1) * 4 + 8 * w.K + 4) for n in cs.sizes)
-    peak, peak_kind = measured_peaks()
-    achieved = bytes_batch / (batch_ms / 1e3) / 1e9
+    if chirp:
+        flops_pair = 5 * 512 * 9 + 6 * 512 + 12 * (2 * T.CHIRP_P + 1)
+        achieved = pairs * flops_pair / (batch_ms / 1e3) / 1e12
+        sm_mhz = 2070.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "unit": "TFLOP/s",
+                "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                "flops_per_pair": flops_pair, "kernel": "chirp_stat_kernel (48 chunk jobs)"}
+    else:
+        peak, peak_kind = measured_peaks()
+        achieved = bytes_batch / (batch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_iteration": bytes_batch,
+                "kernel": "eval_stat_kernel (48 chunk jobs)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and chirp:
+        import oracle.tfstat_oracle as O
+
+        d = O.sft(x, w.dt, w.T_sft)
+        n = cs.sizes[-1]
+        c_s = cmin + (cmax - cmin) * rng.random((4, w.K))
+        t0 = time.perf_counter()
+        Fs = O.track_freqs(U[:, w.n_seg - n:], c_s, np.zeros(4))
+        O.chirp_statistic(d[:n], psd, w.dt, w.T_sft, Fs, valid=O.segment_validity(Fs, w.T_sft))
+        t_s = time.perf_counter() - t0
+        per_pair = t_s / (4 * n)
+        cpu = {"value": res.evaluations / (per_pair * (pairs * (n_iter + 2))), "unit": "evals/s", "cores": 1,
+               "kind": "oracle", "sample": f"masked linear-chirp statistic of 4 walkers of the {n}-segment chunk "
+                                           f"({t_s:.2f} s, one process), scaled by track-segment pairs"}
+    elif not args.no_cpu_baseline:
         import oracle.tfstat_oracle as O
 
         P64 = O.power_table(x, w.dt, w.T_sft, psd)
@@ -632,24 +666,23 @@ def run_tpl_search(args):
         cpu = {"value": res.evaluations / (per_pair * (pairs * (n_iter + 2))), "unit": "evals/s", "cores": 1,
                "kind": "oracle", "sample": f"masked statistic of 4 chunks x {W} walkers ({t_s:.2f} s, one process), "
                                            "scaled by track-segment pairs to the whole search"}
-    best = int(np.argmax(res.normalised))
-    line = {"metric": "plunge-time search statistic evaluations/s (48 chunks x (1024 + iterations x 512))",
+    best = int(np.argmax(res.stat if chirp else res.normalised))
+    line = {"metric": "plunge-time search statistic evaluations/s (48 chunks x (1024 + iterations x 512))"
+                      + (", linear-chirp statistic" if chirp else ""),
             "value": res.evaluations / res.seconds, "unit": "evals/s", "n_gpus": 1, "steps": n_iter,
             "warmup": args.warmup, "ms_per_step": res.seconds / max(1, n_iter) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": "oneyear_5e4_631 plunge-time search", "n_seg": w.n_seg, "n_bin": w.n_bin,
                        "K": w.K, "m": w.m, "chunks": len(cs.sizes), "chunk_segments": [cs.sizes[0], cs.sizes[-1]],
                        "walkers": W, "initial": 1024, "iterations": n_iter, "table_dtype": args.dtype,
-                       "launch_shape": None if args.no_autotune else shape,
+                       "launch_shape": shape, "statistic": args.statistic,
                        "l2": "the 12.6 MB table and every chunk's walkers stay in L2"},
             "search": {"evaluations": res.evaluations, "seconds": res.seconds, "segment_cuts": True,
                        "best_chunk_segments": cs.sizes[best], "best_stat": float(res.stat[best]),
-                       "best_normalised": float(res.normalised[best]),
+                       "best_normalised": None if chirp else float(res.normalised[best]),
                        "injection": {k: float(v) for k, v in inj.items() if k != "kind"}},
             "breakdown_ms": {"batched_statistic_per_iteration": batch_ms},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                         "bytes_per_iteration": bytes_batch, "kernel": "eval_stat_kernel (48 chunk jobs)"},
+            "roofline": roof,
             "e2e": {"value": res.evaluations / res.seconds, "unit": "evals/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                     "note": "the whole search is host-driven; its random draws are uploaded once before the "

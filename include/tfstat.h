@@ -377,6 +377,25 @@ int tfs_eval_chirp_stat(const tfs_ctable* ct, const tfs_basis* basis, const doub
                         int64_t N, int P, int flags, float* stat, int topk, int64_t* top_idx, float* top_val,
                         void* stream);
 
+/* Linear-chirp statistic of many jobs in one launch (up to 64 per launch;
+ * larger batches are split): each job as tfs_eval_chirp_stat without top-k
+ * (coeffs [N][K], f_ref [N] or NULL, stat [N]: device pointers; 0 <= P <= 111;
+ * flags 0 or TFS_JOB_SEGMENT_CUTS).  1 <= n_jobs <= 4096; stream-ordered and
+ * asynchronous.  tfs_ctable_view: rows seg0 .. seg0 + n_seg - 1 of a chirp
+ * table sharing its memory (as tfs_table_view; freed with tfs_ctable_free). */
+typedef struct tfs_chirp_job {
+  const tfs_ctable* table;
+  const tfs_basis* basis;
+  const double* coeffs; /* [N][K] */
+  const double* f_ref;  /* [N] or NULL */
+  int64_t N;
+  int32_t P;
+  int32_t flags;
+  float* stat;          /* [N] */
+} tfs_chirp_job;
+int tfs_eval_chirp_batch(const tfs_chirp_job* jobs, int n_jobs, void* stream);
+int tfs_ctable_view(const tfs_ctable* t, int64_t seg0, int64_t n_seg, tfs_ctable** out);
+
 /* Number of kernels this library has launched in this process (all devices). */
 long long tfs_kernel_launches(void);
 

@@ -270,6 +270,44 @@ def eval_chirp_stat(ctable: ChirpTable, basis: Basis, coeffs, f_ref=None, P: int
     return stat, top_idx, top_val
 
 
+def ctable_view(ctable: ChirpTable, seg0: int, n_seg: int) -> ChirpTable:
+    """Rows seg0 .. seg0 + n_seg - 1 of a chirp table, sharing its memory (tfs_ctable_view)."""
+    h = ctypes.c_void_p()
+    check(lib().tfs_ctable_view(ctable.handle, int(seg0), int(n_seg), ctypes.byref(h)))
+    v = ChirpTable(h)
+    v._parent = ctable
+    return v
+
+
+@dataclasses.dataclass
+class ChirpJob:
+    """One job of a batched linear-chirp evaluation (struct tfs_chirp_job); CUDA tensors."""
+
+    table: ChirpTable
+    basis: Basis
+    coeffs: object
+    f_ref: object = None
+    P: int = CHIRP_P
+    segment_cuts: bool = False
+    stat: object = None
+
+
+def eval_chirp_batch(jobs, stream=None):
+    """The linear-chirp statistic of many jobs in one launch (tfs_eval_chirp_batch); a Job's
+    missing stat is allocated here.  Asynchronous on `stream`."""
+    torch = _torch()
+    arr = (_lib.TfsChirpJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        N = j.coeffs.shape[0]
+        if j.stat is None:
+            j.stat = torch.empty(N, dtype=torch.float32, device=j.coeffs.device)
+        arr[i] = _lib.TfsChirpJob(j.table.handle, j.basis.handle, _ptr(j.coeffs),
+                                  _ptr(j.f_ref) if j.f_ref is not None else None, N, int(j.P),
+                                  _lib.JOB_SEGMENT_CUTS if j.segment_cuts else 0, _ptr(j.stat))
+    check(lib().tfs_eval_chirp_batch(arr, len(jobs), _stream_ptr(stream)))
+    return jobs
+
+
 @dataclasses.dataclass
 class EvalResult:
     stat: object            # [N] float32 (numpy, or torch on the device)

@@ -51,6 +51,8 @@ SIGNATURES = {
     "tfs_de_propose": (I, [P, I64, I, P, P, P, P, P, P, P, P]),
     "tfs_de_accept": (I, [P, P, P, P, P, I64, I, P]),
     "tfs_build_chirp_table": (I, [P, I64, D, D, P, I, P, P]),
+    "tfs_ctable_view": (I, [P, I64, I64, P]),
+    "tfs_eval_chirp_batch": (I, [P, I, P]),
     "tfs_ctable_info": (I, [P, P, P, P, P, P]),
     "tfs_ctable_to_host": (I, [P, P, P]),
     "tfs_ctable_free": (I, [P]),
@@ -92,6 +94,21 @@ class TfsJob(ctypes.Structure):
 
 
 JOB_SEGMENT_CUTS = 1  # TFS_JOB_SEGMENT_CUTS
+
+
+class TfsChirpJob(ctypes.Structure):
+    """struct tfs_chirp_job (include/tfstat.h): one job of a batched linear-chirp launch."""
+
+    _fields_ = [
+        ("table", P),
+        ("basis", P),
+        ("coeffs", P),
+        ("f_ref", P),
+        ("N", I64),
+        ("P", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+        ("stat", P),
+    ]
 
 ERR_NAMES = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY", -6: "NOT_FOUND"}
 

@@ -16,8 +16,10 @@
 // template within aliasing of order 1 / (2 pi (512 - P - beta / 2)^3) of its peak.  The
 // scaled complex table (L2-resident) supplies the data bins; sums in FP32, S_alpha summed
 // over segments in FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "tfs_internal.cuh"
 
@@ -30,7 +32,9 @@ constexpr int kCThreads = 32 * kCW;
 constexpr int kChirpPMax = 111;   // the output mapping covers |j| <= 111
 constexpr double kFLow = 0x1.4b96be9c2da2cp-12;  // 10^-3.5 Hz, the nearest double
 
-struct ChirpArgs {
+constexpr int kChirpMaxJobs = 64;  // jobs per launch
+
+struct ChirpJob {
   const float2* z;      // [n_seg][n_bin]
   const float* wt;      // [n_bin]
   int n_seg, n_bin;
@@ -42,6 +46,12 @@ struct ChirpArgs {
   double T;
   int P, cuts;
   float* stat;          // [N]
+};
+
+struct ChirpBatch {
+  ChirpJob jobs[kChirpMaxJobs];
+  long long start[kChirpMaxJobs + 1];  // first track of each job in the launch's numbering
+  int n_jobs;
 };
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -107,13 +117,13 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 }
 __device__ __forceinline__ int at16(int k) { return 4 * (k & 3) + (k >> 2); }
 
-__device__ __forceinline__ double track_f(const ChirpArgs& a, const double* c, double fr, int seg) {
+__device__ __forceinline__ double track_f(const ChirpJob& a, const double* c, double fr, int seg) {
   double f = fr;
   for (int k = 0; k < a.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], a.U[(size_t)k * a.n_seg + seg]));
   return f;
 }
 
-__global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const ChirpArgs a) {
+__global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_constant__ ChirpBatch B) {
   __shared__ float s_win[kM];                 // sin^2(pi m / 512)
   __shared__ float2 s_buf[kCW][16][33];       // per-warp transpose (padded rows)
   __shared__ double s_c[kCW][32];             // the warp's track coefficients
@@ -131,12 +141,16 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const ChirpArgs a
     tw[j0] = make_float2(cs, sn);
   }
   __syncthreads();
-  const int n = a.n_seg;
-  const double T = a.T;
-  const double T6 = __ddiv_rn(T, 6.0);
   const int h = lane & 1, j0p = lane >> 1;
   const long long nw = (long long)gridDim.x * kCW;
-  for (long long t = (long long)blockIdx.x * kCW + w; t < a.N; t += nw) {
+  int jb = 0;  // the job of the current track (tracks are visited in increasing order)
+  for (long long gt = (long long)blockIdx.x * kCW + w; gt < B.start[B.n_jobs]; gt += nw) {
+    while (gt >= B.start[jb + 1]) ++jb;
+    const ChirpJob& a = B.jobs[jb];
+    const long long t = gt - B.start[jb];
+    const int n = a.n_seg;
+    const double T = a.T;
+    const double T6 = __ddiv_rn(T, 6.0);
     __syncwarp();
     if (lane < a.K) s_c[w][lane] = a.coeffs[t * a.K + lane];
     __syncwarp();
@@ -278,6 +292,50 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const ChirpArgs a
 
 using namespace tfs;
 
+// Launches the kernel over up to kChirpMaxJobs jobs (tracks numbered job after job).
+static int launch_chirp(const ChirpJob* jobs, int n_jobs, cudaStream_t st) {
+  ChirpBatch B;
+  B.n_jobs = n_jobs;
+  B.start[0] = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    B.jobs[i] = jobs[i];
+    B.start[i + 1] = B.start[i] + jobs[i].N;
+  }
+  for (int i = n_jobs; i < kChirpMaxJobs; ++i) B.start[i + 1] = B.start[n_jobs];
+  const long long total = B.start[n_jobs];
+  if (total == 0) return TFS_OK;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chirp_stat_kernel, kCThreads, 0);
+  const long long want = (total + kCW - 1) / kCW;
+  const int grid =
+      (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(1, n_sm) * std::max(1, per_sm)));
+  chirp_stat_kernel<<<grid, kCThreads, 0, st>>>(B);
+  count_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TFS_OK : cuda_fail(e, "chirp statistic");
+}
+
+static ChirpJob make_chirp_job(const tfs_ctable* ct, const tfs_basis* basis, const double* coeffs,
+                               const double* f_ref, int64_t N, int P, int flags, float* stat) {
+  ChirpJob a;
+  a.z = ct->z;
+  a.wt = ct->wt;
+  a.n_seg = (int)ct->n_seg;
+  a.n_bin = (int)ct->n_bin;
+  a.U = basis->U;
+  a.K = basis->K;
+  a.coeffs = coeffs;
+  a.f_ref = f_ref;
+  a.N = N;
+  a.T = ct->T_sft;
+  a.P = P;
+  a.cuts = (flags & TFS_JOB_SEGMENT_CUTS) ? 1 : 0;
+  a.stat = stat;
+  return a;
+}
+
 extern "C" int tfs_eval_chirp_stat(const tfs_ctable* ct, const tfs_basis* basis, const double* coeffs,
                                    const double* f_ref, int64_t N, int P, int flags, float* stat, int topk,
                                    int64_t* top_idx, float* top_val, void* stream) {
@@ -303,31 +361,50 @@ extern "C" int tfs_eval_chirp_stat(const tfs_ctable* ct, const tfs_basis* basis,
   if (need) TFS_CUDA(cudaMallocAsync((void**)&scratch, need, st));
   if (!stat) d_stat = reinterpret_cast<float*>(scratch);
   if (kk) ws = scratch + (stat ? 0 : (((size_t)N * 4 + 255) & ~(size_t)255));
-  ChirpArgs a;
-  a.z = ct->z;
-  a.wt = ct->wt;
-  a.n_seg = (int)ct->n_seg;
-  a.n_bin = (int)ct->n_bin;
-  a.U = basis->U;
-  a.K = basis->K;
-  a.coeffs = coeffs;
-  a.f_ref = f_ref;
-  a.N = N;
-  a.T = ct->T_sft;
-  a.P = P;
-  a.cuts = (flags & TFS_JOB_SEGMENT_CUTS) ? 1 : 0;
-  a.stat = d_stat;
-  int dev = 0, n_sm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chirp_stat_kernel, kCThreads, 0);
-  const long long want = (N + kCW - 1) / kCW;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(1, n_sm) * std::max(1, per_sm)));
-  chirp_stat_kernel<<<grid, kCThreads, 0, st>>>(a);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  int rc = e == cudaSuccess ? TFS_OK : cuda_fail(e, "chirp statistic");
+  const ChirpJob a = make_chirp_job(ct, basis, coeffs, f_ref, N, P, flags, d_stat);
+  int rc = launch_chirp(&a, 1, st);
   if (rc == TFS_OK && kk) rc = topk_device(d_stat, N, kk, top_idx, top_val, ws, st);
   if (scratch) cudaFreeAsync(scratch, st);
   return rc;
+}
+
+extern "C" int tfs_ctable_view(const tfs_ctable* t, int64_t seg0, int64_t n_seg, tfs_ctable** out) {
+  clear_error();
+  TFS_CHECK(t && out, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(seg0 >= 0 && n_seg >= 1 && seg0 + n_seg <= t->n_seg, TFS_ERR_INVALID_ARG,
+            "rows [%lld, %lld) outside the table's %lld", (long long)seg0, (long long)(seg0 + n_seg),
+            (long long)t->n_seg);
+  tfs_ctable* v = new tfs_ctable();
+  *v = *t;
+  v->n_seg = n_seg;
+  v->z = t->z + (size_t)seg0 * t->n_bin;
+  v->sft_plan = nullptr;
+  v->owns = false;
+  *out = v;
+  return TFS_OK;
+}
+
+extern "C" int tfs_eval_chirp_batch(const tfs_chirp_job* jobs, int n_jobs, void* stream) {
+  clear_error();
+  TFS_CHECK(jobs && n_jobs >= 1 && n_jobs <= 4096, TFS_ERR_INVALID_ARG, "need 1 <= n_jobs <= 4096 jobs");
+  std::vector<ChirpJob> cj;
+  for (int i = 0; i < n_jobs; ++i) {
+    const tfs_chirp_job& j = jobs[i];
+    TFS_CHECK(j.table && j.basis, TFS_ERR_INVALID_ARG, "job %d: null table or basis", i);
+    TFS_CHECK(j.basis->n_seg == j.table->n_seg, TFS_ERR_INVALID_ARG, "job %d: basis and table segment counts differ",
+              i);
+    TFS_CHECK(j.basis->K >= 1 && j.basis->K <= 32, TFS_ERR_INVALID_ARG, "job %d: basis size must be in [1, 32]", i);
+    TFS_CHECK(j.N >= 0 && j.N < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "job %d: N must be in [0, 2^31)", i);
+    TFS_CHECK(j.P >= 0 && j.P <= kChirpPMax, TFS_ERR_INVALID_ARG, "job %d: P must be in [0, %d]", i, kChirpPMax);
+    TFS_CHECK((j.flags & ~TFS_JOB_SEGMENT_CUTS) == 0, TFS_ERR_INVALID_ARG, "job %d: unknown flags", i);
+    TFS_CHECK(j.N == 0 || (j.coeffs && j.stat), TFS_ERR_INVALID_ARG, "job %d: null coeffs or stat", i);
+    if (j.N > 0) cj.push_back(make_chirp_job(j.table, j.basis, j.coeffs, j.f_ref, j.N, j.P, j.flags, j.stat));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (size_t g0 = 0; g0 < cj.size(); g0 += kChirpMaxJobs) {
+    const int n = (int)std::min<size_t>(kChirpMaxJobs, cj.size() - g0);
+    const int rc = launch_chirp(cj.data() + g0, n, st);
+    if (rc) return rc;
+  }
+  return TFS_OK;
 }

@@ -749,8 +749,10 @@ extern "C" int tfs_build_chirp_table(const double* strain, int64_t n, double dt,
 
 extern "C" int tfs_ctable_free(tfs_ctable* t) {
   if (!t) return TFS_OK;
-  if (t->z) cudaFree(t->z);
-  free_sft_plan(t->sft_plan);  // owns wt
+  if (t->owns) {
+    if (t->z) cudaFree(t->z);
+    free_sft_plan(t->sft_plan);  // owns wt
+  }
   delete t;
   return TFS_OK;
 }

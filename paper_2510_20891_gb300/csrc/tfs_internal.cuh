@@ -85,6 +85,7 @@ struct tfs_ctable {          // linear-chirp table: scaled complex spectra of a 
   float2* z = nullptr;      // device [n_seg][n_bin]: sqrt(4 dt / (sum w^2 S_ref)) X_k S_ref / S_k
   float* wt = nullptr;      // device [n_bin]: S_ref / S_k (owned by the plan)
   void* sft_plan = nullptr; // the SFT plan (window, twiddles, scales)
+  bool owns = true;         // false for a view: z and wt belong to another table
 };
 
 struct tfs_basis {

@@ -21,7 +21,8 @@ import math
 
 import numpy as np
 
-from . import Job, basis_view, check, eval_batch, lib, table_view
+from . import (CHIRP_P, ChirpJob, Job, basis_view, check, ctable_view, eval_batch, eval_chirp_batch, lib,
+               table_view, topk)
 
 JULIAN_YEAR_S = 365.25 * 86400.0
 
@@ -45,28 +46,50 @@ def noise_moments(n_segments: int, m: int, window: str = "hann"):
 
 
 class ChunkSearch:
-    """Chunks of one table (views) with their shifted bases."""
+    """Chunks of one table (views) with their shifted bases.  With a chirp table (the same
+    strain's linear-chirp table) the chunks can also be evaluated with the paper's
+    linear-chirp statistic (``statistic="chirp"``)."""
 
-    def __init__(self, table, basis, sizes=None):
+    def __init__(self, table, basis, sizes=None, chirp_table=None, P: int = CHIRP_P):
         self.table, self.basis = table, basis
-        self.sizes = list(sizes) if sizes is not None else chunk_sizes(table.n_seg, table.T_sft)
-        self.tables = [table_view(table, 0, n) for n in self.sizes]
+        ref = table if table is not None else chirp_table
+        self.sizes = list(sizes) if sizes is not None else chunk_sizes(ref.n_seg, ref.T_sft)
+        self.tables = [table_view(table, 0, n) for n in self.sizes] if table is not None else None
+        self.ctables = [ctable_view(chirp_table, 0, n) for n in self.sizes] if chirp_table is not None else None
         self.bases = [basis_view(basis, basis.n_seg - n, n) for n in self.sizes]
+        self.P = P
 
-    def jobs(self, coeffs, f_ref=None, m: int = 0, topk: int = 0, segment_cuts: bool = False, stats=None):
-        """One Job per chunk; coeffs (and f_ref, stats) are per-chunk CUDA tensors."""
+    def jobs(self, coeffs, f_ref=None, m: int = 0, topk: int = 0, segment_cuts: bool = False, stats=None,
+             statistic: str = "nearest"):
+        """One job per chunk; coeffs (and f_ref, stats) are per-chunk CUDA tensors."""
         out = []
         for i, c in enumerate(coeffs):
-            out.append(Job(self.tables[i], self.bases[i], c, f_ref[i] if f_ref is not None else None, m=m,
-                           topk=topk, stat=stats[i] if stats is not None else None, segment_cuts=segment_cuts))
+            fr = f_ref[i] if f_ref is not None else None
+            st = stats[i] if stats is not None else None
+            if statistic == "chirp":
+                out.append(ChirpJob(self.ctables[i], self.bases[i], c, fr, P=self.P, segment_cuts=segment_cuts,
+                                    stat=st))
+            else:
+                out.append(Job(self.tables[i], self.bases[i], c, fr, m=m, topk=topk, stat=st,
+                               segment_cuts=segment_cuts))
         return out
 
     def evaluate(self, coeffs, f_ref=None, m: int = 0, topk: int = 0, segment_cuts: bool = False, stats=None,
-                 dev_status=None, stream=None):
-        """All chunks' statistics in one eval_batch call; returns the Jobs (their .stat, .top_*)."""
-        jobs = self.jobs(coeffs, f_ref, m, topk, segment_cuts, stats)
-        eval_batch(jobs, dev_status=dev_status, stream=stream)
+                 dev_status=None, stream=None, statistic: str = "nearest"):
+        """All chunks' statistics in one batched call; returns the jobs (their .stat; .top_* for the
+        nearest-bin statistic).  The linear-chirp statistic ignores m, topk and dev_status."""
+        jobs = self.jobs(coeffs, f_ref, m, topk, segment_cuts, stats, statistic)
+        if statistic == "chirp":
+            eval_chirp_batch(jobs, stream=stream)
+        else:
+            eval_batch(jobs, dev_status=dev_status, stream=stream)
         return jobs
+
+    def launch(self, jobs, statistic: str, dev_status=None, stream=None):
+        if statistic == "chirp":
+            eval_chirp_batch(jobs, stream=stream)
+        else:
+            eval_batch(jobs, dev_status=dev_status, stream=stream)
 
     def moments(self, m: int, window: str = "hann"):
         return [noise_moments(n, m, window) for n in self.sizes]
@@ -85,7 +108,8 @@ class DESearch:
     """Differential-evolution population search over the chunks of a ChunkSearch."""
 
     def __init__(self, search: ChunkSearch, lo, hi, m: int = 0, n_init: int = 1024, n_walkers: int = 512,
-                 f_start=(5e-4, 1e-2), seed: int = 0, graph: bool = True, segment_cuts: bool = False):
+                 f_start=(5e-4, 1e-2), seed: int = 0, graph: bool = True, segment_cuts: bool = False,
+                 statistic: str = "nearest"):
         self.s, self.m = search, m
         self.lo, self.hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
         self.n_init, self.n_walkers = n_init, n_walkers
@@ -94,6 +118,7 @@ class DESearch:
         self.K = self.lo.size
         self.graph = graph
         self.cuts = segment_cuts  # the paper's exclusions (Sec. II.B, II.D)
+        self.statistic = statistic  # "nearest" (the configs' default) or "chirp" (the paper's S_alpha)
 
     def _initial(self, U_chunk):
         """n_init candidates uniform in the prior box, each track shifted by a constant so that
@@ -119,9 +144,14 @@ class DESearch:
         t0 = time.perf_counter()
         # initial population, best n_walkers per chunk
         init = [torch.tensor(self._initial(U_full[:, U_full.shape[1] - n:]), device=dev) for n in s.sizes]
-        jobs = s.evaluate(init, m=self.m, topk=W, segment_cuts=self.cuts, stream=stream)
-        c = torch.cat([init[i][jobs[i].top_idx] for i in range(n_ch)])          # [n_ch W, K]
-        st = torch.cat([jobs[i].top_val for i in range(n_ch)]).contiguous()
+        if self.statistic == "chirp":
+            jobs = s.evaluate(init, segment_cuts=self.cuts, stream=stream, statistic="chirp")
+            tops = [topk(j.stat, W, stream=stream) for j in jobs]
+        else:
+            jobs = s.evaluate(init, m=self.m, topk=W, segment_cuts=self.cuts, stream=stream)
+            tops = [(j.top_idx, j.top_val) for j in jobs]
+        c = torch.cat([init[i][tops[i][0]] for i in range(n_ch)])               # [n_ch W, K]
+        st = torch.cat([tops[i][1] for i in range(n_ch)]).contiguous()
         evals = n_ch * self.n_init
         lo = torch.tensor(self.lo, device=dev)
         hi = torch.tensor(self.hi, device=dev)
@@ -130,7 +160,7 @@ class DESearch:
         inp = torch.empty(n_ch * W, dtype=torch.int32, device=dev)
         views = [ct[i * W:(i + 1) * W] for i in range(n_ch)]
         stats = [s_trial[i * W:(i + 1) * W] for i in range(n_ch)]
-        trial_jobs = s.jobs(views, m=self.m, stats=stats, segment_cuts=self.cuts)
+        trial_jobs = s.jobs(views, m=self.m, stats=stats, segment_cuts=self.cuts, statistic=self.statistic)
         base = (np.arange(n_ch) * W).repeat(W)
         # the random draws of every iteration (r1 != r2 != t within the walker's own chunk,
         # F_DE ~ U[0.3, 1.5]), made up front and uploaded once
@@ -159,7 +189,7 @@ class DESearch:
             sp = strm.cuda_stream
             check(L.tfs_de_propose(c.data_ptr(), n, K, r1_b.data_ptr(), r2_b.data_ptr(), F_b.data_ptr(),
                                    lo.data_ptr(), hi.data_ptr(), ct.data_ptr(), inp.data_ptr(), sp))
-            eval_batch(trial_jobs, dev_status=status, stream=sp)
+            s.launch(trial_jobs, self.statistic, dev_status=status, stream=sp)
             check(L.tfs_de_accept(c.data_ptr(), st.data_ptr(), ct.data_ptr(), s_trial.data_ptr(), inp.data_ptr(),
                                   n, K, sp))
 
@@ -190,5 +220,9 @@ class DESearch:
         c_h = c.cpu().numpy().reshape(n_ch, W, K)
         best = st_h.argmax(axis=1)
         stat = st_h[np.arange(n_ch), best].astype(np.float64)
-        mom = np.array(s.moments(self.m))
-        return DEResult([c_h[i, best[i]] for i in range(n_ch)], stat, (stat - mom[:, 0]) / mom[:, 1], evals, secs)
+        if self.statistic == "chirp":
+            norm = np.full(n_ch, np.nan)  # no closed form for the linear-chirp statistic's noise moments
+        else:
+            mom = np.array(s.moments(self.m))
+            norm = (stat - mom[:, 0]) / mom[:, 1]
+        return DEResult([c_h[i, best[i]] for i in range(n_ch)], stat, norm, evals, secs)

@@ -78,6 +78,9 @@ def test_host_validation_without_device(L):
     assert L.tfs_eval_chirp_stat(None, None, None, None, 0, 100, 0, None, 0, None, None, None) == -1
     assert L.tfs_ctable_info(None, None, None, None, None, None) == -1
     assert L.tfs_ctable_free(None) == 0
+    assert L.tfs_eval_chirp_batch(None, 1, None) == -1
+    assert L.tfs_ctable_view(None, 0, 1, ctypes.byref(out)) == -1
+    assert ctypes.sizeof(_lib.TfsChirpJob) == 7 * 8 and _lib.TfsChirpJob.P.offset == 40
 
 
 def test_tuning_cache_round_trip(L, tmp_path):

@@ -180,3 +180,34 @@ def test_chirp_edges(T):
     empty = torch.zeros((0, V.shape[0]), dtype=torch.float64, device="cuda")
     stat, _, _ = T.eval_chirp_stat(ct, T.basis_from_host(V), empty)
     assert stat.numel() == 0
+
+
+def test_chirp_batch_equals_single_calls_and_views(T):
+    """Jobs of different tables, bases, P and cuts in one launch give exactly what each gives
+    alone (one warp per track: nothing depends on the neighbours); a view of a table's first
+    rows equals the table built from the strain's first segments."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    dt, L = 1.0, 1024
+    Tsft = L * dt
+    jobs, singles = [], []
+    tables = []
+    for n_seg, K, P, cuts in [(9, 3, 100, False), (12, 4, 50, True), (5, 2, 111, False), (9, 2, 0, True)]:
+        x, psd = _strain(rng, n_seg, L, dt, chirp=(200.2 / Tsft, 3.0 / Tsft ** 2, 0.2))
+        ct = T.build_chirp_table(x, dt, Tsft, psd)
+        tables.append((x, psd, ct))
+        V = _basis(n_seg, K)
+        b = T.basis_from_host(V)
+        c = torch.tensor(_tracks(rng, V, int(rng.integers(1, 600)), L // 2 + 1, Tsft, 40.0), device="cuda")
+        jobs.append(T.ChirpJob(ct, b, c, None, P=P, segment_cuts=cuts))
+        singles.append(T.eval_chirp_stat(ct, b, c, None, P=P, segment_cuts=cuts)[0])
+    T.eval_chirp_batch(jobs)
+    torch.cuda.synchronize()
+    for j, s1 in zip(jobs, singles):
+        assert np.array_equal(j.stat.cpu().numpy().view(np.uint32), s1.cpu().numpy().view(np.uint32))
+    x, psd, ct = tables[1]
+    v = T.ctable_view(ct, 0, 7)
+    pre = T.build_chirp_table(x[: 7 * L], dt, Tsft, psd)
+    zv, wv = v.to_host()
+    zp, wp = pre.to_host()
+    assert np.array_equal(zv, zp) and np.array_equal(wv, wp)

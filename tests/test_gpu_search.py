@@ -137,3 +137,34 @@ def test_de_driver_results_are_the_oracles(T):
     assert np.array_equal(rp.stat, r.stat)
     mom = np.array([O.noise_moments(n, 1) for n in sizes])
     assert np.allclose(r.normalised, (r.stat - mom[:, 0]) / mom[:, 1])
+
+
+def test_de_driver_with_the_linear_chirp_statistic(T):
+    """The same driver on the paper's own statistic (chirp table views, one chirp launch per
+    iteration, the paper's exclusions): its results are the oracle's masked linear-chirp
+    statistic of the returned coefficients."""
+    torch = pytest.importorskip("torch")
+    from paper_2510_20891_gb300 import search
+
+    rng = np.random.default_rng(9)
+    dt, L, n_seg, K = 4.0, 1024, 24, 3
+    Tsft = L * dt
+    t = (np.arange(n_seg) + 0.5) * Tsft
+    D = n_seg * Tsft
+    F = rng.uniform(40, 150, 400)[:, None] / Tsft * (1 - t[None, :] / (D * rng.uniform(1.001, 1.3, 400))[:, None]) ** -0.3
+    V = np.linalg.svd(F, full_matrices=False)[2][:K].copy()
+    c = F @ V.T
+    lo, hi = c.min(axis=0), c.max(axis=0)
+    x = rng.standard_normal(n_seg * L)
+    psd = np.full(L // 2 + 1, 2.0 * dt)
+    ct = T.build_chirp_table(x, dt, Tsft, psd)
+    sizes = [8, 12, 16, 20, 24]
+    cs = search.ChunkSearch(None, T.basis_from_host(V), sizes, chirp_table=ct)
+    r = search.DESearch(cs, lo, hi, n_init=128, n_walkers=32, f_start=(40 / Tsft, 150 / Tsft), seed=3,
+                        segment_cuts=True, statistic="chirp").run(n_iter=10, U_full=V)
+    assert r.evaluations == len(sizes) * (128 + 10 * 32)
+    d = O.sft(x, dt, Tsft)
+    for i, n in enumerate(sizes):
+        Fi = O.track_freqs(V[:, n_seg - n:], r.coeffs[i][None, :], np.zeros(1))
+        want = O.chirp_statistic(d[:n], psd, dt, Tsft, Fi, valid=O.segment_validity(Fi, Tsft))[0]
+        assert abs(r.stat[i] - want) <= 2e-5 * abs(want)
