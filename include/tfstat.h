@@ -396,6 +396,12 @@ typedef struct tfs_chirp_job {
 int tfs_eval_chirp_batch(const tfs_chirp_job* jobs, int n_jobs, void* stream);
 int tfs_ctable_view(const tfs_ctable* t, int64_t seg0, int64_t n_seg, tfs_ctable** out);
 
+/* Measurement support, not part of the paper's method: the current device's L2
+ * read bandwidth in GB/s (a buffer of buffer_bytes, 1 MB .. 1 GB, read `reps`
+ * times, 1..1000, after one warm-up pass, with 16-byte L1-bypassing loads).
+ * Allocates and frees its buffer; synchronous on the default stream. */
+int tfs_measure_l2_read(int64_t buffer_bytes, int reps, double* gbs);
+
 /* Number of kernels this library has launched in this process (all devices). */
 long long tfs_kernel_launches(void);
 

@@ -57,7 +57,14 @@ def _f64(x):
 
 
 def _ptr(a):
-    return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+    """The address of a C-contiguous array or tensor (the library reads row-major layouts)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays passed to the library must be C-contiguous (np.ascontiguousarray)")
+        return ctypes.c_void_p(a.ctypes.data)
+    if not a.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous (.contiguous())")
+    return ctypes.c_void_p(a.data_ptr())
 
 
 class Table:

@@ -53,6 +53,7 @@ SIGNATURES = {
     "tfs_build_chirp_table": (I, [P, I64, D, D, P, I, P, P]),
     "tfs_ctable_view": (I, [P, I64, I64, P]),
     "tfs_eval_chirp_batch": (I, [P, I, P]),
+    "tfs_measure_l2_read": (I, [I64, I, P]),
     "tfs_ctable_info": (I, [P, P, P, P, P, P]),
     "tfs_ctable_to_host": (I, [P, P, P]),
     "tfs_ctable_free": (I, [P]),

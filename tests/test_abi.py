@@ -129,3 +129,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.lib()
+
+
+def test_binding_refuses_non_contiguous_arrays():
+    """Every pointer the binding hands over must address a row-major array: a transposed view
+    (the natural result of a least-squares solve, for example) is refused, not misread."""
+    import numpy as np
+    import pytest
+
+    from paper_2510_20891_gb300 import _ptr
+
+    a = np.zeros((4, 3))
+    _ptr(a)
+    with pytest.raises(ValueError):
+        _ptr(a.T)

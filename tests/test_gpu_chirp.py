@@ -170,7 +170,11 @@ def test_chirp_edges(T):
     for n_seg in (1, 2):
         x, psd = _strain(rng, n_seg, L, dt)
         V = _basis(n_seg, 1) if n_seg == 1 else _basis(n_seg, 2)
-        c = rng.uniform(-0.5, 1.5, (200, V.shape[0])) * 257 / Tsft
+        # tracks across and beyond the band, drifting at most 60 bins per segment (the
+        # documented range of the template is |fdot| T^2 <= 100)
+        Ft = rng.uniform(-0.5, 1.5, (200, 1)) * 257 / Tsft + rng.uniform(-30, 30, (200, 1)) / Tsft * \
+            np.arange(n_seg)[None, :]
+        c = np.ascontiguousarray(np.linalg.lstsq(V.T, Ft.T, rcond=None)[0].T)
         ct = T.build_chirp_table(x, dt, Tsft, psd)
         got, *_ = _run(T, torch, ct, T.basis_from_host(V), c)
         F = O.track_freqs(V, c, np.zeros(200))
