@@ -111,7 +111,11 @@ struct JobDesc {
   int tile_tracks;      // tracks per tile (<= consumer threads * R); the last tile may hold fewer
   const float* emax;    // [KP] segment-cut launches: max |E_k|, max |G_k| (see SegParams)
   const float* gmax;
+  int seg_split;        // tiles per track range, each over seg_chunk consecutive segments
+  int seg_chunk;
+  float* part;          // [seg_split][N] partial sums when seg_split > 1 (summed in order afterwards)
 };
+
 
 constexpr double kFLowHz = 0x1.4b96be9c2da2cp-12;  // 10^-3.5 Hz, the nearest double
 constexpr double kFdotLow = 1e-13;                 // Hz/s
@@ -135,6 +139,18 @@ struct EvalArgs {
   int tile_start[MJ + 1];  // first tile of each job (prefix sums), tile_start[n_jobs] = n_tiles
   JobDesc jobs[MJ];
 };
+
+// The tracks [tile0, tile0 + tile_tracks) and segments [s0, s1) of a tile of job j.
+template <int MJ>
+__device__ __forceinline__ void tile_range(const EvalArgs<MJ>& a, const JobDesc& J, int tile, int j,
+                                           long long* tile0, int* sp, int* s0, int* s1) {
+  const int local = tile - a.tile_start[j];
+  const int tt = local / J.seg_split;
+  *sp = local - tt * J.seg_split;
+  *tile0 = (long long)tt * J.tile_tracks;
+  *s0 = *sp * J.seg_chunk;
+  *s1 = min(J.n_seg, *s0 + J.seg_chunk);
+}
 
 struct QHdr {
   int qbase;     // window centre held at q[ws_lo]
@@ -464,6 +480,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       const int j = job_of(a, tile);
       const JobDesc& J = a.jobs[j];
       const int n_seg = J.n_seg, m = J.m, W = 2 * m + 1;
+      long long tile0_unused;
+      int sp_unused, s0, s1;
+      tile_range(a, J, tile, j, &tile0_unused, &sp_unused, &s0, &s1);
+      const int ns = s1 - s0;  // this tile's segments
       // -------------------------------------------------------------- tile set-up (all 128)
       if (tid == 0) {
         if (thread_wait(&tile_ready[ltile & 1], (uint32_t)((ltile >> 1) & 1), flags)) {
@@ -499,28 +519,28 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       const float* sscales = J.seg_resident ? segs + n_seg * a.nsp : J.scales;
       const int bm = reinterpret_cast<const int*>(box)[2 * KP];
       const int bx = reinterpret_cast<const int*>(box)[2 * KP + 1];
-      if (n_seg <= kBandCap) {  // (band_of gives an in-range band for any box, even after an abort)
-        for (int sg = tid; sg < n_seg; sg += kProd) {
+      if (ns <= kBandCap) {  // (band_of gives an in-range band for any box, even after an abort)
+        for (int i = tid; i < ns; i += kProd) {
           int lo, len;
-          band_of<KP, EALIGN>(segrows + (size_t)sg * a.nsp, box, box + KP, bm, bx, m, J.n_bin, J.row_stride,
-                              a.pcap, &lo, &len);
-          band[2 * sg] = lo;
-          band[2 * sg + 1] = len;
+          band_of<KP, EALIGN>(segrows + (size_t)(s0 + i) * a.nsp, box, box + KP, bm, bx, m, J.n_bin,
+                              J.row_stride, a.pcap, &lo, &len);
+          band[2 * i] = lo;
+          band[2 * i + 1] = len;
         }
       }
       prod_bar();
       if (pw == 0) {
         // ------------------------------------------------------------ stager warp
-        for (int sg = 0; sg < n_seg; ++sg) {
+        for (int sg = s0; sg < s1; ++sg) {
           const int ps = (int)(p_seq % kNP);
           bool go = true;
           if (p_seq >= kNP) go = warp_wait(&empty_p[ps], ((p_seq / kNP) - 1u) & 1u, flags);
           else go = !__any_sync(0xffffffffu, flags[0] != 0);
           if (go && lane == 0) {
             int blo, blen;
-            if (n_seg <= kBandCap) {
-              blo = band[2 * sg];
-              blen = band[2 * sg + 1];
+            if (ns <= kBandCap) {
+              blo = band[2 * (sg - s0)];
+              blen = band[2 * (sg - s0) + 1];
             } else {
               band_of<KP, EALIGN>(segrows + (size_t)sg * a.nsp, box, box + KP, bm, bx, m, J.n_bin, J.row_stride,
                                   a.pcap, &blo, &blen);
@@ -557,8 +577,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         // ------------------------------------------------------------ builder warps
         // builder warp w builds the window sums of segments w, w + 3, w + 6, ...: the latency of
         // each warp's per-segment waits and set-up overlaps the other two warps' work
-        for (int sg = pw - 1; sg < n_seg; sg += kBuildWarps) {
-          const uint32_t gs = b_base + (uint32_t)sg;  // launch-wide segment sequence number
+        for (int sg = s0 + pw - 1; sg < s1; sg += kBuildWarps) {
+          const uint32_t gs = b_base + (uint32_t)(sg - s0);  // launch-wide segment sequence number
           const int ps = (int)(gs % kNP), qs = (int)(gs % kNQ);
           bool go = warp_wait(&full_p[ps], (gs / kNP) & 1u, flags);
           if (go && gs >= kNQ) go = warp_wait(&empty_q[qs], ((gs / kNQ) - 1u) & 1u, flags);
@@ -668,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
           }
         }
       }
-      b_base += (uint32_t)n_seg;
+      b_base += (uint32_t)ns;
     }
   } else {
     // ================================================================ consumer warpgroups
@@ -681,7 +701,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       const int j = job_of(a, tile);
       const JobDesc& J = a.jobs[j];
       const int n_seg = J.n_seg, m = J.m, K = J.K;
-      const long long tile0 = (long long)(tile - a.tile_start[j]) * J.tile_tracks;
+      long long tile0;
+      int sp, s0, s1;
+      tile_range(a, J, tile, j, &tile0, &sp, &s0, &s1);
       const long long tend = min(J.N, tile0 + J.tile_tracks);
       const bool live = !__any_sync(0xffffffffu, flags[0] != 0);  // warp-uniform
       // -------------------------------------------------------------- tile prologue
@@ -876,7 +898,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       const f32x2 kC2 = f2pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23 in both lanes
       // -------------------------------------------------------------- segments
       const unsigned nin = (unsigned)(J.n_bin + 2 * m);
-      for (int sg = 0; sg < n_seg; ++sg) {
+      for (int sg = s0; sg < s1; ++sg) {
         const int qs = (int)(q_seq % kNQ);
         ++q_seq;
         if (!live || !warp_wait(&full_q[qs], ((q_seq - 1u) / kNQ) & 1u, flags)) continue;
@@ -1045,7 +1067,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const long long t = tile0 + ctid + r * kCons;
-          if (t < tend) J.stat[t] = (tot[r * kCons + ctid] + acc[r]) + corr[r * kCons + ctid];
+          if (t < tend) {
+            const float v = (tot[r * kCons + ctid] + acc[r]) + corr[r * kCons + ctid];
+            if (J.seg_split > 1) J.part[(size_t)sp * J.N + t] = v;
+            else J.stat[t] = v;
+          }
         }
       }
     }
@@ -1087,6 +1113,32 @@ inline int sm_count() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+// Partial sums of tiles that cover a segment range, added in range order into the statistic.
+struct PartJob {
+  const float* part;  // [S][N]
+  float* stat;        // [N]
+  long long N;
+  int S;
+};
+struct PartArgs {
+  PartJob jobs[kMaxJobs];
+  long long start[kMaxJobs + 1];
+  int n;
+};
+static __global__ void sum_parts_kernel(const __grid_constant__ PartArgs p) {
+  const long long total = p.start[p.n];
+  int j = 0;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    while (g >= p.start[j + 1]) ++j;
+    const PartJob& J = p.jobs[j];
+    const long long t = g - p.start[j];
+    float v = 0.f;
+    for (int q = 0; q < J.S; ++q) v += J.part[(size_t)q * J.N + t];
+    J.stat[t] = v;
+  }
 }
 
 inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 4 : 2)); }
@@ -1157,6 +1209,9 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     }
     const long long tt = ntj > 0 ? (E.N + ntj - 1) / ntj : tile;
     D.tile_tracks = (int)tt;
+    D.seg_split = 1;
+    D.seg_chunk = (int)tb->n_seg;
+    D.part = nullptr;
     a.tile_start[i] = (int)nt;
     nt += tt > 0 ? (E.N + tt - 1) / tt : 0;
     row_max = std::max(row_max, (int)tb->row_stride);
@@ -1164,6 +1219,27 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     bins = bins || E.bins_out != nullptr;
   }
   if (nt == 0) return TFS_OK;
+  // Few track tiles (small jobs): split each job's segments over several tiles so that every
+  // SM gets work, at least 16 segments per tile; the tiles' partial sums are added in segment
+  // order by a second small kernel.
+  size_t part_floats = 0;
+  const long long sms_all = sm_count();
+  if (!bins && nt < sms_all) {
+    const int S = (int)std::min<long long>(8, sms_all / nt);
+    if (S > 1) {
+      nt = 0;
+      for (int i = 0; i < L.n_jobs; ++i) {
+        JobDesc& D = a.jobs[i];
+        const long long ntj = D.N > 0 ? (D.N + D.tile_tracks - 1) / D.tile_tracks : 0;
+        const int Sj = std::max(1, std::min(S, D.n_seg / 16));
+        D.seg_chunk = (D.n_seg + Sj - 1) / Sj;
+        D.seg_split = (D.n_seg + D.seg_chunk - 1) / D.seg_chunk;
+        if (D.seg_split > 1) part_floats += (size_t)D.seg_split * D.N;
+        a.tile_start[i] = (int)nt;
+        nt += ntj * D.seg_split;
+      }
+    }
+  }
   if (nt > 0x7fffffffLL) {
     set_error("too many tracks for one launch");
     return TFS_ERR_INVALID_ARG;
@@ -1211,7 +1287,19 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     return TFS_ERR_INVALID_ARG;
   }
   const int grid = (int)std::min<long long>(nt, (long long)sm_count());
-
+  float* parts = nullptr;
+  if (part_floats) {
+    TFS_CUDA(cudaMallocAsync((void**)&parts, part_floats * sizeof(float), st));
+    size_t o = 0;
+    for (int i = 0; i < L.n_jobs; ++i) {
+      JobDesc& D = a.jobs[i];
+      if (D.seg_split > 1) {
+        D.part = parts + o;
+        o += (size_t)D.seg_split * D.N;
+      }
+    }
+  }
+  auto dispatch = [&]() -> int {
 #define TFS_LAUNCH_KP(KPV, RV, RCV)                                                     \
   if (KP == KPV) {                                                                      \
     if (cuts) return launch_one<DT, KPV, RCV, false, true, MJ>(a, grid, smem, st);       \
@@ -1220,16 +1308,38 @@ int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t s
     }                                                                                   \
     return launch_one<DT, KPV, RV, false, false, MJ>(a, grid, smem, st);                 \
   }
-  TFS_LAUNCH_KP(2, 12, 8)
-  TFS_LAUNCH_KP(4, 12, 8)
-  TFS_LAUNCH_KP(6, 12, 8)
-  TFS_LAUNCH_KP(8, 9, 6)
-  TFS_LAUNCH_KP(16, 4, 2)
-  TFS_LAUNCH_KP(32, 2, 2)
+    TFS_LAUNCH_KP(2, 12, 8)
+    TFS_LAUNCH_KP(4, 12, 8)
+    TFS_LAUNCH_KP(6, 12, 8)
+    TFS_LAUNCH_KP(8, 9, 6)
+    TFS_LAUNCH_KP(16, 4, 2)
+    TFS_LAUNCH_KP(32, 2, 2)
 #undef TFS_LAUNCH_KP
+    set_error("unsupported coefficient slot count %d", KP);
+    return TFS_ERR_INVALID_ARG;
+  };
   (void)R;
-  set_error("unsupported coefficient slot count %d", KP);
-  return TFS_ERR_INVALID_ARG;
+  int rc = dispatch();
+  if (rc == TFS_OK && parts) {
+    PartArgs pa;
+    pa.n = 0;
+    pa.start[0] = 0;
+    for (int i = 0; i < L.n_jobs; ++i) {
+      const JobDesc& D = a.jobs[i];
+      if (D.seg_split <= 1) continue;
+      pa.jobs[pa.n] = PartJob{D.part, D.stat, D.N, D.seg_split};
+      pa.start[pa.n + 1] = pa.start[pa.n] + D.N;
+      ++pa.n;
+    }
+    const long long total = pa.start[pa.n];
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, sm_count() * 8));
+    sum_parts_kernel<<<blocks, 256, 0, st>>>(pa);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "partial sums");
+  }
+  if (parts) cudaFreeAsync(parts, st);
+  return rc;
 }
 
 template <int DT>
