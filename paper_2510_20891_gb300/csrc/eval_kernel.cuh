@@ -955,13 +955,43 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         auto pairs = [&](auto complete_c, auto zt_c) {
           constexpr bool COMPLETE = decltype(complete_c)::value;
           constexpr bool ZT = CUTS && decltype(zt_c)::value;
+          // y of every pair, coefficient by coefficient (R2 independent FMA chains in flight)
+          f32x2 yv[R2];
+#pragma unroll
+          for (int p = 0; p < R2; ++p) yv[p] = y02[p];
+#pragma unroll
+          for (int k = 0; k < KP; ++k)
+#pragma unroll
+            for (int p = 0; p < R2; ++p) yv[p] = f2fma(c2[p][k], d2[k], yv[p]);
+          if constexpr (COMPLETE && !CUTS && !BINS) {
+            // the hot path in three passes: every slot offset and decision, every gather, every sum
+            unsigned offs[2 * R2];
+            unsigned undm = 0u;
+#pragma unroll
+            for (int p = 0; p < R2; ++p) {
+              const f32x2 tt2 = f2add(yv[p], kC2);
+              const f32x2 dd2 = f2sub(yv[p], f2sub(tt2, kC2));
+              float tts[2], dds[2];
+              f2split(tt2, tts[0], tts[1]);
+              f2split(dd2, dds[0], dds[1]);
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                offs[2 * p + hh] = min((unsigned)__float_as_int(tts[hh]) + koff, qn);
+                undm |= (unsigned)!(fabsf(dds[hh]) < wlim) << (2 * p + hh);
+              }
+            }
+            float vals[2 * R2];
+#pragma unroll
+            for (int r = 0; r < R; ++r) vals[r] = q[offs[r]];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += ((undm >> r) & 1u) ? 0.f : vals[r];
+            pend |= undm & ((R >= 32) ? 0xffffffffu : ((1u << R) - 1u));
+            return;
+          }
 #pragma unroll
           for (int p = 0; p < R2; ++p) {
-            // y for the pair (2p, 2p + 1); tt = y + 1.5 * 2^23 rounds y to an integer
-            // (|y| < 2^22); dd = y - rint(y), exact
-            f32x2 y2 = y02[p];
-#pragma unroll
-            for (int k = 0; k < KP; ++k) y2 = f2fma(c2[p][k], d2[k], y2);
+            // tt = y + 1.5 * 2^23 rounds y to an integer (|y| < 2^22); dd = y - rint(y), exact
+            const f32x2 y2 = yv[p];
             const f32x2 tt2 = f2add(y2, kC2);
             const f32x2 dd2 = f2sub(y2, f2sub(tt2, kC2));
             float tts[2], dds[2], ys[2], zs[2], ws[2];
