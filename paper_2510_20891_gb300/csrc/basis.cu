@@ -179,6 +179,7 @@ using namespace tfs;
 extern "C" int tfs_build_basis(const double* tracks, int64_t M, int64_t n_seg, int K, double tol, int mem,
                                void* stream, tfs_basis** out) {
   clear_error();
+  NvtxRange nvtx("tfs_build_basis");
   TFS_CHECK(tracks && out, TFS_ERR_INVALID_ARG, "null argument");
   TFS_CHECK(M >= 1 && n_seg >= 1 && M <= (1 << 24) && n_seg <= (1 << 20), TFS_ERR_INVALID_ARG, "bad shape");
   TFS_CHECK(K >= 0 && K <= 32 && K <= std::min<int64_t>(M, n_seg), TFS_ERR_INVALID_ARG,

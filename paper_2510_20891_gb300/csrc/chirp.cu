@@ -340,6 +340,7 @@ extern "C" int tfs_eval_chirp_stat(const tfs_ctable* ct, const tfs_basis* basis,
                                    const double* f_ref, int64_t N, int P, int flags, float* stat, int topk,
                                    int64_t* top_idx, float* top_val, void* stream) {
   clear_error();
+  NvtxRange nvtx("tfs_eval_chirp_stat");
   TFS_CHECK(ct && basis, TFS_ERR_INVALID_ARG, "null table or basis");
   TFS_CHECK(basis->n_seg == ct->n_seg, TFS_ERR_INVALID_ARG, "basis has %lld segments, table %lld",
             (long long)basis->n_seg, (long long)ct->n_seg);
@@ -386,6 +387,7 @@ extern "C" int tfs_ctable_view(const tfs_ctable* t, int64_t seg0, int64_t n_seg,
 
 extern "C" int tfs_eval_chirp_batch(const tfs_chirp_job* jobs, int n_jobs, void* stream) {
   clear_error();
+  NvtxRange nvtx("tfs_eval_chirp_batch");
   TFS_CHECK(jobs && n_jobs >= 1 && n_jobs <= 4096, TFS_ERR_INVALID_ARG, "need 1 <= n_jobs <= 4096 jobs");
   std::vector<ChirpJob> cj;
   for (int i = 0; i < n_jobs; ++i) {

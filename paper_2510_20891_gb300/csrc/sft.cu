@@ -627,6 +627,7 @@ static int run_sft(const SftPlan* p, const double* d_x, tfs_table* t, cudaStream
 extern "C" int tfs_build_sfts(const double* strain, int64_t n, double dt, double T_sft, int window,
                               const double* psd, int dtype, int mem, void* stream, tfs_table** out) {
   clear_error();
+  NvtxRange nvtx("tfs_build_sfts");
   TFS_CHECK(strain && psd && out, TFS_ERR_INVALID_ARG, "null argument");
   TFS_CHECK(dt > 0 && T_sft > 0 && std::isfinite(dt) && std::isfinite(T_sft), TFS_ERR_INVALID_ARG,
             "dt and T_sft must be positive");
@@ -668,6 +669,7 @@ extern "C" int tfs_build_sfts(const double* strain, int64_t n, double dt, double
 
 extern "C" int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, int mem, void* stream) {
   clear_error();
+  NvtxRange nvtx("tfs_table_rebuild");
   TFS_CHECK(t && strain, TFS_ERR_INVALID_ARG, "null argument");
   TFS_CHECK(t->sft_plan, TFS_ERR_INVALID_ARG, "table was not made by tfs_build_sfts");
   TFS_CHECK(mem == TFS_MEM_HOST || mem == TFS_MEM_DEVICE, TFS_ERR_INVALID_ARG, "bad mem kind");
@@ -694,6 +696,7 @@ extern "C" int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, 
 extern "C" int tfs_build_chirp_table(const double* strain, int64_t n, double dt, double T_sft, const double* psd,
                                      int mem, void* stream, tfs_ctable** out) {
   clear_error();
+  NvtxRange nvtx("tfs_build_chirp_table");
   TFS_CHECK(strain && psd && out, TFS_ERR_INVALID_ARG, "null argument");
   TFS_CHECK(dt > 0 && T_sft > 0 && std::isfinite(dt) && std::isfinite(T_sft), TFS_ERR_INVALID_ARG,
             "dt and T_sft must be positive");

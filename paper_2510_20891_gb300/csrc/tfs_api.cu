@@ -453,6 +453,7 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
                   int64_t N, int m, int topk, float* stat, int64_t* top_idx, float* top_val, tfs_tie_report* ties,
                   int mem, void* stream) {
   clear_error();
+  NvtxRange nvtx("tfs_eval_stat");
   TFS_CHECK(table && basis_c, TFS_ERR_INVALID_ARG, "null table or basis");
   tfs_basis* basis = const_cast<tfs_basis*>(basis_c);
   TFS_CHECK(mem == TFS_MEM_HOST || mem == TFS_MEM_DEVICE, TFS_ERR_INVALID_ARG, "bad mem kind");
@@ -617,6 +618,7 @@ int tfs_eval_bins(const tfs_table* table, const tfs_basis* basis_c, const double
 
 int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* stream) {
   clear_error();
+  NvtxRange nvtx("tfs_eval_batch");
   TFS_CHECK(jobs && n_jobs >= 1 && n_jobs <= 4096, TFS_ERR_INVALID_ARG, "need 1 <= n_jobs <= 4096 jobs");
   for (int i = 0; i < n_jobs; ++i) {
     const tfs_job& j = jobs[i];

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -37,6 +38,14 @@ int cuda_fail(cudaError_t e, const char* what);  // records the message, returns
 
 // Device status word values written by kernels (0 = ok).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD = 2 };
+
+// An NVTX range over an entry point (seen by profilers that record NVTX; free otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n = 1);
