@@ -301,6 +301,20 @@ int tfs_server_get_stats(tfs_server* s, tfs_server_stats* out);
  * and buffers.  Tickets not yet waited for are dropped. */
 int tfs_server_free(tfs_server* s);
 
+/* ---- saving and restoring a table (not part of the paper's method) ---------
+ * tfs_table_export copies the stored table exactly as it is held, row-major
+ * [n_seg][row_stride] elements of the storage dtype (row_stride from
+ * tfs_table_info; elements beyond n_bin are 0), into host `data`
+ * (n_seg * row_stride * element size bytes), and the FP8 scales [n_seg] into
+ * host `scales` (may be NULL for other dtypes).  tfs_table_import builds a
+ * table from those bytes: the round trip is exact (the same stored values, so
+ * the same statistic bit for bit), and a search can resume from saved tables.
+ * Synchronous.  The importer's row_stride is that of tfs_table_from_power for
+ * the same n_bin (a multiple of 32 elements). */
+int tfs_table_export(const tfs_table* t, void* data, float* scales);
+int tfs_table_import(const void* data, const float* scales, int64_t n_seg, int64_t n_bin, double T_sft, int dtype,
+                     tfs_table** out);
+
 /* ---- data chunks and shifted bases (the T_pl search of Sec. II.D) ----------
  * The paper searches data of growing duration T_obs (0.1 yr, then 12 SFTs more
  * per chunk, 48 chunks) for a plunge at the end of each chunk, aligning one

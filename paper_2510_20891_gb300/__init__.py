@@ -95,6 +95,16 @@ class Table:
         check(lib().tfs_table_to_host(self._h, _ptr(P), _ptr(sc) if sc is not None else None))
         return P, sc
 
+    def save(self, path: str):
+        """Write the stored table exactly as held (.npz: raw elements, FP8 scales, shape, T_sft)."""
+        es = {"f32": 4, "bf16": 2, "f16": 2, "f8e4m3": 1}[self.dtype]
+        raw = np.empty(self.n_seg * self.row_stride * es, dtype=np.uint8)
+        sc = np.empty(self.n_seg, dtype=np.float32)
+        check(lib().tfs_table_export(self._h, _ptr(raw), _ptr(sc) if self.dtype == "f8e4m3" else None))
+        np.savez(path, raw=raw, scales=sc if self.dtype == "f8e4m3" else np.zeros(0, np.float32),
+                 meta=np.array([self.n_seg, self.n_bin, self.row_stride, DTYPES[self.dtype]], dtype=np.int64),
+                 T_sft=np.array([self.T_sft]))
+
     def free(self):
         if self._h:
             lib().tfs_table_free(self._h)
@@ -178,6 +188,21 @@ def basis_from_host(U) -> Basis:
     h = ctypes.c_void_p()
     check(lib().tfs_basis_from_host(_ptr(U), U.shape[0], U.shape[1], ctypes.byref(h)))
     return Basis(h)
+
+
+def table_load(path: str) -> Table:
+    """A table written by Table.save, bit for bit (tfs_table_import)."""
+    z = np.load(path)
+    n_seg, n_bin, row_stride, dt = (int(v) for v in z["meta"])
+    raw = np.ascontiguousarray(z["raw"])
+    sc = np.ascontiguousarray(z["scales"]) if z["scales"].size else None
+    h = ctypes.c_void_p()
+    check(lib().tfs_table_import(_ptr(raw), _ptr(sc) if sc is not None else None, n_seg, n_bin,
+                                 float(z["T_sft"][0]), dt, ctypes.byref(h)))
+    t = Table(h)
+    if t.row_stride != row_stride:
+        raise ValueError("saved row stride does not match this library's layout")
+    return t
 
 
 def table_view(table: Table, seg0: int, n_seg: int) -> Table:

@@ -47,6 +47,8 @@ SIGNATURES = {
     "tfs_server_get_stats": (I, [P, P]),
     "tfs_server_free": (I, [P]),
     "tfs_table_view": (I, [P, I64, I64, P]),
+    "tfs_table_export": (I, [P, P, P]),
+    "tfs_table_import": (I, [P, P, I64, I64, D, I, P]),
     "tfs_basis_view": (I, [P, I64, I64, P]),
     "tfs_de_propose": (I, [P, I64, I, P, P, P, P, P, P, P, P]),
     "tfs_de_accept": (I, [P, P, P, P, P, I64, I, P]),

@@ -402,6 +402,39 @@ extern "C" int tfs_table_to_host(const tfs_table* t, double* P, float* scales) {
   return TFS_OK;
 }
 
+extern "C" int tfs_table_export(const tfs_table* t, void* data, float* scales) {
+  clear_error();
+  TFS_CHECK(t && data, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(t->data, TFS_ERR_INVALID_ARG, "table has no device data");
+  const size_t bytes = (size_t)t->n_seg * t->row_stride * esize_of(t->dtype);
+  TFS_CUDA(cudaMemcpy(data, t->data, bytes, cudaMemcpyDeviceToHost));
+  if (scales && t->scales) TFS_CUDA(cudaMemcpy(scales, t->scales, (size_t)t->n_seg * 4, cudaMemcpyDeviceToHost));
+  return TFS_OK;
+}
+
+extern "C" int tfs_table_import(const void* data, const float* scales, int64_t n_seg, int64_t n_bin, double T_sft,
+                                int dtype, tfs_table** out) {
+  clear_error();
+  TFS_CHECK(data && out, TFS_ERR_INVALID_ARG, "null argument");
+  TFS_CHECK(n_seg >= 1 && n_seg <= (1 << 24) && n_bin >= 1 && n_bin <= (1 << 24), TFS_ERR_INVALID_ARG,
+            "bad table shape");
+  TFS_CHECK(dtype >= TFS_F32 && dtype <= TFS_F8E4M3, TFS_ERR_INVALID_ARG, "bad dtype");
+  TFS_CHECK(dtype != TFS_F8E4M3 || scales, TFS_ERR_INVALID_ARG, "an FP8 table needs its scales");
+  TFS_CHECK(T_sft > 0 && std::isfinite(T_sft), TFS_ERR_INVALID_ARG, "bad T_sft");
+  tfs_table* t = nullptr;
+  int rc = alloc_table(n_seg, n_bin, dtype, T_sft, &t);
+  if (rc) return rc;
+  const size_t bytes = (size_t)n_seg * t->row_stride * esize_of(dtype);
+  cudaError_t e = cudaMemcpy(t->data, data, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && t->scales) e = cudaMemcpy(t->scales, scales, (size_t)n_seg * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    tfs_table_free(t);
+    return cuda_fail(e, "table import");
+  }
+  *out = t;
+  return TFS_OK;
+}
+
 extern "C" int tfs_table_from_power(const double* P, int64_t n_seg, int64_t n_bin, double T_sft, int dtype, int mem,
                                     void* stream, tfs_table** out) {
   clear_error();

@@ -79,6 +79,9 @@ def test_host_validation_without_device(L):
     assert L.tfs_ctable_info(None, None, None, None, None, None) == -1
     assert L.tfs_ctable_free(None) == 0
     assert L.tfs_eval_chirp_batch(None, 1, None) == -1
+    assert L.tfs_table_export(None, None, None) == -1
+    assert L.tfs_table_import(ctypes.cast(x, P), None, 4, 10, 1.0, 3, ctypes.byref(out)) == -1  # FP8 without scales
+    assert L.tfs_table_import(ctypes.cast(x, P), None, 0, 10, 1.0, 0, ctypes.byref(out)) == -1
     assert L.tfs_ctable_view(None, 0, 1, ctypes.byref(out)) == -1
     assert ctypes.sizeof(_lib.TfsChirpJob) == 7 * 8 and _lib.TfsChirpJob.P.offset == 40
 

@@ -203,3 +203,22 @@ def test_autotuned_launch_shape(T):
         assert O.stat_relative_error(j.stat.cpu().numpy().astype(np.float64), S) <= 1e-5
     T.lib().tfs_tuning_clear()
 
+
+
+def test_table_save_and_load_round_trip(T, tmp_path):
+    """A saved table comes back bit for bit (every dtype), so its statistic is identical."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(41)
+    for dtype in ("f32", "bf16", "f16", "f8e4m3"):
+        table, basis, U = _dataset(T, rng, 37, 900, 2.0e4, dtype, 4)
+        path = str(tmp_path / f"t_{dtype}.npz")
+        table.save(path)
+        back = T.table_load(path)
+        assert (back.n_seg, back.n_bin, back.dtype, back.T_sft) == (table.n_seg, table.n_bin, table.dtype, table.T_sft)
+        P0, s0 = table.to_host()
+        P1, s1 = back.to_host()
+        assert np.array_equal(P0, P1) and (s0 is None or np.array_equal(s0, s1))
+        c, f = _tracks(rng, 2000, 4, 37, 900, 2.0e4)
+        a = T.eval_stat(table, basis, c, f, m=1).stat
+        b = T.eval_stat(back, basis, c, f, m=1).stat
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
