@@ -480,6 +480,12 @@ class Server:
     def submit(self, ds: int, coeffs, f_ref=None, m: int = 0, topk: int = 0) -> int:
         c = _f64(coeffs)
         fr = _f64(f_ref) if f_ref is not None else None
+        if 0 <= ds < len(self._bases):
+            K = self._bases[ds].K
+            if c.ndim != 2 or c.shape[1] != K:
+                raise ValueError(f"coefficients must be [N, {K}] for dataset {ds}, got {c.shape}")
+            if fr is not None and fr.shape != (c.shape[0],):
+                raise ValueError("f_ref must have one entry per track")
         N = c.shape[0]
         t = ctypes.c_int64()
         check(lib().tfs_server_submit(self._h, int(ds), _ptr(c), _ptr(fr) if fr is not None else None, N, int(m),
