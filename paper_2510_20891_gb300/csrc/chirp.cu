@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_cons
   int jb = 0;  // the job of the current track (tracks are visited in increasing order)
   for (long long gt = (long long)blockIdx.x * kCW + w; gt < B.start[B.n_jobs]; gt += nw) {
     while (gt >= B.start[jb + 1]) ++jb;
-    const ChirpJob& a = B.jobs[jb];
+    const ChirpJob a = B.jobs[jb];  // by value: the inner loops read registers, not indexed parameters
     const long long t = gt - B.start[jb];
     const int n = a.n_seg;
     const double T = a.T;
