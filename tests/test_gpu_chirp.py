@@ -215,3 +215,28 @@ def test_chirp_batch_equals_single_calls_and_views(T):
     zv, wv = v.to_host()
     zp, wp = pre.to_host()
     assert np.array_equal(zv, zp) and np.array_equal(wv, wp)
+
+
+def test_chirp_full_size_sampled(T):
+    """The benchmark's one-year configuration (`bench.py --workload chirp`: 2 x 10^5 tracks,
+    P = 100, table from the strain on the device); 12 sampled tracks against the oracle."""
+    torch = pytest.importorskip("torch")
+    from paper_2510_20891_gb300 import synth
+
+    w = synth.WORKLOADS["oneyear_daily_fp32"]
+    rng = np.random.default_rng(0)
+    x, _ = synth.make_strain(w, rng)
+    psd = synth.psd_bins(w.psd_fn(), w.n_bin, w.T_sft)
+    V, s, lo, hi = O.svd_basis(synth.make_training_tracks(w, rng), w.K)
+    N = 200_000
+    coeffs = synth.uniform_coeffs(N, lo, hi, np.random.default_rng(5))
+    ct = T.build_chirp_table(torch.from_numpy(x).cuda(), w.dt, w.T_sft, psd)
+    stat, ti, tv = T.eval_chirp_stat(ct, T.basis_from_host(V), torch.from_numpy(coeffs).cuda(), topk=16)
+    torch.cuda.synchronize()
+    got = stat.cpu().numpy().astype(np.float64)
+    sample = np.concatenate([np.random.default_rng(6).choice(N, 8, replace=False), ti.cpu().numpy()[:4]])
+    F = O.track_freqs(V, coeffs[sample], np.zeros(sample.size))
+    want = O.chirp_statistic(O.sft(x, w.dt, w.T_sft), psd, w.dt, w.T_sft, F)
+    assert O.stat_relative_error(got[sample], want) <= TOL
+    gi, _ = O.topk(got, 16)
+    assert np.array_equal(ti.cpu().numpy(), gi)

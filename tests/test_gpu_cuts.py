@@ -175,3 +175,33 @@ def test_segment_cuts_short_and_wide(T):
     T.eval_batch([job])
     torch.cuda.synchronize()
     assert (job.stat.cpu().numpy() == 0).all()
+
+
+def test_segment_cuts_full_size_sampled(T):
+    """Ten million one-year tracks with the exclusions, in the benchmark's launch configuration
+    (`bench.py --segment-cuts`); 4000 sampled tracks and the top 32 against the masked oracle."""
+    torch = pytest.importorskip("torch")
+    from paper_2510_20891_gb300 import synth
+
+    w = synth.WORKLOADS["oneyear_daily_fp32"]
+    rng = np.random.default_rng(0)
+    x, _ = synth.make_strain(w, rng)
+    psd = synth.psd_bins(w.psd_fn(), w.n_bin, w.T_sft)
+    P64 = O.power_table(x, w.dt, w.T_sft, psd)
+    V, s, lo, hi = O.svd_basis(synth.make_training_tracks(w, rng), w.K)
+    N = w.n_tracks
+    coeffs = synth.uniform_coeffs(N, lo, hi, np.random.default_rng(8))
+    table = T.table_from_power(P64, w.T_sft, "f32")
+    job = T.Job(table, T.basis_from_host(V), torch.from_numpy(coeffs).cuda(), None, m=1, topk=32,
+                segment_cuts=True)
+    T.eval_batch([job])
+    torch.cuda.synchronize()
+    stat = job.stat.cpu().numpy().astype(np.float64)
+    sample = np.random.default_rng(9).choice(N, 4000, replace=False)
+    S, valid = O.eval_stat_masked(P64, V, coeffs[sample], np.zeros(sample.size), w.T_sft, 1)
+    assert O.stat_relative_error(stat[sample], S) <= 1e-5
+    assert 0 < 1 - valid.mean() < 0.5
+    gi, _ = O.topk(stat, 32)
+    assert np.array_equal(job.top_idx.cpu().numpy(), gi)
+    St, _ = O.eval_stat_masked(P64, V, coeffs[gi], np.zeros(gi.size), w.T_sft, 1)
+    assert O.stat_relative_error(job.top_val.cpu().numpy().astype(np.float64), St) <= 1e-5
