@@ -167,7 +167,14 @@ int tfs_basis_free(tfs_basis* b);
  * lowest).  ties may be NULL; if given, the call waits for completion to
  * fill it (even with mem = DEVICE).  The basis must have n_seg equal to the
  * table's.  N may be 0.  stat may be NULL only if topk > 0 (then the
- * per-track values are kept in library scratch). */
+ * per-track values are kept in library scratch).  mem = HOST without a tie
+ * report: the inputs go up in chunks (whole rounds of full tiles over the SMs,
+ * at least 64 MB of coefficients each, at most 8 chunks) on a library stream,
+ * each chunk evaluated on `stream` by its own launch as soon as it has arrived
+ * and its values read back while the next one runs; the bins are unchanged and
+ * the statistic agrees with the one-launch result within FP32 rounding (which
+ * pairs the FP32 filter leaves to the FP64 fix-up depends on the tiling).  Host
+ * buffers should be pinned for the copies to overlap. */
 int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis, const double* coeffs, const double* f_ref,
                   int64_t N, int m, int topk, float* stat, int64_t* top_idx, float* top_val, tfs_tie_report* ties,
                   int mem, void* stream);

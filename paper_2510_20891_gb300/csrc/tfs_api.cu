@@ -5,10 +5,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 
 #include <map>
 #include <string>
+#include <vector>
 
 #include "tfs_internal.cuh"
 
@@ -305,6 +307,60 @@ struct Arena {
 
 static size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+long long eval_round_tracks(int KP, bool cuts, int tile_div);  // beside the F32 instantiation
+
+// Host inputs of tfs_eval_stat are uploaded in chunks on a side stream, each chunk
+// evaluated by its own launch as soon as it has arrived, so that the upload of chunk c+1
+// overlaps the statistic of chunk c.  A chunk is a whole number of rounds of full tiles
+// over the SMs (so that the chunks' launches together take no more rounds than one launch
+// over all the tracks), at least 64 MB of coefficients, at most 8 chunks.  Returns the
+// tracks per chunk (N: no chunking).
+static int64_t host_chunk_tracks(const EvalLaunch& L, int64_t N, int K) {
+  int div = 1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(launch_key(L));
+    if (it != g_tune.end() && it->second.tile_div > 0) div = it->second.tile_div;
+  }
+  const int64_t round = eval_round_tracks(L.jobs[0].sp->KP, L.jobs[0].cuts != 0, div);
+  const int64_t min_tracks = ((int64_t)64 << 20) / (8 * (int64_t)K);
+  const int64_t r = std::max<int64_t>({1, (min_tracks + round - 1) / round, (N + 8 * round - 1) / (8 * round)});
+  return r * round >= N ? N : r * round;
+}
+
+// Side streams of one call, drained before the call's scratch is freed (declare after the
+// Arena so that this is destroyed first) and on every early return.
+struct SideStreams {
+  cudaStream_t s[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> ev;
+  int init() {
+    for (auto& x : s) TFS_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    return TFS_OK;
+  }
+  int event(cudaEvent_t* e) {
+    TFS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    ev.push_back(*e);
+    return TFS_OK;
+  }
+  // `to` waits for the work enqueued so far on `from`
+  int order(cudaStream_t from, cudaStream_t to) {
+    cudaEvent_t e;
+    int rc = event(&e);
+    if (rc) return rc;
+    TFS_CUDA(cudaEventRecord(e, from));
+    TFS_CUDA(cudaStreamWaitEvent(to, e, 0));
+    return TFS_OK;
+  }
+  ~SideStreams() {
+    for (auto x : s)
+      if (x) {
+        cudaStreamSynchronize(x);
+        cudaStreamDestroy(x);
+      }
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace tfs
 
 using namespace tfs;
@@ -495,35 +551,69 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   const double* d_c = coeffs;
   const double* d_f = f_ref;
   float* d_stat = stat;
+  double* up_c = nullptr;  // device copies of host inputs
+  double* up_f = nullptr;
   if (host) {
-    double* c = ar.take<double>((size_t)N * K);
-    TFS_CUDA(cudaMemcpyAsync(c, coeffs, (size_t)N * K * 8, cudaMemcpyHostToDevice, st));
-    d_c = c;
-    if (f_ref) {
-      double* f = ar.take<double>((size_t)N);
-      TFS_CUDA(cudaMemcpyAsync(f, f_ref, (size_t)N * 8, cudaMemcpyHostToDevice, st));
-      d_f = f;
-    }
+    d_c = up_c = ar.take<double>((size_t)N * K);
+    if (f_ref) d_f = up_f = ar.take<double>((size_t)N);
   }
   if (host || !stat) d_stat = ar.take<float>((size_t)N);
   TFS_CUDA(cudaMemsetAsync(d_tc, 0, sizeof(unsigned long long), st));
   TFS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
 
+  // tie reports carry track indices of one launch: chunk only without them
   EvalJob J{table, basis, sp, d_c, d_f, N, m, d_stat, nullptr};
   EvalLaunch L{&J, 1, d_tc, d_tt, d_ts, tie_cap, d_status};
+  const int64_t per = (host && !ties && N > 0) ? host_chunk_tracks(L, N, K) : N;
+  const bool chunked = per < N;
+  SideStreams side;
+  if (!chunked) {
+    if (host) {
+      TFS_CUDA(cudaMemcpyAsync(up_c, coeffs, (size_t)N * K * 8, cudaMemcpyHostToDevice, st));
+      if (f_ref) TFS_CUDA(cudaMemcpyAsync(up_f, f_ref, (size_t)N * 8, cudaMemcpyHostToDevice, st));
+    }
 #ifdef TFS_DEBUG_CHECKS
-  unsigned long long* d_dbg = nullptr;
-  TFS_CUDA(cudaMallocAsync((void**)&d_dbg, 32, st));
-  TFS_CUDA(cudaMemsetAsync(d_dbg, 0, 32, st));
-  L.dbg = d_dbg;
+    unsigned long long* d_dbg = nullptr;
+    TFS_CUDA(cudaMallocAsync((void**)&d_dbg, 32, st));
+    TFS_CUDA(cudaMemsetAsync(d_dbg, 0, 32, st));
+    L.dbg = d_dbg;
 #endif
-  rc = launch_eval(L, EvalTuning(), st);
-  if (rc) return rc;
+    rc = launch_eval(L, EvalTuning(), st);
+    if (rc) return rc;
 #ifdef TFS_DEBUG_CHECKS
-  TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
-  TFS_CUDA(cudaStreamSynchronize(st));
-  cudaFreeAsync(d_dbg, st);
+    TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
+    TFS_CUDA(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_dbg, st);
 #endif
+  } else {
+    // uploads on side stream 0 (after the scratch exists), launches on `stream` as each
+    // chunk arrives, the per-track values read back on side stream 1 as each launch ends
+    rc = side.init();
+    if (rc) return rc;
+    rc = side.order(st, side.s[0]);
+    if (rc) return rc;
+    for (int64_t t0 = 0; t0 < N; t0 += per) {
+      const int64_t n = std::min(per, N - t0);
+      TFS_CUDA(cudaMemcpyAsync(up_c + t0 * K, coeffs + t0 * K, (size_t)n * K * 8,
+                               cudaMemcpyHostToDevice, side.s[0]));
+      if (f_ref)
+        TFS_CUDA(cudaMemcpyAsync(up_f + t0, f_ref + t0, (size_t)n * 8, cudaMemcpyHostToDevice,
+                                 side.s[0]));
+      rc = side.order(side.s[0], st);
+      if (rc) return rc;
+      EvalJob Jc{table, basis, sp, d_c + t0 * K, d_f ? d_f + t0 : nullptr, n, m, d_stat + t0, nullptr};
+      EvalLaunch Lc{&Jc, 1, d_tc, d_tt, d_ts, 0, d_status};
+      rc = launch_eval(Lc, EvalTuning(), st);
+      if (rc) return rc;
+      if (stat) {
+        rc = side.order(st, side.s[1]);
+        if (rc) return rc;
+        TFS_CUDA(cudaMemcpyAsync(stat + t0, d_stat + t0, (size_t)n * 4, cudaMemcpyDeviceToHost, side.s[1]));
+      }
+    }
+    rc = side.order(side.s[1], st);
+    if (rc) return rc;
+  }
 
   int64_t* d_ti = nullptr;
   float* d_tv = nullptr;
@@ -535,7 +625,8 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
     if (rc) return rc;
   }
   if (host) {
-    if (stat && N > 0) TFS_CUDA(cudaMemcpyAsync(stat, d_stat, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    if (stat && N > 0 && !chunked)
+      TFS_CUDA(cudaMemcpyAsync(stat, d_stat, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
     if (kk > 0) {
       TFS_CUDA(cudaMemcpyAsync(top_idx, d_ti, (size_t)kk * 8, cudaMemcpyDeviceToHost, st));
       TFS_CUDA(cudaMemcpyAsync(top_val, d_tv, (size_t)kk * 4, cudaMemcpyDeviceToHost, st));

@@ -248,6 +248,39 @@ def test_eval_stat_full_size_sampled(T, oneyear):
     assert O.stat_relative_error(res.top_val.cpu().numpy(), St) <= STAT_TOL_SAME_TABLE
 
 
+def test_eval_stat_full_size_host_chunks(T, oneyear):
+    """Ten million tracks from host buffers (the end-to-end configuration): the coefficients
+    and offsets go up in chunks, each evaluated as soon as it has arrived, and the values come
+    back chunk by chunk.  Bins are those of one launch; the statistic agrees with the
+    device-pointer call within FP32 rounding (the tiling decides which pairs take the FP64
+    fix-up), a sample matches the oracle, and the top-k is that of the returned values."""
+    torch = pytest.importorskip("torch")
+    w = oneyear["w"]
+    N = w.n_tracks
+    rng = np.random.default_rng(17)
+    coeffs = synth.uniform_coeffs(N, oneyear["cmin"], oneyear["cmax"], rng)
+    f_ref = rng.uniform(-0.5, 0.5, N) / w.T_sft
+    table = T.table_from_power(oneyear["P64"], w.T_sft, "f32")
+    basis = T.basis_from_host(oneyear["V"])
+    res = T.eval_stat(table, basis, coeffs, f_ref, m=1, topk=128)
+    dev = T.eval_stat(table, basis, torch.from_numpy(coeffs).cuda(), torch.from_numpy(f_ref).cuda(), m=1, topk=128)
+    torch.cuda.synchronize()
+    assert O.stat_relative_error(res.stat.astype(np.float64), dev.stat.cpu().numpy().astype(np.float64)) <= 1e-5
+    sample = rng.choice(N, 20000, replace=False)
+    Pq, _ = O.quantise_table(oneyear["P64"], "f32")
+    S, *_ = O.eval_stat(Pq, oneyear["V"], coeffs[sample], f_ref[sample], w.T_sft, 1)
+    assert O.stat_relative_error(res.stat[sample].astype(np.float64), S) <= STAT_TOL_SAME_TABLE
+    gi, _ = O.topk(res.stat.astype(np.float64), 128)
+    assert np.array_equal(res.top_idx, gi)
+    assert np.array_equal(res.top_val, res.stat[gi])
+    # top-k alone (no per-track output): the same launches, the same answer
+    ti = np.empty(128, np.int64)
+    tv = np.empty(128, np.float32)
+    T.check(T.lib().tfs_eval_stat(table.handle, basis.handle, coeffs.ctypes.data, f_ref.ctypes.data, N, 1, 128,
+                                  None, ti.ctypes.data, tv.ctypes.data, None, 0, None))
+    assert np.array_equal(ti, gi) and np.array_equal(tv, res.top_val)
+
+
 def test_injected_track_stands_out(T, tiny):
     """Strain -> GPU table -> statistic of the true track: far above the noise
     distribution of m = 1 (mean 2*64*3, variance 19.33*64)."""
