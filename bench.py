@@ -349,17 +349,24 @@ def run_ours(args):
         c_e2e = torch.empty_like(coeffs_d)
         e2e_job = T.Job(table, basis, c_e2e, None, m=w.m, topk=kk, stat=stat, segment_cuts=True)
 
+    # one stream of its own: the rebuild returns once the strain is up and its transform
+    # overlaps the upload of the first coefficients; the statistic call returns with the
+    # top-k in host memory
+    e2e_stream = torch.cuda.Stream()
+    e2e_sp = ctypes.c_void_p(e2e_stream.cuda_stream)
+
     def e2e_step():
-        T.check(L.tfs_table_rebuild(table.handle, x_pin.data_ptr(), x_pin.numel(), 0, None))
+        T.check(L.tfs_table_rebuild(table.handle, x_pin.data_ptr(), x_pin.numel(), 0, e2e_sp))
         if cut_job is None:
             T.check(L.tfs_eval_stat(table.handle, basis.handle, c_pin.data_ptr(), None, N, w.m, kk, None,
-                                    e_top_i.ctypes.data, e_top_v.ctypes.data, None, 0, None))
+                                    e_top_i.ctypes.data, e_top_v.ctypes.data, None, 0, e2e_sp))
         else:
             # host coefficients uploaded on the stream, the batched entry point, top-k read back
-            c_e2e.copy_(c_pin, non_blocking=True)
-            T.eval_batch([e2e_job], stream=stream.cuda_stream)
-            e_top_i[:] = e2e_job.top_idx.cpu().numpy()
-            e_top_v[:] = e2e_job.top_val.cpu().numpy()
+            with torch.cuda.stream(e2e_stream):
+                c_e2e.copy_(c_pin, non_blocking=True)
+                T.eval_batch([e2e_job], stream=e2e_stream.cuda_stream)
+                e_top_i[:] = e2e_job.top_idx.cpu().numpy()
+                e_top_v[:] = e2e_job.top_val.cpu().numpy()
 
     e2e_step()
     if world > 1:

@@ -102,10 +102,12 @@ int tfs_build_sfts(const double* strain, int64_t n, double dt, double T_sft, int
 
 /* Recompute an existing table (made by tfs_build_sfts) from new strain of
  * the same length in segments, with the dt, T_sft, window, PSD and dtype
- * given at build time.  Allocates only stream-ordered scratch.  mem = DEVICE:
- * enqueued on `stream`, returns without waiting (unless stream is NULL);
- * mem = HOST: returns when done.  INVALID_ARG if n / L differs from n_seg or
- * the table was not built from strain. */
+ * given at build time.  Allocates only stream-ordered scratch.  Enqueued on
+ * `stream`; with stream NULL the call returns when the table is complete.
+ * Otherwise mem = DEVICE returns without waiting and mem = HOST returns once
+ * the strain has been copied (the host buffer may then be reused), the
+ * transform still running on `stream`.  INVALID_ARG if n / L differs from
+ * n_seg or the table was not built from strain. */
 int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, int mem, void* stream);
 
 /* Wrap an existing FP64 power table P [n_seg][n_bin] (e.g. computed elsewhere)

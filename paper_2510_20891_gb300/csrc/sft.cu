@@ -713,15 +713,31 @@ extern "C" int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, 
   const double* d_x = strain;
   double* tmp = nullptr;
   const size_t xbytes = (size_t)t->n_seg * p->L * 8;
+  cudaEvent_t copied = nullptr;  // host strain with a stream: wait for the upload only
   if (mem == TFS_MEM_HOST) {
-    TFS_CUDA(cudaMallocAsync((void**)&tmp, xbytes, st));
-    TFS_CUDA(cudaMemcpyAsync(tmp, strain, xbytes, cudaMemcpyHostToDevice, st));
+    if (st != nullptr) TFS_CUDA(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+    cudaError_t e = cudaMallocAsync((void**)&tmp, xbytes, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, strain, xbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && copied) e = cudaEventRecord(copied, st);
+    if (e != cudaSuccess) {
+      if (copied) cudaEventDestroy(copied);
+      if (tmp) cudaFreeAsync(tmp, st);
+      cudaStreamSynchronize(st);
+      return cuda_fail(e, "strain upload");
+    }
     d_x = tmp;
   }
   int rc = run_sft(p, d_x, t, st);
   if (tmp) cudaFreeAsync(tmp, st);
+  if (copied) {
+    // the caller may reuse the host strain once it has been copied; the transform keeps
+    // running on the stream
+    const cudaError_t e = cudaEventSynchronize(copied);
+    cudaEventDestroy(copied);
+    if (rc == TFS_OK && e != cudaSuccess) rc = cuda_fail(e, "strain upload");
+  }
   if (rc) return rc;
-  if (mem == TFS_MEM_HOST || st == nullptr) TFS_CUDA(cudaStreamSynchronize(st));
+  if (st == nullptr) TFS_CUDA(cudaStreamSynchronize(st));
   return TFS_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <atomic>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -281,6 +282,25 @@ int launch_eval(const EvalLaunch& L, const EvalTuning& tune_in, cudaStream_t st)
   return TFS_ERR_INVALID_ARG;
 }
 
+// Stream-ordered scratch comes from the device's default memory pool, which by default
+// returns all freed memory to the system at every synchronisation, so that the next call
+// maps its scratch afresh (hundreds of MB for host inputs).  Keep up to 8 GB reserved
+// (never lowering a larger threshold set by the application).
+static void retain_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  done.push_back(dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  uint64_t cur = 0, want = (uint64_t)8 << 30;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < want)
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+}
+
 // A small device arena for one call: one cudaMallocAsync, freed stream-ordered.
 struct Arena {
   char* base = nullptr;
@@ -293,6 +313,7 @@ struct Arena {
     st = s;
     size = bytes;
     if (bytes == 0) return TFS_OK;
+    retain_pool_memory();
     TFS_CUDA(cudaMallocAsync((void**)&base, bytes, s));
     return TFS_OK;
   }
@@ -328,8 +349,23 @@ static int64_t host_chunk_tracks(const EvalLaunch& L, int64_t N, int K) {
   return r * round >= N ? N : r * round;
 }
 
+// Device memory allocated on one stream and freed on another (after its last use there).
+struct CrossBuf {
+  char* p = nullptr;
+  cudaStream_t free_on = nullptr;
+  int init(size_t bytes, cudaStream_t alloc_on, cudaStream_t free_st) {
+    free_on = free_st;
+    retain_pool_memory();
+    TFS_CUDA(cudaMallocAsync((void**)&p, bytes, alloc_on));
+    return TFS_OK;
+  }
+  ~CrossBuf() {
+    if (p) cudaFreeAsync(p, free_on);
+  }
+};
+
 // Side streams of one call, drained before the call's scratch is freed (declare after the
-// Arena so that this is destroyed first) and on every early return.
+// Arena and any CrossBuf so that this is destroyed first) and on every early return.
 struct SideStreams {
   cudaStream_t s[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> ev;
@@ -534,11 +570,21 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   int rc = get_segparams(basis, table->T_sft, 0, st, &sp);
   if (rc) return rc;
 
+  // host inputs go up in chunks (tie reports carry track indices of one launch: not with them)
+  int64_t per = N;
+  if (host && !ties && N > 0) {
+    EvalJob J0{table, basis, sp, nullptr, nullptr, N, m, nullptr, nullptr};
+    EvalLaunch L0{&J0, 1, nullptr, nullptr, nullptr, 0, nullptr};
+    per = host_chunk_tracks(L0, N, K);
+  }
+  const bool chunked = per < N;
+  const size_t up_bytes = host ? round256((size_t)N * K * 8) + (f_ref ? round256((size_t)N * 8) : 0) : 0;
+
   // one arena for everything this call needs on the device
   size_t need = 0;
   need += round256(sizeof(unsigned long long)) + round256(sizeof(int));
   need += round256((size_t)std::max(tie_cap, 1) * 8) + round256((size_t)std::max(tie_cap, 1) * 4);
-  if (host) need += round256((size_t)N * K * 8) + round256((size_t)N * 8);
+  if (host && !chunked) need += up_bytes;
   if (host || !stat) need += round256((size_t)N * 4);
   if (kk > 0) need += round256((size_t)kk * 12) + round256(topk_workspace_bytes(N));
   Arena ar;
@@ -548,25 +594,31 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
   int* d_status = ar.take<int>(1);
   int64_t* d_tt = ar.take<int64_t>(std::max(tie_cap, 1));
   int* d_ts = ar.take<int>(std::max(tie_cap, 1));
-  const double* d_c = coeffs;
-  const double* d_f = f_ref;
-  float* d_stat = stat;
+  // chunked uploads: their buffer is allocated on side stream 0, so that they need not wait
+  // for earlier work on `stream` (a table rebuild, say), and freed on `stream`
+  CrossBuf upb;
+  SideStreams side;
   double* up_c = nullptr;  // device copies of host inputs
   double* up_f = nullptr;
-  if (host) {
-    d_c = up_c = ar.take<double>((size_t)N * K);
-    if (f_ref) d_f = up_f = ar.take<double>((size_t)N);
+  if (chunked) {
+    rc = side.init();
+    if (rc) return rc;
+    rc = upb.init(up_bytes, side.s[0], st);
+    if (rc) return rc;
+    up_c = reinterpret_cast<double*>(upb.p);
+    if (f_ref) up_f = reinterpret_cast<double*>(upb.p + round256((size_t)N * K * 8));
+  } else if (host) {
+    up_c = ar.take<double>((size_t)N * K);
+    if (f_ref) up_f = ar.take<double>((size_t)N);
   }
-  if (host || !stat) d_stat = ar.take<float>((size_t)N);
+  const double* d_c = host ? up_c : coeffs;
+  const double* d_f = host ? up_f : f_ref;
+  float* d_stat = (host || !stat) ? ar.take<float>((size_t)N) : stat;
   TFS_CUDA(cudaMemsetAsync(d_tc, 0, sizeof(unsigned long long), st));
   TFS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
 
-  // tie reports carry track indices of one launch: chunk only without them
   EvalJob J{table, basis, sp, d_c, d_f, N, m, d_stat, nullptr};
   EvalLaunch L{&J, 1, d_tc, d_tt, d_ts, tie_cap, d_status};
-  const int64_t per = (host && !ties && N > 0) ? host_chunk_tracks(L, N, K) : N;
-  const bool chunked = per < N;
-  SideStreams side;
   if (!chunked) {
     if (host) {
       TFS_CUDA(cudaMemcpyAsync(up_c, coeffs, (size_t)N * K * 8, cudaMemcpyHostToDevice, st));
@@ -586,12 +638,8 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
     cudaFreeAsync(d_dbg, st);
 #endif
   } else {
-    // uploads on side stream 0 (after the scratch exists), launches on `stream` as each
-    // chunk arrives, the per-track values read back on side stream 1 as each launch ends
-    rc = side.init();
-    if (rc) return rc;
-    rc = side.order(st, side.s[0]);
-    if (rc) return rc;
+    // uploads on side stream 0, launches on `stream` as each chunk arrives, the per-track
+    // values read back on side stream 1 as each launch ends
     for (int64_t t0 = 0; t0 < N; t0 += per) {
       const int64_t n = std::min(per, N - t0);
       TFS_CUDA(cudaMemcpyAsync(up_c + t0 * K, coeffs + t0 * K, (size_t)n * K * 8,

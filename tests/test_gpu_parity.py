@@ -142,6 +142,22 @@ def test_table_rebuild_equals_build(T, tiny):
     assert np.array_equal(table.to_host()[0], fresh.to_host()[0])
 
 
+def test_table_rebuild_host_strain_on_a_stream(T, tiny):
+    """Host strain and a stream: the call returns once the strain has been copied (the buffer
+    may be overwritten at once) and the transform completes on the stream."""
+    torch = pytest.importorskip("torch")
+    w = tiny["w"]
+    table = T.build_sfts(tiny["x"], w.dt, w.T_sft, tiny["psd"], "hann", "f32")
+    x2 = np.random.default_rng(10).standard_normal(w.n_samples)
+    keep = x2.copy()
+    s = torch.cuda.Stream()
+    T.check(T.lib().tfs_table_rebuild(table.handle, x2.ctypes.data, x2.size, 0, s.cuda_stream))
+    x2[:] = np.nan
+    s.synchronize()
+    fresh = T.build_sfts(keep, w.dt, w.T_sft, tiny["psd"], "hann", "f32")
+    assert np.array_equal(table.to_host()[0], fresh.to_host()[0])
+
+
 # --------------------------------------------------------------------------- basis
 def _basis_tol(s, k):
     gap = min([abs(s[k] - s[j]) for j in range(len(s)) if j != k] + [s[k]])
@@ -273,11 +289,13 @@ def test_eval_stat_full_size_host_chunks(T, oneyear):
     gi, _ = O.topk(res.stat.astype(np.float64), 128)
     assert np.array_equal(res.top_idx, gi)
     assert np.array_equal(res.top_val, res.stat[gi])
-    # top-k alone (no per-track output): the same launches, the same answer
+    # top-k alone (no per-track output), on a stream of its own: the same launches, the same
+    # answer, in host memory when the call returns
     ti = np.empty(128, np.int64)
     tv = np.empty(128, np.float32)
+    s = torch.cuda.Stream()
     T.check(T.lib().tfs_eval_stat(table.handle, basis.handle, coeffs.ctypes.data, f_ref.ctypes.data, N, 1, 128,
-                                  None, ti.ctypes.data, tv.ctypes.data, None, 0, None))
+                                  None, ti.ctypes.data, tv.ctypes.data, None, 0, s.cuda_stream))
     assert np.array_equal(ti, gi) and np.array_equal(tv, res.top_val)
 
 
