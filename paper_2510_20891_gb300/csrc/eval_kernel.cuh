@@ -965,8 +965,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
             for (int p = 0; p < R2; ++p) yv[p] = f2fma(c2[p][k], d2[k], yv[p]);
           if constexpr (COMPLETE && !CUTS && !BINS) {
             // the hot path in three passes: every slot offset and decision, every gather, every sum
+            // the decisions are first OR-ed into one flag; only when a pair of the thread is
+            // undecided (a few in 10^4 pairs) are they taken one by one, y recomputed as above
             unsigned offs[2 * R2];
-            unsigned undm = 0u;
+            bool und = false;
 #pragma unroll
             for (int p = 0; p < R2; ++p) {
               const f32x2 tt2 = f2add(yv[p], kC2);
@@ -977,12 +979,30 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
 #pragma unroll
               for (int hh = 0; hh < 2; ++hh) {
                 offs[2 * p + hh] = min((unsigned)__float_as_int(tts[hh]) + koff, qn);
-                undm |= (unsigned)!(fabsf(dds[hh]) < wlim) << (2 * p + hh);
+                und |= !(fabsf(dds[hh]) < wlim);
               }
             }
             float vals[2 * R2];
 #pragma unroll
             for (int r = 0; r < R; ++r) vals[r] = q[offs[r]];
+            if (!und) {
+#pragma unroll
+              for (int r = 0; r < R; ++r) acc[r] += vals[r];
+              return;
+            }
+            unsigned undm = 0u;
+#pragma unroll
+            for (int p = 0; p < R2; ++p) {
+              f32x2 y2 = y02[p];
+#pragma unroll
+              for (int k = 0; k < KP; ++k) y2 = f2fma(c2[p][k], d2[k], y2);
+              const f32x2 tt2 = f2add(y2, kC2);
+              const f32x2 dd2 = f2sub(y2, f2sub(tt2, kC2));
+              float dds[2];
+              f2split(dd2, dds[0], dds[1]);
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) undm |= (unsigned)!(fabsf(dds[hh]) < wlim) << (2 * p + hh);
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] += ((undm >> r) & 1u) ? 0.f : vals[r];
             pend |= undm & ((R >= 32) ? 0xffffffffu : ((1u << R) - 1u));
