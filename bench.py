@@ -585,7 +585,7 @@ def run_tpl_search(args):
     """The paper's whole search (Sec. II.D) on one year of data in 631 SFTs of 5e4 s: 48 chunks of
     growing duration, 1024 initial candidates per chunk, the best 512 kept, then DE iterations,
     each one graph-replayed batched launch over all chunks.  Value: statistic evaluations/s of the
-    whole search, host included (the random draws, uploads and the driver are inside)."""
+    whole search, host included (the random draws, uploads and the search driver are inside)."""
     import torch
 
     from paper_2510_20891_gb300 import build as B

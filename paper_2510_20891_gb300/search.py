@@ -118,7 +118,7 @@ class DESearch:
         self.K = self.lo.size
         self.graph = graph
         self.cuts = segment_cuts  # the paper's exclusions (Sec. II.B, II.D)
-        self.statistic = statistic  # "nearest" (the configs' default) or "chirp" (the paper's S_alpha)
+        self.statistic = statistic  # "nearest" (nearest-bin power sums) or "chirp" (the paper's S_alpha)
 
     def _initial(self, U_chunk):
         """n_init candidates uniform in the prior box, each track shifted by a constant so that
