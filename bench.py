@@ -820,6 +820,7 @@ def run_served(args):
     """Poisson requests (a dataset and 10^3-10^6 tracks, BF16 or FP32 table) against resident
     datasets of the 1577 x 20001 shape, served with continuous batching under a budget;
     compared with the plain FP32 path that runs one request at a time."""
+    import queue
     import threading
 
     import torch
@@ -858,15 +859,21 @@ def run_served(args):
     done_t = [0.0] * len(reqs)
     t_start = time.perf_counter()
 
-    def collect(k, n_threads):
-        for i in range(k, len(reqs), n_threads):
-            while tickets[i] is None:
-                time.sleep(0.0002)
+    # collectors block on a queue and enter the server's wait as soon as a ticket exists (a
+    # collector that polled for its ticket could enter late, and the server's latency, which
+    # runs from submit to results in host memory, would count that)
+    todo = queue.Queue()
+
+    def collect():
+        while True:
+            i = todo.get()
+            if i is None:
+                return
             srv.wait(tickets[i], 600000)
             done_t[i] = time.perf_counter()
 
     n_coll = 16
-    coll = [threading.Thread(target=collect, args=(k, n_coll)) for k in range(n_coll)]
+    coll = [threading.Thread(target=collect) for _ in range(n_coll)]
     for t in coll:
         t.start()
     with ClockSampler(0) as clk:
@@ -875,6 +882,9 @@ def run_served(args):
             if ta > now:
                 time.sleep(ta - now)
             tickets[i] = srv.submit(ids[(d, dt)], coeffs_of(i), None, m=w.m, topk=16)
+            todo.put(i)
+        for _ in coll:
+            todo.put(None)
         for t in coll:
             t.join()
     t_end = max(done_t)

@@ -13,7 +13,8 @@
 // that is not resident, fit under the budget; idle tables (no admitted or
 // running request uses them) are evicted least recently used first to make
 // room (their bytes are kept in host memory and copied back on the next use).
-// Results are copied out by tfs_server_wait in the caller's thread.
+// Results are copied out by tfs_server_wait in the caller's thread, through pinned buffers
+// the server keeps (one per concurrent waiter).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -64,6 +65,15 @@ struct SrvReq {
   std::string err;
 };
 
+// A stream and a pinned buffer through which tfs_server_wait copies results out.  A copy into
+// pageable memory is staged by the driver, and under the worker's concurrent uploads (also
+// staged) a few MB took milliseconds; a pinned destination is a plain DMA.
+constexpr size_t kCopyChunk = (size_t)8 << 20;
+struct CopySlot {
+  cudaStream_t st = nullptr;
+  void* pinned = nullptr;
+};
+
 struct SrvBatch {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
@@ -88,6 +98,8 @@ struct tfs_server {
   int64_t used = 0;  // resident tables + admitted/running/uncollected request buffers
   int64_t use_clock = 0;
   SrvBatch batch[2];
+  std::mutex copy_mu;                // guards copy_free (slots are created on demand)
+  std::vector<CopySlot*> copy_free, copy_all;
   std::thread worker;
   bool stop = false;
   // statistics
@@ -393,6 +405,50 @@ int tfs_server_submit(tfs_server* s, int ds_id, const double* coeffs, const doub
   return TFS_OK;
 }
 
+namespace {
+
+cudaError_t take_copy_slot(tfs_server* s, CopySlot** out) {
+  {
+    std::lock_guard<std::mutex> g(s->copy_mu);
+    if (!s->copy_free.empty()) {
+      *out = s->copy_free.back();
+      s->copy_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  CopySlot* c = new CopySlot();
+  cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, kCopyChunk);
+  if (e != cudaSuccess) {
+    if (c->st) cudaStreamDestroy(c->st);
+    delete c;
+    return e;
+  }
+  std::lock_guard<std::mutex> g(s->copy_mu);
+  s->copy_all.push_back(c);
+  *out = c;
+  return cudaSuccess;
+}
+
+void give_copy_slot(tfs_server* s, CopySlot* c) {
+  std::lock_guard<std::mutex> g(s->copy_mu);
+  s->copy_free.push_back(c);
+}
+
+// device -> caller's host memory through the slot's pinned buffer, a chunk at a time
+cudaError_t copy_out(CopySlot* c, void* dst, const void* src, size_t bytes) {
+  for (size_t o = 0; o < bytes; o += kCopyChunk) {
+    const size_t n = std::min(kCopyChunk, bytes - o);
+    cudaError_t e = cudaMemcpyAsync(c->pinned, static_cast<const char*>(src) + o, n, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return e;
+    std::memcpy(static_cast<char*>(dst) + o, c->pinned, n);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 int tfs_server_wait(tfs_server* s, int64_t ticket, int timeout_ms, float* stat, int64_t* top_idx, float* top_val) {
   clear_error();
   TFS_CHECK(s, TFS_ERR_INVALID_ARG, "null server");
@@ -412,18 +468,20 @@ int tfs_server_wait(tfs_server* s, int64_t ticket, int timeout_ms, float* stat, 
   int rc = r->rc;
   std::string err = r->err;
   if (r->state == kDone) {
-    // copy the results out on a private stream (the worker's streams keep running)
+    // copy the results out on a copy slot's stream (the worker's streams keep running)
     cudaSetDevice(s->device);
-    cudaStream_t st = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e == cudaSuccess && stat) e = cudaMemcpyAsync(stat, r->d_stat, (size_t)r->N * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && r->topk && top_idx)
-      e = cudaMemcpyAsync(top_idx, r->d_ti, (size_t)r->topk * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && r->topk && top_val)
-      e = cudaMemcpyAsync(top_val, r->d_tv, (size_t)r->topk * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaFreeAsync(r->dev, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (st) cudaStreamDestroy(st);
+    CopySlot* c = nullptr;
+    cudaError_t e = take_copy_slot(s, &c);
+    if (e == cudaSuccess && stat) e = copy_out(c, stat, r->d_stat, (size_t)r->N * 4);
+    if (e == cudaSuccess && r->topk && top_idx) e = copy_out(c, top_idx, r->d_ti, (size_t)r->topk * 8);
+    if (e == cudaSuccess && r->topk && top_val) e = copy_out(c, top_val, r->d_tv, (size_t)r->topk * 4);
+    if (c) {
+      if (e == cudaSuccess) e = cudaFreeAsync(r->dev, c->st);
+      else cudaFree(r->dev);
+      give_copy_slot(s, c);
+    } else if (r->dev) {
+      cudaFree(r->dev);
+    }
     if (e != cudaSuccess) {
       rc = TFS_ERR_CUDA;
       err = cudaGetErrorString(e);
@@ -498,6 +556,12 @@ int tfs_server_free(tfs_server* s) {
   for (SrvDataset* d : s->ds) {
     tfs_table_free(d->table);
     delete d;
+  }
+  for (CopySlot* c : s->copy_all) {
+    cudaStreamSynchronize(c->st);
+    cudaStreamDestroy(c->st);
+    cudaFreeHost(c->pinned);
+    delete c;
   }
   for (SrvBatch& b : s->batch) {
     if (b.ev) cudaEventDestroy(b.ev);
