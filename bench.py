@@ -41,7 +41,8 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for the one-year workload, about 1 s, so that the clocks are sampled several times; 20 otherwise)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="oneyear_daily_fp32")
@@ -64,7 +65,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="request arrival rate (Hz) of the served workload")
     ap.add_argument("--datasets", type=int, default=32, help="resident datasets of the served workload")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="device-memory budget of the served workload")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if (args.impl == "ours" and args.workload == "oneyear_daily_fp32") else 20
+    return args
 
 
 # --------------------------------------------------------------------------- inputs
