@@ -360,6 +360,21 @@ int tfs_de_propose(const double* c, int64_t N, int K, const int32_t* r1, const i
 int tfs_de_accept(double* c, float* s, const double* c_trial, const float* s_trial, const int32_t* in_prior,
                   int64_t N, int K, void* stream);
 
+/* The random draws of one DE iteration (Sec. II.D: for walker t of a chunk of W,
+ * two distinct partners r1, r2 other than t from the same chunk, and F_DE
+ * uniform in [f_lo, f_hi)), from the counter-based SplitMix64 generator (Steele,
+ * Lea and Flood 2014): s(k) = mix(seed + k * 0x9E3779B97F4A7C15 mod 2^64) with
+ * its 64-bit finaliser.  Walker g = c W + t of iteration i = *iter takes
+ * z_j = s(3 (i n + g) + j), j = 1, 2, 3 (n = n_chunks W); a = 1 + ((z_1 >> 32)
+ * (W - 1) >> 32), b = 1 + ((z_2 >> 32) (W - 2) >> 32), b += (b >= a);
+ * r1 = c W + (t + a) mod W, r2 = c W + (t + b) mod W; F = f_lo + (f_hi - f_lo)
+ * u with u = (z_3 >> 40) 2^-24, each FP32 operation rounded to nearest.
+ * iter: a device int32, read and then incremented by the call (so a captured
+ * graph draws afresh on every replay).  r1, r2 (int32) and F (float) [n]
+ * device arrays.  W >= 3, n < 2^31, f_lo <= f_hi.  Stream-ordered, asynchronous. */
+int tfs_de_draw(uint64_t seed, int32_t* iter, int64_t n_chunks, int W, float f_lo, float f_hi, int32_t* r1,
+                int32_t* r2, float* F, void* stream);
+
 /* ---- the paper's linear-chirp statistic (Sec. II.B, Eq. det_stat) ----------
  * The full per-segment statistic of the paper: the local waveform of segment
  * alpha is the chirping sinusoid exp(i [2 pi f_a (t - t_a) + pi fdot_a (t - t_a)^2])

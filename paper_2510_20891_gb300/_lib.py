@@ -52,6 +52,7 @@ SIGNATURES = {
     "tfs_basis_view": (I, [P, I64, I64, P]),
     "tfs_de_propose": (I, [P, I64, I, P, P, P, P, P, P, P, P]),
     "tfs_de_accept": (I, [P, P, P, P, P, I64, I, P]),
+    "tfs_de_draw": (I, [ctypes.c_uint64, P, I64, I, ctypes.c_float, ctypes.c_float, P, P, P, P]),
     "tfs_build_chirp_table": (I, [P, I64, D, D, P, I, P, P]),
     "tfs_ctable_view": (I, [P, I64, I64, P]),
     "tfs_eval_chirp_batch": (I, [P, I, P]),

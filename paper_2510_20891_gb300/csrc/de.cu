@@ -3,7 +3,10 @@
 // Tracks are linear in the coefficients (f = f_ref + sum_k c_k U_k), so the proposal's
 // projection back onto the basis through its pseudo-inverse is exactly
 // c + F_DE (c_r1 - c_r2); both steps therefore run on the coefficients.  The random draws
-// (r1, r2, F_DE) are inputs.
+// (r1, r2, F_DE) are inputs, or come from tfs_de_draw: the counter-based SplitMix64 generator
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014)
+// keyed by a seed and an iteration number kept on the device, so that a captured graph of one
+// iteration draws afresh on every replay.
 #include <cstdint>
 
 #include "tfs_internal.cuh"
@@ -27,6 +30,37 @@ __global__ void de_propose_kernel(const double* __restrict__ c, int64_t N, int K
     ok &= (v >= lo[k] && v <= hi[k]) ? 1 : 0;
   }
   in_prior[t] = ok;
+}
+
+// SplitMix64: the output for the state after `k` steps from `seed`, the golden-gamma increment
+// added k times (mod 2^64) and the 64-bit finaliser applied.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * kGamma;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// One block: every thread reads the iteration number, the block draws for all walkers, and
+// thread 0 advances the number after the block's last read.
+__global__ void de_draw_kernel(uint64_t seed, int32_t* __restrict__ iter, int64_t n, int W, float f_lo, float f_hi,
+                               int32_t* __restrict__ r1, int32_t* __restrict__ r2, float* __restrict__ F) {
+  const uint64_t it = (uint64_t)(uint32_t)iter[0];
+  for (int64_t g = threadIdx.x; g < n; g += blockDim.x) {
+    const uint64_t k = 3u * (it * (uint64_t)n + (uint64_t)g);
+    const uint64_t z0 = splitmix64_at(seed, k + 1u), z1 = splitmix64_at(seed, k + 2u), z2 = splitmix64_at(seed, k + 3u);
+    const int64_t c0 = g - g % W, t = g % W;
+    const int64_t a = 1 + (int64_t)(((z0 >> 32) * (uint64_t)(W - 1)) >> 32);  // 1 .. W-1
+    int64_t b = 1 + (int64_t)(((z1 >> 32) * (uint64_t)(W - 2)) >> 32);        // 1 .. W-2, then skip a
+    b += (b >= a) ? 1 : 0;
+    r1[g] = (int32_t)(c0 + (t + a) % W);
+    r2[g] = (int32_t)(c0 + (t + b) % W);
+    const float u = (float)(uint32_t)(z2 >> 40) * 0x1p-24f;  // [0, 1), exact
+    F[g] = __fadd_rn(f_lo, __fmul_rn(__fsub_rn(f_hi, f_lo), u));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) iter[0] = (int32_t)(it + 1u);
 }
 
 __global__ void de_accept_kernel(double* __restrict__ c, float* __restrict__ s, const double* __restrict__ ct,
@@ -72,4 +106,21 @@ extern "C" int tfs_de_accept(double* c, float* s, const double* c_trial, const f
   count_launch();
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TFS_OK : cuda_fail(e, "de_accept");
+}
+
+extern "C" int tfs_de_draw(uint64_t seed, int32_t* iter, int64_t n_chunks, int W, float f_lo, float f_hi, int32_t* r1,
+                           int32_t* r2, float* F, void* stream) {
+  clear_error();
+  TFS_CHECK(W >= 3, TFS_ERR_INVALID_ARG, "need at least 3 walkers per chunk");
+  TFS_CHECK(n_chunks >= 0 && n_chunks * (int64_t)W < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG,
+            "n_chunks * W must be in [0, 2^31)");
+  TFS_CHECK(f_lo <= f_hi, TFS_ERR_INVALID_ARG, "f_lo must not exceed f_hi");
+  TFS_CHECK(iter, TFS_ERR_INVALID_ARG, "null iteration counter");
+  const int64_t n = n_chunks * (int64_t)W;
+  TFS_CHECK(n == 0 || (r1 && r2 && F), TFS_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  de_draw_kernel<<<1, 1024, 0, st>>>(seed, iter, n, W, f_lo, f_hi, r1, r2, F);
+  count_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TFS_OK : cuda_fail(e, "de_draw");
 }

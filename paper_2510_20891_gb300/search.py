@@ -119,6 +119,7 @@ class DESearch:
         self.graph = graph
         self.cuts = segment_cuts  # the paper's exclusions (Sec. II.B, II.D)
         self.statistic = statistic  # "nearest" (nearest-bin power sums) or "chirp" (the paper's S_alpha)
+        self.uncounted_launches = 0  # kernels of graph replays beyond the captured one (set by run)
 
     def _initial(self, U_chunk):
         """n_init candidates uniform in the prior box, each track shifted by a constant so that
@@ -161,24 +162,12 @@ class DESearch:
         views = [ct[i * W:(i + 1) * W] for i in range(n_ch)]
         stats = [s_trial[i * W:(i + 1) * W] for i in range(n_ch)]
         trial_jobs = s.jobs(views, m=self.m, stats=stats, segment_cuts=self.cuts, statistic=self.statistic)
-        base = (np.arange(n_ch) * W).repeat(W)
         # the random draws of every iteration (r1 != r2 != t within the walker's own chunk,
-        # F_DE ~ U[0.3, 1.5]), made up front and uploaded once
+        # F_DE ~ U[0.3, 1.5]) come from a counter-based generator on the device, keyed by one
+        # seed and an iteration number that each draw advances
         n = n_ch * W
-        t_loc = np.tile(np.arange(W), n_ch)
-        R1 = np.empty((n_iter, n), np.int32)
-        R2 = np.empty((n_iter, n), np.int32)
-        FF = np.empty((n_iter, n), np.float32)
-        for it in range(n_iter):
-            r1 = (t_loc + self.rng.integers(1, W, n)) % W
-            r2 = (t_loc + self.rng.integers(1, W - 1, n)) % W
-            r2 = np.where(r2 == r1, (r2 + 1) % W, r2)
-            r2 = np.where(r2 == t_loc, (r2 + 1) % W, r2)
-            r2 = np.where(r2 == r1, (r2 + 1) % W, r2)
-            R1[it] = base + r1
-            R2[it] = base + r2
-            FF[it] = self.rng.uniform(0.3, 1.5, n)
-        R1_d, R2_d, FF_d = (torch.tensor(a, device=dev) for a in (R1, R2, FF))
+        seed = int(self.rng.integers(0, 1 << 63))
+        it_d = torch.zeros(1, dtype=torch.int32, device=dev)
         r1_b = torch.empty(n, dtype=torch.int32, device=dev)
         r2_b = torch.empty(n, dtype=torch.int32, device=dev)
         F_b = torch.empty(n, dtype=torch.float32, device=dev)
@@ -187,6 +176,8 @@ class DESearch:
 
         def iteration(strm):
             sp = strm.cuda_stream
+            check(L.tfs_de_draw(seed, it_d.data_ptr(), n_ch, W, 0.3, 1.5, r1_b.data_ptr(), r2_b.data_ptr(),
+                                F_b.data_ptr(), sp))
             check(L.tfs_de_propose(c.data_ptr(), n, K, r1_b.data_ptr(), r2_b.data_ptr(), F_b.data_ptr(),
                                    lo.data_ptr(), hi.data_ptr(), ct.data_ptr(), inp.data_ptr(), sp))
             s.launch(trial_jobs, self.statistic, dev_status=status, stream=sp)
@@ -198,13 +189,15 @@ class DESearch:
             with torch.cuda.stream(side):
                 graph = None
                 if self.graph:
-                    # one propose + batched statistic + accept, captured once and replayed
-                    r1_b.copy_(R1_d[0]); r2_b.copy_(R2_d[0]); F_b.copy_(FF_d[0])
+                    # one draw + propose + batched statistic + accept, captured once and replayed
+                    # (the library counts the captured kernels once; replays pass it by)
                     graph = torch.cuda.CUDAGraph()
+                    k0 = L.tfs_kernel_launches()
                     with torch.cuda.graph(graph, stream=side):
                         iteration(side)
+                    per_iter = L.tfs_kernel_launches() - k0
+                    self.uncounted_launches = per_iter * (n_iter - 1)
                 for it in range(n_iter):
-                    r1_b.copy_(R1_d[it]); r2_b.copy_(R2_d[it]); F_b.copy_(FF_d[it])
                     if graph is not None:
                         graph.replay()
                     else:

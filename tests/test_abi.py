@@ -84,6 +84,12 @@ def test_host_validation_without_device(L):
     assert L.tfs_table_import(ctypes.cast(x, P), None, 0, 10, 1.0, 0, ctypes.byref(out)) == -1
     assert L.tfs_ctable_view(None, 0, 1, ctypes.byref(out)) == -1
     assert ctypes.sizeof(_lib.TfsChirpJob) == 7 * 8 and _lib.TfsChirpJob.P.offset == 40
+    # the search's device draws: fewer than 3 walkers, an empty interval or no counter
+    it = (ctypes.c_int32 * 1)()
+    assert L.tfs_de_draw(1, ctypes.cast(it, P), 4, 2, 0.3, 1.5, None, None, None, None) == -1
+    assert L.tfs_de_draw(1, ctypes.cast(it, P), 4, 8, 1.5, 0.3, None, None, None, None) == -1
+    assert L.tfs_de_draw(1, None, 4, 8, 0.3, 1.5, None, None, None, None) == -1
+    assert L.tfs_de_draw(1, ctypes.cast(it, P), 4, 8, 0.3, 1.5, None, None, None, None) == -1  # null outputs
 
 
 def test_tuning_cache_round_trip(L, tmp_path):

@@ -1,6 +1,7 @@
 """The plunge-time search (Sec. II.D) on the GPU: chunk views and shifted bases evaluated in
 one batched launch against the oracle's chunk_eval; the differential-evolution kernels
-against numpy; the population driver against the oracle's statistic of its result."""
+against numpy and the device draws against the generator's host definition; the population
+driver against the oracle's statistic of its result."""
 import numpy as np
 import pytest
 
@@ -108,6 +109,31 @@ def test_de_kernels_against_numpy(T):
     acc = (ip.cpu().numpy() == 1) & (s_trial > s)
     assert np.array_equal(cd.cpu().numpy(), np.where(acc[:, None], want, c))
     assert np.array_equal(sd.cpu().numpy(), np.where(acc, s_trial, s))
+
+
+def test_de_draw_is_the_published_generator(T):
+    """tfs_de_draw against the host definition of the same SplitMix64 draws, bit for bit, over
+    three iterations (the device counter advances once per call), with a ragged chunk count."""
+    torch = pytest.importorskip("torch")
+    from tests.splitmix import de_draws
+
+    L = T.lib()
+    for n_ch, W, seed in ((5, 3, 1), (48, 512, 123456789123), (7, 1000, (1 << 63) - 25)):
+        n = n_ch * W
+        it = torch.zeros(1, dtype=torch.int32, device="cuda")
+        r1 = torch.empty(n, dtype=torch.int32, device="cuda")
+        r2 = torch.empty(n, dtype=torch.int32, device="cuda")
+        F = torch.empty(n, dtype=torch.float32, device="cuda")
+        for i in range(3):
+            T.check(L.tfs_de_draw(seed, it.data_ptr(), n_ch, W, 0.3, 1.5, r1.data_ptr(), r2.data_ptr(), F.data_ptr(),
+                                  None))
+            w1, w2, wF = de_draws(seed, i, n_ch, W, 0.3, 1.5)
+            assert np.array_equal(r1.cpu().numpy(), w1)
+            assert np.array_equal(r2.cpu().numpy(), w2)
+            assert np.array_equal(F.cpu().numpy().view(np.uint32), wF.view(np.uint32))
+        assert int(it.item()) == 3
+    with pytest.raises(T.TfsError):
+        T.check(L.tfs_de_draw(1, it.data_ptr(), 4, 2, 0.3, 1.5, r1.data_ptr(), r2.data_ptr(), F.data_ptr(), None))
 
 
 def test_de_driver_results_are_the_oracles(T):

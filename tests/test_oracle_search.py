@@ -73,3 +73,38 @@ def test_noise_moments_against_monte_carlo(window_kind):
     # the hand values at m = 0 and 1 (Hann): variance 4 and 19.333 per segment
     assert np.isclose(O.noise_moments(1, 0)[1] ** 2, 4.0)
     assert np.isclose(O.noise_moments(1, 1)[1] ** 2, 19.0 + 1.0 / 3.0)
+
+
+def test_splitmix64_published_values():
+    """The search's device draws come from SplitMix64; its host definition gives the published
+    outputs: seed 1234567 -> 6457827717110365317, 3203168211198807973, 9817491932198370423
+    (Rosetta Code, "Pseudo-random numbers/Splitmix64"), and seed 0 -> 0xE220A8397B1DCDAF,
+    0x6E789E6AA1B965F4, 0x06C45D188009454F."""
+    from tests.splitmix import splitmix64_at
+
+    got = [int(x) for x in splitmix64_at(1234567, np.arange(1, 4, dtype=np.uint64))]
+    assert got == [6457827717110365317, 3203168211198807973, 9817491932198370423]
+    got0 = [int(x) for x in splitmix64_at(0, np.arange(1, 4, dtype=np.uint64))]
+    assert got0 == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_de_draws_are_valid_partners():
+    """Every walker's partners are two distinct other walkers of its own chunk; the offsets are
+    uniform over the W - 1 others (chi-square over many draws); F lies in [0.3, 1.5)."""
+    from tests.splitmix import de_draws
+
+    n_ch, W = 6, 17
+    r1s, r2s = [], []
+    for it in range(400):
+        r1, r2, F = de_draws(99, it, n_ch, W, 0.3, 1.5)
+        g = np.arange(n_ch * W)
+        assert np.all(r1 // W == g // W) and np.all(r2 // W == g // W)
+        assert np.all(r1 != g) and np.all(r2 != g) and np.all(r1 != r2)
+        assert F.dtype == np.float32 and np.all(F >= np.float32(0.3)) and np.all(F < np.float32(1.5))
+        r1s.append((r1 - g) % W)
+        r2s.append((r2 - g) % W)
+    for off in (np.concatenate(r1s), np.concatenate(r2s)):
+        counts = np.bincount(off, minlength=W)[1:]
+        e = off.size / (W - 1)
+        chi2 = float(np.sum((counts - e) ** 2 / e))
+        assert counts.size == W - 1 and chi2 < 60.0   # 16 degrees of freedom: p ~ 1e-6 at 60
