@@ -639,7 +639,10 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
 #endif
   } else {
     // uploads on side stream 0, launches on `stream` as each chunk arrives, the per-track
-    // values read back on side stream 1 as each launch ends
+    // values read back on side stream 1 as each launch ends.  The read-backs are enqueued after
+    // every upload and launch: a copy into pageable memory returns only once it is done, and
+    // enqueued inside the loop it would hold back the next chunk's upload.
+    std::vector<cudaEvent_t> ran;
     for (int64_t t0 = 0; t0 < N; t0 += per) {
       const int64_t n = std::min(per, N - t0);
       TFS_CUDA(cudaMemcpyAsync(up_c + t0 * K, coeffs + t0 * K, (size_t)n * K * 8,
@@ -654,10 +657,17 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
       rc = launch_eval(Lc, EvalTuning(), st);
       if (rc) return rc;
       if (stat) {
-        rc = side.order(st, side.s[1]);
+        cudaEvent_t e;
+        rc = side.event(&e);
         if (rc) return rc;
-        TFS_CUDA(cudaMemcpyAsync(stat + t0, d_stat + t0, (size_t)n * 4, cudaMemcpyDeviceToHost, side.s[1]));
+        TFS_CUDA(cudaEventRecord(e, st));
+        ran.push_back(e);
       }
+    }
+    for (size_t c = 0; c < ran.size(); ++c) {
+      const int64_t t0 = (int64_t)c * per, n = std::min(per, N - t0);
+      TFS_CUDA(cudaStreamWaitEvent(side.s[1], ran[c], 0));
+      TFS_CUDA(cudaMemcpyAsync(stat + t0, d_stat + t0, (size_t)n * 4, cudaMemcpyDeviceToHost, side.s[1]));
     }
     rc = side.order(side.s[1], st);
     if (rc) return rc;
