@@ -52,9 +52,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
-    ap.add_argument("--stat-error", type=int, default=0,
-                    help="also report the statistic's error against the FP64 oracle on the exact table, "
-                         "over this many sampled tracks")
+    ap.add_argument("--stat-error", type=int, default=20000,
+                    help="report the statistic's error against the FP64 oracle on the exact table over this "
+                         "many sampled tracks, outside the timed region (0: skip)")
     ap.add_argument("--statistic", default="nearest", choices=["nearest", "chirp"],
                     help="plunge-time search: the nearest-bin statistic or the paper's linear-chirp statistic")
     ap.add_argument("--segment-cuts", action="store_true",
@@ -92,7 +92,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("eval_kernel.cuh", "tfs_internal.cuh"):
+    for f in ("eval_kernel.cuh", "eval_host.cu", "wsum.cu", "tfs_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2510_20891_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -164,6 +164,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- CPU oracle arm
 _W = {}
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
 def _oracle_init(P, V, T_sft, m, cuts=False):
@@ -190,9 +191,20 @@ class OracleArm:
 
         self.O, self.x, self.psd, self.w, self.V, self.ncores = O, x, psd, w, V, ncores
         P = O.power_table(x, w.dt, w.T_sft, psd)
-        self.pool = mp.get_context("spawn").Pool(ncores, initializer=_oracle_init,
-                                                 initargs=(P, V, w.T_sft, w.m, cuts))
-        self.pool.map(_oracle_chunk, [np.zeros((1, V.shape[0]))] * ncores)   # warm the workers
+        # one thread per worker process (numpy's BLAS would otherwise start a thread per core in
+        # each of them), so that `ncores` is the number of cores the oracle actually uses
+        saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+        os.environ.update({k: "1" for k in _THREAD_VARS})
+        try:
+            self.pool = mp.get_context("spawn").Pool(ncores, initializer=_oracle_init,
+                                                     initargs=(P, V, w.T_sft, w.m, cuts))
+            self.pool.map(_oracle_chunk, [np.zeros((1, V.shape[0]))] * ncores)   # warm the workers
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
 
     def step(self, coeffs):
         w = self.w
@@ -223,23 +235,24 @@ def run_reference(args):
     sample = min(args.cpu_sample, N)
     coeffs = synth.uniform_coeffs(sample, cmin, cmax, rng)
     arm = OracleArm(x, psd, w, V, ncores)
-    rates = []
+    steps_s = []
     for i in range(args.warmup + args.steps):
         t_sft, t_eval = arm.step(coeffs)
-        step_s = t_sft + N * (t_eval / sample)
         if i >= args.warmup:
-            rates.append(N / step_s)
+            steps_s.append(t_sft + t_eval)
     arm.close()
-    value = float(statistics.median(rates))
-    ms = 1e3 * N / value
+    # what was timed: one step is the FP64 SFT of the whole strain plus the statistic of `sample`
+    # tracks of the workload (not scaled up to the full batch)
+    step_s = float(statistics.median(steps_s))
+    value = sample / step_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "tracks_per_step": N, "n_seg": w.n_seg, "n_bin": w.n_bin,
+            "config": {"workload": args.workload, "tracks_per_step": sample, "n_seg": w.n_seg, "n_bin": w.n_bin,
                        "K": w.K, "m": w.m, "topk": args.topk},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                             "sample": f"per step: FP64 SFT of the full strain + statistic of {sample} tracks "
-                                       f"on {ncores} processes, scaled to {N} tracks"},
+                             "sample": f"per step: FP64 SFT of the full strain + statistic of {sample} of the "
+                                       f"workload's tracks on {ncores} single-threaded processes"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -346,6 +359,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     x_pin = torch.from_numpy(x).pin_memory()
     c_pin = torch.from_numpy(coeffs_h).pin_memory()
+    s_pin = torch.empty(N, dtype=torch.float32).pin_memory()   # statistic[N] comes back every step
     e_top_i = np.empty(kk, np.int64)
     e_top_v = np.empty(kk, np.float32)
 
@@ -362,13 +376,14 @@ def run_ours(args):
     def e2e_step():
         T.check(L.tfs_table_rebuild(table.handle, x_pin.data_ptr(), x_pin.numel(), 0, e2e_sp))
         if cut_job is None:
-            T.check(L.tfs_eval_stat(table.handle, basis.handle, c_pin.data_ptr(), None, N, w.m, kk, None,
-                                    e_top_i.ctypes.data, e_top_v.ctypes.data, None, 0, e2e_sp))
+            T.check(L.tfs_eval_stat(table.handle, basis.handle, c_pin.data_ptr(), None, N, w.m, kk,
+                                    s_pin.data_ptr(), e_top_i.ctypes.data, e_top_v.ctypes.data, None, 0, e2e_sp))
         else:
             # host coefficients uploaded on the stream, the batched entry point, top-k read back
             with torch.cuda.stream(e2e_stream):
                 c_e2e.copy_(c_pin, non_blocking=True)
                 T.eval_batch([e2e_job], stream=e2e_stream.cuda_stream)
+                s_pin.copy_(stat, non_blocking=True)
                 e_top_i[:] = e2e_job.top_idx.cpu().numpy()
                 e_top_v[:] = e2e_job.top_val.cpu().numpy()
 
@@ -384,17 +399,25 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     h2d = x.nbytes + coeffs_h.nbytes
-    d2h = kk * 12
+    d2h = N * 4 + kk * 12
 
     # roofline of the dominant kernel (the fused statistic kernel)
     esize = {"f32": 4, "bf16": 2, "f16": 2, "f8e4m3": 1}[args.dtype]
     bytes_per_track = w.n_seg * (2 * w.m + 1) * esize + w.K * 8 + 4
     achieved = N * bytes_per_track / (eval_ms / 1e3) / 1e9
-    peak, peak_kind = measured_peaks()
+    hbm_peak, peak_kind = measured_peaks()
     traffic = profiled_traffic(args.workload, args.dtype)
-    # the table fits in L2: the L2 read bandwidth, measured live, is the other applicable roofline
+    # L2 read bandwidth, measured in this run (MEASURED_PEAKS.json has no L2 figure)
     l2_gbs = ctypes.c_double()
     T.check(L.tfs_measure_l2_read(48 << 20, 40, ctypes.byref(l2_gbs)))
+    # the kernel gathers from the table's FP32 window sums; when they and the table fit in half of
+    # the 126 MB L2 (the rest holds the streamed coefficients), the applicable bound is L2, else HBM
+    pad32 = lambda n: (n + 31) // 32 * 32  # noqa: E731
+    resident = w.n_seg * (pad32(w.n_bin + 2 * w.m) * 4 + pad32(w.n_bin) * esize)
+    bound = "l2" if resident <= 63e6 else "hbm"
+    peak = l2_gbs.value if bound == "l2" else hbm_peak
+    peak_source = ("tfs_measure_l2_read in this run: 16-byte L1-bypassing loads over a 48 MB buffer, 40 passes"
+                   if bound == "l2" else f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -436,12 +459,12 @@ def run_ours(args):
                              "from L2 within a step" % (coeffs_h.nbytes / 1e6),
                        "parallelism": f"tracks sharded over {world} GPU(s)"},
             "breakdown_ms": {"sft_rebuild": sft_ms, "eval_stat": eval_ms, "topk": topk_ms},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": f"{peak_kind} hbm_gbs",
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_source,
                          "bytes_per_track": bytes_per_track, "kernel": "eval_stat_kernel",
-                         "l2_peak_gbs": l2_gbs.value, "frac_of_l2": achieved / l2_gbs.value,
-                         "l2_peak_source": "tfs_measure_l2_read, 48 MB buffer x 40 reads, this run"},
+                         "resident_bytes": resident,
+                         "hbm_peak_gbs": hbm_peak, "frac_of_hbm": achieved / hbm_peak,
+                         "l2_peak_gbs": l2_gbs.value, "frac_of_l2": achieved / l2_gbs.value},
             "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
@@ -614,7 +637,7 @@ def run_tpl_search(args):
     if not args.no_autotune and not chirp:
         # launch shape for one iteration's batch (48 chunk jobs of 512 walkers, with the cuts)
         tune_c = [torch.tensor(cmin + (cmax - cmin) * rng.random((W, w.K)), device="cuda") for _ in cs.sizes]
-        shape, _ = T.autotune(cs.jobs(tune_c, m=w.m, segment_cuts=True), reps=3)
+        shape, _, _ = T.autotune(cs.jobs(tune_c, m=w.m, segment_cuts=True), reps=3)
     # warm-up: a short search builds the cached per-chunk data and the graph machinery
     search.DESearch(cs, cmin, cmax, m=w.m, seed=1, segment_cuts=True,
                     statistic=args.statistic).run(n_iter=max(1, args.warmup), U_full=U)
@@ -751,7 +774,7 @@ def run_batched(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_default = e0.elapsed_time(e1) / 3
-        tuned, _ = T.autotune(jobs, reps=3)   # untimed: picks the launch shape used below
+        tuned, _, _ = T.autotune(jobs, reps=3)   # untimed: picks the launch shape used below
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(stream)

@@ -125,7 +125,11 @@ int tfs_table_info(const tfs_table* t, int64_t* n_seg, int64_t* n_bin, int* dtyp
  * (FP8: q * s_alpha in FP32, widened) and, for FP8, the scales [n_seg] (may be NULL). */
 int tfs_table_to_host(const tfs_table* t, double* P, float* scales);
 
-/* Device bytes held by the table. */
+/* Device bytes held by the table: its stored values plus the window sums kept
+ * for the neighbour half-widths m it has been evaluated with (the statistic
+ * reads W_m[alpha][c] = sum_{|j|<=m} P[alpha][c+j], FP32, one row of n_bin + 2m
+ * centres rounded up to 32 per segment, built on the first evaluation with that
+ * m, recomputed with the table by tfs_table_rebuild and released with it). */
 int64_t tfs_table_bytes(const tfs_table* t);
 
 int tfs_table_free(tfs_table* t);
@@ -239,22 +243,33 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
 
 /* ---- launch-shape autotuning ---------------------------------------------
  * Not part of the paper's method: it picks how the statistic kernel is laid
- * out for a kind of workload.  pcap is the number of table elements of one
- * segment's band staged per tile (wide bands beyond it take a slower path),
- * tile_div (1, 2, 4 or 8) divides the tracks per tile (smaller tiles: more of
- * them, better balance for small jobs).  tfs_autotune_batch evaluates `jobs` (as
- * tfs_eval_batch, overwriting their outputs) under every candidate shape,
- * `reps` times each, and keeps the fastest for every launch of this kind
- * (table dtype, coefficient slots, widest row and longest job in powers of
- * two, single job or batch); later tfs_eval_stat / tfs_eval_batch calls of
- * that kind use it.  Synchronous.  The choices live in the process; save and
- * load them as a small JSON object {"key": [pcap, tile_div], ...}. */
+ * out for a kind of workload, along four axes.  group (1..32) is the largest
+ * number of consecutive segments one staging slot carries (a slot never
+ * crosses a multiple of 32 segments), i.e. how many segments the consumers
+ * take per hand-off; slots (2..8) is the depth of the staging ring;
+ * pcap is the number of window sums of one segment's band staged per tile
+ * (wider bands are cut to it and their pairs outside it take the slower exact
+ * path); tile_div (1, 2, 4 or 8) divides the tracks per tile (smaller tiles:
+ * more of them, better balance for small jobs).  Zeros select the defaults
+ * (group 32, slots 2, pcap 2048, tile_div 1).  tfs_autotune_batch evaluates
+ * `jobs` (as tfs_eval_batch, overwriting their outputs) under candidate shapes,
+ * `reps` times each, by coordinate descent from the default shape (each axis
+ * in turn, two passes, a move must gain 0.5%), and keeps the fastest for every
+ * launch of this kind (coefficient slots, widest row and longest job in powers
+ * of two, single job or batch); later tfs_eval_stat / tfs_eval_batch calls of
+ * that kind use it.  best_ms and default_ms (either may be NULL) receive the
+ * time per call of the chosen and of the default shape.  Synchronous.  The
+ * choices live in the process; save and load them as a small JSON object
+ * {"key": [pcap, tile_div, slots, group], ...}. */
 typedef struct tfs_tuning {
   int32_t pcap;
   int32_t tile_div;
+  int32_t slots;
+  int32_t group;
 } tfs_tuning;
 
-int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms, void* stream);
+int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms,
+                       double* default_ms, void* stream);
 int tfs_tuning_save(const char* path);
 int tfs_tuning_load(const char* path);
 int tfs_tuning_clear(void);
@@ -445,11 +460,23 @@ int tfs_measure_l2_read(int64_t buffer_bytes, int reps, double* gbs);
 /* Number of kernels this library has launched in this process (all devices). */
 long long tfs_kernel_launches(void);
 
+/* Failure-detection control (not part of the paper's method).  Every wait of
+ * the statistic kernel on one of its pipeline barriers gives up after
+ * limit_ns nanoseconds (limit_ns <= 0 restores the default, 2 s); the kernel
+ * then leaves its loops, lets every copy still in flight land and reports a
+ * timeout, so that the call returns TFS_ERR_TIMEOUT (or sets dev_status) and
+ * the context stays usable.  hold = 1 makes the kernel's staging warp first
+ * wait for a signal that nothing sends, so that the next statistic launches
+ * time out after limit_ns: a deterministic way for tests to exercise that
+ * path without a fault.  hold = 0 is normal operation.  Process-wide; read
+ * when a launch is enqueued. */
+int tfs_set_wait_limit(int64_t limit_ns, int hold);
+
 /* ---- step 5 alone: top-k of a float array ---------------------------------
  * k in [1, 1024], 1 <= N < 2^31.  Writes min(k, N) entries of idx (int64) and
  * val in descending order of val; equal values keep the lower index first,
  * -0.0 equals +0.0, NaN ranks below every number.  Device scratch (about
- * 8 KB plus 16 bytes per 2048 elements) is allocated stream-ordered per call. */
+ * 8 KB plus 4 bytes per 4096 elements) is allocated stream-ordered per call. */
 int tfs_topk(const float* val_in, int64_t N, int k, int64_t* idx, float* val, int mem, void* stream);
 
 /* ---- top-k that allocates nothing -----------------------------------------

@@ -11,7 +11,7 @@ marshals arguments.  Functions keep the C names without the ``tfs_`` prefix:
 * ``eval_batch([Job(table, basis, coeffs, ...), ...], dev_status=None)`` -> the jobs, outputs filled
 * ``Server(budget_bytes)``: ``add_dataset(table, basis)``, ``submit(ds, coeffs, ...)`` -> ticket,
   ``wait(ticket)`` -> (stat, top_idx, top_val), ``stats()``
-* ``autotune(jobs)`` -> (launch shape, ms); ``tuning_save(path)`` / ``tuning_load(path)``
+* ``autotune(jobs)`` -> (launch shape, ms, default ms); ``tuning_save(path)`` / ``tuning_load(path)``
 * ``topk(values, k)`` -> (idx, val)
 
 Array arguments are numpy arrays (host memory: the call copies in and out
@@ -438,14 +438,23 @@ def _job_array(jobs):
 
 
 def autotune(jobs, reps: int = 3, stream=None):
-    """Time every candidate launch shape on `jobs` and keep the fastest for launches of
-    this kind (tfs_autotune_batch); returns ({"pcap": .., "tile_div": ..}, ms per batch)."""
+    """Choose the statistic kernel's launch shape for `jobs` by coordinate descent over its four
+    axes and keep it for launches of this kind (tfs_autotune_batch); returns
+    ({"pcap": .., "tile_div": .., "slots": .., "group": ..}, ms per batch, ms per batch with the
+    default shape)."""
     arr = _job_array(jobs)
     best = _lib.TfsTuning()
     ms = ctypes.c_double()
+    ms0 = ctypes.c_double()
     check(lib().tfs_autotune_batch(arr, len(jobs), int(reps), ctypes.byref(best), ctypes.byref(ms),
-                                   _stream_ptr(stream)))
-    return {"pcap": best.pcap, "tile_div": best.tile_div}, ms.value
+                                   ctypes.byref(ms0), _stream_ptr(stream)))
+    return {"pcap": best.pcap, "tile_div": best.tile_div, "slots": best.slots, "group": best.group}, ms.value, ms0.value
+
+
+def set_wait_limit(limit_ns: int = 0, hold: bool = False):
+    """Limit of the statistic kernel's device waits (0: the default 2 s); hold=True makes its next
+    launches time out deterministically (tfs_set_wait_limit; for failure-detection tests)."""
+    check(lib().tfs_set_wait_limit(int(limit_ns), 1 if hold else 0))
 
 
 def tuning_save(path: str):

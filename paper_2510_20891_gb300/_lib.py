@@ -36,7 +36,8 @@ SIGNATURES = {
     "tfs_kernel_launches": (ctypes.c_longlong, []),
     "tfs_topk_noalloc": (I, [P, I64, I, P, P, P]),
     "tfs_eval_batch": (I, [P, I, P, P]),
-    "tfs_autotune_batch": (I, [P, I, I, P, P, P]),
+    "tfs_autotune_batch": (I, [P, I, I, P, P, P, P]),
+    "tfs_set_wait_limit": (I, [I64, I]),
     "tfs_tuning_save": (I, [ctypes.c_char_p]),
     "tfs_tuning_load": (I, [ctypes.c_char_p]),
     "tfs_tuning_clear": (I, []),
@@ -67,7 +68,8 @@ SIGNATURES = {
 class TfsTuning(ctypes.Structure):
     """struct tfs_tuning (include/tfstat.h)."""
 
-    _fields_ = [("pcap", ctypes.c_int32), ("tile_div", ctypes.c_int32)]
+    _fields_ = [("pcap", ctypes.c_int32), ("tile_div", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("group", ctypes.c_int32)]
 
 
 class TfsServerStats(ctypes.Structure):

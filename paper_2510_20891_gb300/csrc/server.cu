@@ -40,7 +40,9 @@ struct SrvDataset {
   bool resident = true;
   int pins = 0;                      // admitted or running requests using the table
   int64_t last_use = 0;
-  int64_t dev_bytes() const { return (int64_t)(data_bytes + scale_bytes); }
+  std::vector<int> wsum_m;           // m values whose window sums are counted in the budget
+  int64_t wsum_bytes = 0;            // their bytes (built with the first launch that needs them)
+  int64_t dev_bytes() const { return (int64_t)(data_bytes + scale_bytes) + wsum_bytes; }
 };
 
 enum ReqState { kQueued, kRunning, kDone, kFailed };
@@ -48,6 +50,7 @@ enum ReqState { kQueued, kRunning, kDone, kFailed };
 struct SrvReq {
   int64_t ticket = 0;
   int ds = 0;
+  SrvDataset* dsp = nullptr;       // the dataset (stable: datasets are never moved or freed before the server)
   int64_t N = 0;
   int m = 0, topk = 0, K = 0;
   const double* coeffs = nullptr;  // caller's host memory, read at admission
@@ -123,6 +126,7 @@ int evict(SrvDataset* d) {
       TFS_CUDA(cudaMemcpy(d->host_scales.data(), t->scales, d->scale_bytes, cudaMemcpyDeviceToHost));
     }
   }
+  wsum_free(t);
   TFS_CUDA(cudaFree(t->data));
   t->data = nullptr;
   if (t->scales) {
@@ -156,8 +160,11 @@ bool make_room(tfs_server* s, int64_t need, int keep) {
       if (!victim || d->last_use < victim->last_use) victim = d;
     }
     if (!victim) return false;
+    const int64_t freed = victim->dev_bytes();
     if (evict(victim) != TFS_OK) return false;
-    s->used -= victim->dev_bytes();
+    s->used -= freed;
+    victim->wsum_m.clear();
+    victim->wsum_bytes = 0;
     ++s->evictions;
   }
   return true;
@@ -178,7 +185,7 @@ void finish_batch(tfs_server* s, SrvBatch& b) {
     } else {
       r->state = kDone;
     }
-    s->ds[r->ds]->pins -= 1;
+    r->dsp->pins -= 1;
   }
   b.reqs.clear();
   b.busy = false;
@@ -189,8 +196,11 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
   std::vector<SrvReq*> adm;
   while (!s->queue.empty() && (int)adm.size() < s->max_jobs) {
     SrvReq* r = s->queue.front();
-    SrvDataset* d = s->ds[r->ds];
-    const int64_t need = (int64_t)r->dev_bytes + (d->resident ? 0 : d->dev_bytes());
+    SrvDataset* d = r->dsp;
+    // the request's buffers, its table if evicted, and the table's window sums for this m if new
+    const bool new_w = std::find(d->wsum_m.begin(), d->wsum_m.end(), r->m) == d->wsum_m.end();
+    const int64_t w_bytes = new_w ? wsum_bytes(d->table, r->m) : 0;
+    const int64_t need = (int64_t)r->dev_bytes + (d->resident ? 0 : d->dev_bytes()) + w_bytes;
     if (s->used + need > s->budget && !make_room(s, need, r->ds)) break;
     if (!d->resident) {
       const int rc = reload(d, b.st);
@@ -215,6 +225,11 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
       continue;
     }
     s->used += (int64_t)r->dev_bytes;
+    if (new_w) {
+      d->wsum_m.push_back(r->m);
+      d->wsum_bytes += w_bytes;
+      s->used += w_bytes;
+    }
     d->pins += 1;
     d->last_use = ++s->use_clock;
     char* p = static_cast<char*>(r->dev);
@@ -252,8 +267,8 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
     if (e != cudaSuccess) rc = cuda_fail(e, "request upload");
     tfs_job& j = jobs[i];
     std::memset(&j, 0, sizeof(j));
-    j.table = s->ds[r->ds]->table;
-    j.basis = s->ds[r->ds]->basis;
+    j.table = r->dsp->table;
+    j.basis = r->dsp->basis;
     j.coeffs = r->d_c;
     j.f_ref = r->d_f;
     j.N = r->N;
@@ -277,7 +292,7 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
       r->state = kFailed;
       r->rc = rc;
       r->err = msg;
-      s->ds[r->ds]->pins -= 1;
+      r->dsp->pins -= 1;
     }
     b.reqs.clear();
     b.busy = false;
@@ -354,6 +369,7 @@ int tfs_server_add_dataset(tfs_server* s, tfs_table* table, const tfs_basis* bas
   TFS_CHECK(table->data, TFS_ERR_INVALID_ARG, "table has no device data");
   TFS_CHECK(table->owns, TFS_ERR_INVALID_ARG, "a table view cannot be handed to a server");
   std::lock_guard<std::mutex> lk(s->mu);
+  wsum_free(table);  // window sums come back within the budget, as launches need them
   SrvDataset* d = new SrvDataset();
   d->table = table;
   d->basis = basis;
@@ -380,6 +396,7 @@ int tfs_server_submit(tfs_server* s, int ds_id, const double* coeffs, const doub
   SrvDataset* d = s->ds[ds_id];
   SrvReq* r = new SrvReq();
   r->ds = ds_id;
+  r->dsp = d;
   r->N = N;
   r->m = m;
   r->topk = (int)std::min<int64_t>(topk, N);
@@ -389,10 +406,12 @@ int tfs_server_submit(tfs_server* s, int ds_id, const double* coeffs, const doub
   r->dev_bytes = r256((size_t)N * r->K * 8) + (f_ref ? r256((size_t)N * 8) : 0) + r256((size_t)N * 4) +
                  (r->topk ? r256((size_t)r->topk * 8) + r256((size_t)r->topk * 4) : 0) +
                  (r->topk ? r256(topk_workspace_bytes(N)) : 0) + 4096;
-  if ((int64_t)r->dev_bytes + d->dev_bytes() > s->budget) {
+  const int64_t with_table = (int64_t)r->dev_bytes + (int64_t)(d->data_bytes + d->scale_bytes) +
+                             wsum_bytes(d->table, m);
+  if (with_table > s->budget) {
     delete r;
-    set_error("request needs %lld bytes with its table, over the %lld-byte budget",
-              (long long)(r->dev_bytes + d->dev_bytes()), (long long)s->budget);
+    set_error("request needs %lld bytes with its table and window sums, over the %lld-byte budget",
+              (long long)with_table, (long long)s->budget);
     return TFS_ERR_OOM;
   }
   r->ticket = s->next_ticket++;

@@ -728,6 +728,7 @@ extern "C" int tfs_table_rebuild(tfs_table* t, const double* strain, int64_t n, 
     d_x = tmp;
   }
   int rc = run_sft(p, d_x, t, st);
+  if (rc == TFS_OK) rc = wsum_refresh(t, st);  // window sums kept with the table follow its new values
   if (tmp) cudaFreeAsync(tmp, st);
   if (copied) {
     // the caller may reuse the host strain once it has been copied; the transform keeps

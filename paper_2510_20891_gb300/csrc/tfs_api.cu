@@ -264,22 +264,17 @@ int launch_eval(const EvalLaunch& L, const EvalTuning& tune_in, cudaStream_t st)
   if (g_force_tuning) {
     tune = *g_force_tuning;
     g_last_keys.push_back(key);
-  } else if (tune.cap == 0 && tune.tile_div == 0) {
+  } else if (tune.cap == 0 && tune.tile_div == 0 && tune.slots == 0 && tune.group == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       tune.cap = it->second.pcap;
       tune.tile_div = it->second.tile_div;
+      tune.slots = it->second.slots;
+      tune.group = it->second.group;
     }
   }
-  switch (L.jobs[0].table->dtype) {
-    case TFS_F32: return launch_eval_f32(L, tune, st);
-    case TFS_BF16: return launch_eval_bf16(L, tune, st);
-    case TFS_F16: return launch_eval_f16(L, tune, st);
-    case TFS_F8E4M3: return launch_eval_f8(L, tune, st);
-  }
-  set_error("bad table dtype");
-  return TFS_ERR_INVALID_ARG;
+  return launch_eval_shape(L, tune, st);
 }
 
 // Stream-ordered scratch comes from the device's default memory pool, which by default
@@ -328,7 +323,6 @@ struct Arena {
 
 static size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-long long eval_round_tracks(int KP, bool cuts, int tile_div);  // beside the F32 instantiation
 
 // Host inputs of tfs_eval_stat are uploaded in chunks on a side stream, each chunk
 // evaluated by its own launch as soon as it has arrived, so that the upload of chunk c+1
@@ -418,7 +412,14 @@ int tfs_table_info(const tfs_table* t, int64_t* n_seg, int64_t* n_bin, int* dtyp
   return TFS_OK;
 }
 
-int64_t tfs_table_bytes(const tfs_table* t) { return t ? t->bytes : 0; }
+int64_t tfs_table_bytes(const tfs_table* t) { return t ? t->bytes + (t->owns ? wsum_cached_bytes(t) : 0) : 0; }
+
+int tfs_set_wait_limit(int64_t limit_ns, int hold) {
+  clear_error();
+  TFS_CHECK(hold == 0 || hold == 1, TFS_ERR_INVALID_ARG, "hold must be 0 or 1");
+  set_eval_wait(limit_ns > 0 ? (uint64_t)limit_ns : 2000000000ull, hold);
+  return TFS_OK;
+}
 
 long long tfs_kernel_launches(void) { return tfs::g_launches.load(); }
 
@@ -433,6 +434,7 @@ int tfs_table_free(tfs_table* t) {
   if (!t) return TFS_OK;
   if (t->sft_plan) free_sft_plan(t->sft_plan);
   if (t->owns) {
+    wsum_free(t);
     if (t->data) cudaFree(t->data);
     if (t->scales) cudaFree(t->scales);
   }
@@ -459,6 +461,8 @@ int tfs_table_view(const tfs_table* t, int64_t seg0, int64_t n_seg, tfs_table** 
   v->scales = t->scales ? t->scales + seg0 : nullptr;
   v->bytes = 0;
   v->owns = false;
+  v->owner = t->owner ? t->owner : t;
+  v->seg0 = (t->owner ? t->seg0 : 0) + seg0;
   *out = v;
   return TFS_OK;
 }
@@ -636,6 +640,8 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
     TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
     TFS_CUDA(cudaStreamSynchronize(st));
     cudaFreeAsync(d_dbg, st);
+    TFS_CHECK(g_dbg_last[0] == 0, TFS_ERR_CUDA, "debug self-check failed %llu times, first at site %llu (%lld, %lld)",
+              g_dbg_last[0], g_dbg_last[1], (long long)g_dbg_last[2], (long long)g_dbg_last[3]);
 #endif
   } else {
     // uploads on side stream 0, launches on `stream` as each chunk arrives, the per-track
@@ -841,9 +847,18 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
     }
   }
 #ifdef TFS_DEBUG_CHECKS
-  TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
-  TFS_CUDA(cudaStreamSynchronize(st));
-  cudaFreeAsync(d_dbg, st);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TFS_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) {
+    cudaFreeAsync(d_dbg, st);  // inside a capture the self-check record cannot be read back
+    g_dbg_last[0] = 0;
+  } else {
+    TFS_CUDA(cudaMemcpyAsync(g_dbg_last, d_dbg, 32, cudaMemcpyDeviceToHost, st));
+    TFS_CUDA(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_dbg, st);
+  }
+  TFS_CHECK(g_dbg_last[0] == 0, TFS_ERR_CUDA, "debug self-check failed %llu times, first at site %llu (%lld, %lld)",
+            g_dbg_last[0], g_dbg_last[1], (long long)g_dbg_last[2], (long long)g_dbg_last[3]);
 #endif
   // top-k per job, one after another on the stream (they share the scratch)
   for (int i = 0; i < n_jobs; ++i) {
@@ -861,7 +876,8 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
   return TFS_OK;
 }
 
-int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms, void* stream) {
+int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms,
+                       double* default_ms, void* stream) {
   clear_error();
   TFS_CHECK(best && reps >= 1 && reps <= 100, TFS_ERR_INVALID_ARG, "need best and 1 <= reps <= 100");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -870,60 +886,86 @@ int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* be
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // validation, per-segment data and a warm start with the current choice
+  // validation, per-segment data and window sums, and a warm start with the current choice
   int rc = tfs_eval_batch(jobs, n_jobs, d_status, stream);
   if (rc == TFS_OK) {
     const cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "autotune warm-up");
   }
-  double best_t = 1e300;
-  tfs_tuning win{0, 0};
+  // time one launch shape on the caller's jobs (ms per call; < 0 if it does not fit)
   std::vector<std::string> keys;
-  const int caps[] = {512, 1024, 2048, 3072, 4096};
-  const int divs[] = {1, 2, 4, 8};
-  for (int ci = 0; ci < 5 && rc == TFS_OK; ++ci) {
-    for (int di = 0; di < 4 && rc == TFS_OK; ++di) {
-      EvalTuning t;
-      t.cap = caps[ci];
-      t.tile_div = divs[di];
-      g_force_tuning = &t;
-      g_last_keys.clear();
-      int r = tfs_eval_batch(jobs, n_jobs, d_status, stream);  // shape check (shared memory), warm
-      if (r == TFS_OK) {
-        cudaEventRecord(e0, st);
-        for (int k = 0; k < reps && r == TFS_OK; ++k) r = tfs_eval_batch(jobs, n_jobs, d_status, stream);
-        cudaEventRecord(e1, st);
-      }
-      g_force_tuning = nullptr;
-      if (r != TFS_OK) {
-        clear_error();
-        continue;  // this shape does not fit (e.g. shared memory): skip it
-      }
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = cuda_fail(cudaGetLastError(), "autotune timing");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double per = (double)ms / reps;
-      if (per < best_t) {
-        best_t = per;
-        win = tfs_tuning{t.cap, t.tile_div};
-        keys = g_last_keys;
+  auto time_shape = [&](const EvalTuning& t, std::vector<std::string>* k_out) -> double {
+    g_force_tuning = &t;
+    g_last_keys.clear();
+    int r = tfs_eval_batch(jobs, n_jobs, d_status, stream);  // shape check (shared memory), warm
+    if (r == TFS_OK) {
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps && r == TFS_OK; ++k) r = tfs_eval_batch(jobs, n_jobs, d_status, stream);
+      cudaEventRecord(e1, st);
+    }
+    g_force_tuning = nullptr;
+    if (r != TFS_OK) {
+      clear_error();
+      return -1.0;  // this shape does not fit (e.g. shared memory): skip it
+    }
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "autotune timing");
+      return -1.0;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (k_out) *k_out = g_last_keys;
+    return (double)ms / reps;
+  };
+  // coordinate descent over the four axes from the default shape, two passes; a move must gain
+  // at least 0.5% so that timing noise does not wander
+  EvalTuning cur;
+  cur.cap = 2048;
+  cur.tile_div = 1;
+  cur.slots = 2;
+  cur.group = 32;
+  double cur_t = rc == TFS_OK ? time_shape(cur, &keys) : -1.0;
+  const double def_t = cur_t;
+  if (rc == TFS_OK && cur_t < 0) rc = TFS_ERR_INVALID_ARG;
+  static const int groups[] = {1, 4, 8, 16, 32};
+  static const int slots[] = {2, 3, 4, 6, 8};
+  static const int caps[] = {512, 1024, 2048, 3072, 4096};
+  static const int divs[] = {1, 2, 4, 8};
+  for (int pass = 0; pass < 2 && rc == TFS_OK; ++pass) {
+    bool moved = false;
+    for (int axis = 0; axis < 4 && rc == TFS_OK; ++axis) {
+      const int* vals = axis == 0 ? groups : axis == 1 ? slots : axis == 2 ? caps : divs;
+      const int nv = axis == 3 ? 4 : 5;
+      for (int i = 0; i < nv && rc == TFS_OK; ++i) {
+        EvalTuning t = cur;
+        int& f = axis == 0 ? t.group : axis == 1 ? t.slots : axis == 2 ? t.cap : t.tile_div;
+        if (f == vals[i]) continue;
+        f = vals[i];
+        std::vector<std::string> k2;
+        const double tt = time_shape(t, &k2);
+        if (tt > 0 && tt < cur_t * 0.995) {
+          cur = t;
+          cur_t = tt;
+          keys = k2;
+          moved = true;
+        }
       }
     }
+    if (!moved) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(d_status);
+  if (rc == TFS_ERR_INVALID_ARG) set_error("the default launch shape does not fit these jobs");
   if (rc != TFS_OK) return rc;
-  TFS_CHECK(best_t < 1e300, TFS_ERR_INVALID_ARG, "no launch shape fits these jobs");
+  const tfs_tuning win{cur.cap, cur.tile_div, cur.slots, cur.group};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const std::string& k : keys) g_tune[k] = win;
   }
   *best = win;
-  if (best_ms) *best_ms = best_t;
+  if (best_ms) *best_ms = cur_t;
+  if (default_ms) *default_ms = def_t;
   return TFS_OK;
 }
 
@@ -936,8 +978,8 @@ int tfs_tuning_save(const char* path) {
   fprintf(f, "{\n");
   size_t i = 0;
   for (const auto& kv : g_tune)
-    fprintf(f, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.pcap, kv.second.tile_div,
-            ++i < g_tune.size() ? "," : "");
+    fprintf(f, "  \"%s\": [%d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second.pcap, kv.second.tile_div,
+            kv.second.slots, kv.second.group, ++i < g_tune.size() ? "," : "");
   fprintf(f, "}\n");
   fclose(f);
   return TFS_OK;
@@ -959,14 +1001,15 @@ int tfs_tuning_load(const char* path) {
     const size_t end = txt.find('"', pos + 1);
     if (end == std::string::npos) break;
     const std::string key = txt.substr(pos + 1, end - pos - 1);
-    int cap = 0, div = 0;
-    if (sscanf(txt.c_str() + end + 1, " : [%d , %d]", &cap, &div) != 2 || cap < 0 || cap > (1 << 20) || div < 0 ||
-        div > 8) {
+    int cap = 0, div = 0, ns = 0, grp = 0;
+    const int got_n = sscanf(txt.c_str() + end + 1, " : [%d , %d , %d , %d]", &cap, &div, &ns, &grp);
+    if (got_n != 4 || cap < 0 || cap > (1 << 20) || div < 0 || div > 8 || ns < 0 || ns > 8 || grp < 0 || grp > 32) {
       set_error("malformed tuning entry for %s", key.c_str());
       return TFS_ERR_INVALID_ARG;
     }
-    got[key] = tfs_tuning{cap, div};
-    pos = end + 1;
+    got[key] = tfs_tuning{cap, div, ns, grp};
+    pos = txt.find(']', end);
+    if (pos == std::string::npos) break;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (const auto& kv : got) g_tune[kv.first] = kv.second;

@@ -71,6 +71,15 @@ struct SegParams {          // per (basis, T_sft) data for the FP32 filter of th
   float* gmax = nullptr;    // device [KP]: max_alpha |G_k,alpha| (rounded up), cuts only
 };
 
+// Window sums of a table for one neighbour half-width m (see wsum.cu): [n_seg][pitch] FP32,
+// centre c at index c + m; zeros past the last centre whose window overlaps the table.
+struct WSum {
+  int m = 0;
+  int64_t pitch = 0;
+  int64_t bytes = 0;
+  float* q = nullptr;
+};
+
 }  // namespace tfs
 
 struct tfs_table {
@@ -84,6 +93,10 @@ struct tfs_table {
   double dt = 0.0;
   void* sft_plan = nullptr; // cached SFT plan (window, twiddles, PSD normalisation) when built from strain
   bool owns = true;         // false for a view: data and scales belong to another table
+  const tfs_table* owner = nullptr;  // a view: the table that owns the rows (and their window sums)
+  int64_t seg0 = 0;         // a view: its first row in the owner
+  mutable std::mutex wmu;   // guards wsums
+  mutable std::vector<tfs::WSum> wsums;  // window sums per m used so far (owning tables only)
 };
 
 struct tfs_ctable {          // linear-chirp table: scaled complex spectra of a Hann-windowed strain
@@ -109,7 +122,19 @@ struct tfs_basis {
 
 namespace tfs {
 
-inline int esize_of(int dtype) { return dtype == TFS_F32 ? 4 : (dtype == TFS_F8E4M3 ? 1 : 2); }
+__host__ __device__ constexpr int esize_of(int dtype) { return dtype == TFS_F32 ? 4 : (dtype == TFS_F8E4M3 ? 1 : 2); }
+
+// Window sums (wsum.cu).  wsum_get returns the rows of t's window sums for m (built on first
+// use, then kept with the owning table; the first build synchronises `st`, so it must not be
+// inside a stream capture); wsum_refresh recomputes every kept m on `st` after the table's
+// data changed; wsum_free releases them.
+int64_t wsum_pitch(int64_t n_bin, int m);
+int64_t wsum_bytes(const tfs_table* t, int m);
+int64_t wsum_cached_bytes(const tfs_table* t);
+bool wsum_cached(const tfs_table* t, int m);
+int wsum_get(const tfs_table* t, int m, cudaStream_t st, const float** q, int* pitch);
+int wsum_refresh(tfs_table* t, cudaStream_t st);
+void wsum_free(tfs_table* t);
 
 // Cached FP32 filter parameters of a basis for a given T_sft, with at least kp_min coefficient
 // slots (built on first use; rebuilt for another T_sft or a wider slot count).
@@ -140,20 +165,22 @@ struct EvalLaunch {
   unsigned long long* dbg = nullptr;  // self-check record (TFS_DEBUG_CHECKS builds)
 };
 struct EvalTuning {       // launch shape; zeros select defaults
-  int threads = 0;
-  int stages = 0;
-  int cap = 0;            // staged band capacity per row (elements)
-  int qcap = 0;
+  int cap = 0;            // window sums staged per segment at most (a band cut to it takes the slower path)
   int tile_div = 0;       // tiles of (consumer threads x R) / tile_div tracks at most
+  int slots = 0;          // staging slots (ring depth)
+  int group = 0;          // segments per staging slot at most (one hand-off per slot)
 };
 constexpr int kMaxJobs = 64;  // jobs per statistic launch (larger batches are split)
 int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st);
-
-// dtype-specific launchers (one translation unit each)
-int launch_eval_f32(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
-int launch_eval_bf16(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
-int launch_eval_f16(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
-int launch_eval_f8(const EvalLaunch& L, const EvalTuning& t, cudaStream_t st);
+// the statistic kernel for a shape already chosen (eval_host.cu)
+int launch_eval_shape(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st);
+// tracks that one round of full tiles over all SMs holds
+long long eval_round_tracks(int KP, bool cuts, int tile_div);
+// limit of the statistic kernel's waits (ns) and whether its stager first waits for an arrival
+// that never comes (timeout tests); tfs_set_wait_limit sets them process-wide
+uint64_t eval_wait_ns();
+int eval_hold();
+void set_eval_wait(uint64_t ns, int hold);
 
 // top-k over device floats; scratch from `ws` (size from topk_workspace_bytes) or allocated.
 size_t topk_workspace_bytes(int64_t N);

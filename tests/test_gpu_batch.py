@@ -5,8 +5,8 @@ A job's bins do not depend on how its tracks are grouped into tiles, but
 which pairs the FP32 filter leaves to the FP64 fix-up sum does (the decision
 limit and the base bin are warp-uniform, the staged band is per tile), so the
 statistic of a job inside a batch equals tfs_eval_stat on the job alone within
-FP32 rounding (relative 1e-5, the parity tolerance), and each job is checked
-against the FP64 oracle on the same stored table.  The same call repeated
+FP32 rounding of the sum (relative 1e-6), and each job is checked against the
+FP64 oracle on the same stored table (relative 1e-5, the parity tolerance).  The same call repeated
 gives bit-identical results, and so does a CUDA-graph replay against an
 uncaptured call.
 """
@@ -105,7 +105,7 @@ def _same(torch, job, alone, exact=True):
             assert np.array_equal(alone.top_val.cpu().numpy().view(np.uint32),
                                   job.top_val.cpu().numpy().view(np.uint32))
     else:
-        assert O.stat_relative_error(b.astype(np.float64), a.astype(np.float64)) <= 1e-5
+        assert O.stat_relative_error(b.astype(np.float64), a.astype(np.float64)) <= 1e-6
     if job.topk and b.size:
         ref_idx, _ = O.topk(b.astype(np.float64), job.topk)
         assert np.array_equal(job.top_idx.cpu().numpy(), ref_idx)
@@ -194,8 +194,9 @@ def test_autotuned_launch_shape(T):
     torch = pytest.importorskip("torch")
     data = _make_jobs(T, torch, SPECS[:3] + SPECS[5:6], seed=31)
     jobs = [T.Job(d["table"], d["basis"], d["dc"], d["df"], m=d["m"], topk=d["topk"]) for d in data]
-    shape, ms = T.autotune(jobs, reps=2)
+    shape, ms, ms0 = T.autotune(jobs, reps=2)
     assert shape["pcap"] in (512, 1024, 2048, 3072, 4096) and shape["tile_div"] in (1, 2, 4, 8) and ms > 0
+    assert shape["slots"] in (2, 3, 4, 6, 8) and shape["group"] in (1, 4, 8, 16, 32) and 0 < ms <= ms0
     jobs2 = _batch(T, torch, data)
     for d, j in zip(data, jobs2):
         Pq, _ = d["table"].to_host()

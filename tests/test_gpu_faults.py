@@ -73,3 +73,44 @@ def test_server_expired_wait_and_no_room(T):
     with pytest.raises(ValueError):        # malformed: coefficients of the wrong width
         srv.submit(ds, rng.uniform(-1, 1, (10, 5)), rng.uniform(0, 0.05, 10))
     srv.close()
+
+
+def test_device_wait_timeout_and_recovery(T):
+    """A bounded device wait that runs out, made deterministic on the host: the statistic
+    kernel's staging warp is held back on a signal that nothing sends, with a 2 ms limit on
+    every wait.  The synchronous call returns TFS_ERR_TIMEOUT and the batched call sets its
+    device status; the kernel lets its in-flight copies land before it returns, so the next
+    ordinary calls on the same context match the oracle."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    n_seg, n_bin, T_sft, K, N = 41, 700, 1.0e4, 3, 6000
+    P = rng.exponential(2.0, (n_seg, n_bin))
+    U = np.linalg.qr(rng.standard_normal((n_seg, K)))[0].T.copy()
+    table = T.table_from_power(P, T_sft, "f32")
+    basis = T.basis_from_host(U)
+    c = rng.uniform(-1, 1, (N, K)) * 30 / T_sft
+    f = rng.uniform(50, 650, N) / T_sft
+    S, *_ = O.eval_stat(P.astype(np.float32).astype(np.float64), U, c, f, T_sft, 1, 0)
+    first = T.eval_stat(table, basis, c, f, m=1)  # builds the cached per-segment data and window sums
+    assert O.stat_relative_error(first.stat.astype(np.float64), S) <= 1e-5
+    dc = torch.from_numpy(c).cuda()
+    df = torch.from_numpy(f).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    T.set_wait_limit(2_000_000, hold=True)
+    try:
+        with pytest.raises(T.TfsError) as e:
+            T.eval_stat(table, basis, c, f, m=1)
+        assert e.value.code == -4
+        job = T.Job(table, basis, dc, df, m=1)
+        T.eval_batch([job], dev_status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 1
+    finally:
+        T.set_wait_limit(0, hold=False)
+    again = T.eval_stat(table, basis, c, f, m=1, topk=8)
+    assert np.array_equal(again.stat.view(np.uint32), first.stat.view(np.uint32))
+    job = T.Job(table, basis, dc, df, m=1)
+    T.eval_batch([job], dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert O.stat_relative_error(job.stat.cpu().numpy().astype(np.float64), S) <= 1e-5

@@ -207,7 +207,13 @@ def _eval_and_check(T, P64, V, coeffs, f_ref, Tsft, m, dtype, topk=0, check_bins
     assert e_same <= STAT_TOL_SAME_TABLE, e_same
     assert e_64 <= STAT_TOL_P64[dtype], e_64
     assert res.tie_count == len(ties)
-    assert sorted(res.ties) == sorted(ties)[: len(res.ties)] or set(res.ties) <= set(ties)
+    # the report holds min(count, capacity) distinct pairs: all of them when they fit, else a
+    # subset of the oracle's ties (which ones depends on the order the device found them)
+    assert len(res.ties) == min(len(ties), 4096) and len(set(res.ties)) == len(res.ties)
+    if len(ties) <= 4096:
+        assert sorted(res.ties) == sorted(ties)
+    else:
+        assert set(res.ties) <= set(ties)
     if topk:
         gi, gv = O.topk(res.stat, topk)
         assert np.array_equal(res.top_idx, gi)

@@ -1,11 +1,13 @@
 """Serving runtime (tfs_server_*): resident datasets under a device-memory budget,
 requests admitted and batched as they arrive, overlapping on the device.
 
-Every served result must equal tfs_eval_stat on the same dataset and tracks
-alone within FP32 rounding (relative 1e-5, the parity tolerance; the bins are
-identical), whether the request ran alone or in a mix with others, with tables
-resident or evicted and reloaded; the top-k must be the top of the returned
-statistic.
+Every served result must match the FP64 oracle's statistic of the same stored
+table within the parity tolerance (relative 1e-5), and tfs_eval_stat on the same
+dataset and tracks alone within 1e-6 (the bins are identical; only the FP32
+summation can differ, because the tiles a request's tracks share decide which
+pairs the FP32 filter leaves to the exact path), whether the request ran alone
+or in a mix with others, with tables resident or evicted and reloaded; the
+top-k must be the top of the returned statistic.
 """
 import math
 import threading
@@ -69,8 +71,12 @@ def _requests(rng, data, n):
 
 def _check(T, data, r, stat, ti, tv):
     d = data[r["ds"]]
+    if "Pq" not in d:
+        d["Pq"] = d["alone"].to_host()[0]  # the stored (dequantised) values, FP64
+    want, *_ = O.eval_stat(d["Pq"], d["U"], r["c"], r["f"], d["Tsft"], r["m"], 0)
+    assert O.stat_relative_error(stat.astype(np.float64), want) <= 1e-5
     ref = T.eval_stat(d["alone"], d["basis"], r["c"], r["f"], m=r["m"]).stat
-    assert O.stat_relative_error(stat.astype(np.float64), ref.astype(np.float64)) <= 1e-5
+    assert O.stat_relative_error(stat.astype(np.float64), ref.astype(np.float64)) <= 1e-6
     if r["topk"]:
         gi, _ = O.topk(stat.astype(np.float64), r["topk"])
         assert np.array_equal(ti, gi)
@@ -107,7 +113,9 @@ def test_served_results_equal_alone_under_concurrency(T):
     assert st["completed"] == 48 and st["failed"] == 0
     assert st["tracks_completed"] == sum(r["c"].shape[0] for r in reqs)
     assert 0 < st["p50_ms"] <= st["p99_ms"]
-    assert st["batches"] >= 1 and st["mean_jobs_per_batch"] >= 1.0
+    # 48 requests from 4 threads at once: while one batch runs the others queue, so batches carry
+    # several requests (continuous batching, not a queue served one at a time)
+    assert st["batches"] >= 1 and st["mean_jobs_per_batch"] > 1.0
     assert st["evictions"] == 0
     srv.close()
 
@@ -124,7 +132,7 @@ def test_same_result_alone_and_in_the_mix(T):
     mix.insert(15, probe)
     res = _serve(T, srv, ids, mix)
     inmix = res[15]
-    assert O.stat_relative_error(inmix[0].astype(np.float64), alone[0].astype(np.float64)) <= 1e-5
+    assert O.stat_relative_error(inmix[0].astype(np.float64), alone[0].astype(np.float64)) <= 1e-6
     _check(T, data, probe, *inmix)
     _check(T, data, probe, *alone)
     srv.close()
@@ -135,7 +143,8 @@ def test_budget_evicts_and_reloads_tables(T):
     idle tables and bring them back, with unchanged results."""
     data = _datasets(T, 5)
     tables = [T.table_from_power(d["P"], d["Tsft"], d["dtype"]) for d in data]
-    sizes = sorted(t.nbytes for t in tables)
+    # a resident dataset holds its table and, once evaluated with m = 1, its FP32 window sums
+    sizes = sorted(t.nbytes + t.n_seg * ((t.n_bin + 2 + 31) // 32 * 32) * 4 for t in tables)
     budget = sizes[-1] + sizes[-2] + (256 << 10)
     srv = T.Server(budget, max_batch_jobs=8)
     ids = [srv.add_dataset(t, d["basis"]) for t, d in zip(tables, data)]
