@@ -160,16 +160,18 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   pcap = std::max(64, std::min(pcap, qpitch_max));
   pcap = (pcap + 3) / 4 * 4;
   // shared-memory layout
-  const int RW = 2 * KP + 2;
-  size_t off = 8 * (2 * kMaxSlots + 3);
+  const int BW = 2 * KP + 2;
+  const int bcap = std::min(seg_max, kBandCap);
+  a.bcap = bcap;
+  size_t off = 8 * (2 * kMaxSlots + 7);
   off = (off + 15) & ~(size_t)15;
   a.off_hdr = (int)off;   off += (size_t)NS * sizeof(SlotHdr);
   off = (off + 15) & ~(size_t)15;
-  a.off_red = (int)off;   off += (size_t)2 * kConsWarps * RW * 4;
+  a.off_info = (int)off;  off += sizeof(WarpInfo) * kConsWarps + (size_t)kCons * 4 + (size_t)3 * BW * 4;
   off = (off + 15) & ~(size_t)15;
-  a.off_flags = (int)off; off += 16 + kMaxSlots * 4 + (size_t)(2 * KP + 2) * 4;
+  a.off_flags = (int)off; off += 16 + kMaxSlots * 4 + (size_t)2 * BW * 4;
   off = (off + 15) & ~(size_t)15;
-  a.off_band = (int)off;  off += (size_t)2 * std::min(seg_max, kBandCap) * 4;
+  a.off_band = (int)off;  off += (size_t)2 * 2 * bcap * 4;
   off = (off + 15) & ~(size_t)15;
   a.off_queue = (int)off; off += (size_t)kQT * kCons * 4;
   off = (off + 15) & ~(size_t)15;
@@ -200,9 +202,17 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     return TFS_ERR_INVALID_ARG;
   }
   const int grid = (int)std::min<long long>(nt, (long long)sm_count());
+  // the helper warps' prologue columns, one block per CTA (stream-ordered scratch)
+  float* cbuf = nullptr;
+  TFS_CUDA(cudaMallocAsync((void**)&cbuf, (size_t)grid * (KP + 1) * kCons * R * sizeof(float), st));
+  a.cbuf = cbuf;
   double* parts = nullptr;
   if (part_floats) {
-    TFS_CUDA(cudaMallocAsync((void**)&parts, part_floats * sizeof(double), st));
+    const cudaError_t e = cudaMallocAsync((void**)&parts, part_floats * sizeof(double), st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(cbuf, st);
+      return cuda_fail(e, "partial sums");
+    }
     size_t o = 0;
     for (int i = 0; i < L.n_jobs; ++i) {
       JobDesc& D = a.jobs[i];
@@ -243,6 +253,7 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     if (e != cudaSuccess) rc = cuda_fail(e, "partial sums");
   }
   if (parts) cudaFreeAsync(parts, st);
+  cudaFreeAsync(cbuf, st);
   return rc;
 }
 

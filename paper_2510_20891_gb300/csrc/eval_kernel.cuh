@@ -47,7 +47,7 @@ constexpr int kCons = 384;            // three consumer warpgroups
 constexpr int kThreads = kProd + kCons;
 constexpr int kConsWarps = kCons / 32;
 constexpr int kLaunchRegs = (65536 / kThreads) & ~7;  // 128 registers per thread at launch
-constexpr int kProdRegs = 64;         // setmaxnreg targets: 128*64 + 384*144 <= 512*128
+constexpr int kProdRegs = 72;         // setmaxnreg targets: 128*72 + 384*144 <= 512*128
 constexpr int kConsRegs = 144;
 static_assert(kProd * kProdRegs + kCons * kConsRegs <= kThreads * kLaunchRegs, "register split exceeds the launch");
 constexpr int kMaxSlots = 8;          // staging slots at most
@@ -56,7 +56,7 @@ constexpr int kSent = 4;              // zero floats staged after each band (the
 constexpr int kQT = 24;               // fix-up queue entries per consumer thread (a queue that fills
                                       // mid-tile stalls its warp on FP64 work: keep it rare)
 constexpr int kSegTile = 32;          // FP32 partial sums are flushed every kSegTile segments
-constexpr int kBandCap = 2048;        // segments whose bands are precomputed per tile
+constexpr int kBandCap = 1024;        // segments whose bands are precomputed per tile (two buffers)
 constexpr int kTrunc = 1 << 30;       // flag in a band length: the band was cut to the capacity
 constexpr uint64_t kDrainNs = 1000000000ull;  // wait for in-flight copies after a timeout (1 s)
 
@@ -100,10 +100,12 @@ struct EvalArgs {
   int scap;      // floats per staging slot (>= pcap + kSent + nsp)
   int nslots;    // staging slots (<= kMaxSlots)
   int group;     // segments per slot at most (<= kMaxGroup)
+  int bcap;      // segments whose bands are precomputed per tile (<= kBandCap); longer tiles compute them as they stage
+  float* cbuf;   // [grid][KP + 1][consumer threads * R] prologue columns (FP32 coefficients, then y0)
   int n_tiles;
   int n_jobs;
   // shared-memory carve-up (byte offsets)
-  int off_hdr, off_red, off_flags, off_band, off_queue, off_acc, off_slots;
+  int off_hdr, off_info, off_flags, off_band, off_queue, off_acc, off_slots;
   int tile_start[MJ + 1];  // first tile of each job (prefix sums), tile_start[n_jobs] = n_tiles
   JobDesc jobs[MJ];
 };
@@ -305,17 +307,14 @@ __device__ __forceinline__ bool thread_wait(uint64_t* bar, uint32_t parity, vola
     }
   }
 }
-__device__ __forceinline__ void prod_bar() {  // named barrier 1 among the producer warpgroup
-  asm volatile("barrier.sync 1, %0;" ::"n"(kProd) : "memory");
-}
-// Named barrier 1 among the producer warpgroup that also ORs a predicate over its threads: every
-// producer thread gets the same answer, so all of them leave their loop at the same barrier.
-__device__ __forceinline__ bool prod_bar_or(bool v) {
+// Named barrier 1 among the three helper warps that also ORs a predicate over their threads:
+// every helper gets the same answer, so all of them leave their loop at the same barrier.
+__device__ __forceinline__ bool help_bar_or(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, 96, p;\n selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"((uint32_t)v), "n"(kProd)
+      : "r"((uint32_t)v)
       : "memory");
   return r != 0;
 }
@@ -366,28 +365,47 @@ __device__ __forceinline__ void band_of(const float* d, const float* blo_k, cons
   *out_len = len;
 }
 
+// Per consumer warp, the values its tile prologue needs (prepared by the helper warps).
+struct WarpInfo {
+  int Bw;       // base bin: the FP64 mid-segment bin of the warp's first usable track
+  float wlim;   // decision limit: min over the warp's tracks decided in FP32 of 1/2 - g (1/2 if none)
+  float mz;     // segment cuts: margin of the second-order test
+  float mw;     // segment cuts: margin of the fdot test
+  float ylo;    // segment cuts: 10^-3.5 T_SFT - Bw (bin units, FP32)
+  int zt;       // segment cuts: some track of the warp may reach the second-order cut
+  int pad0, pad1;
+};
+
 template <int KP, int R, bool BINS, bool CUTS, int MJ>
 __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_constant__ EvalArgs<MJ> a) {
   constexpr bool kCutRegs = CUTS && KP <= 8;  // segment-cut forms held in registers
-  constexpr int RW = 2 * KP + 2;
+  constexpr int kCR = kCons * R;              // track slots of a tile (slot r * kCons + ctid)
+  constexpr int BW = 2 * KP + 2;              // a box: KP minima, KP maxima, then bm, bx (ints)
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* full = bars;                           // [kMaxSlots] a slot's copies landed (tx)
-  uint64_t* empty = bars + kMaxSlots;              // [kMaxSlots] consumers done with the slot (12 warps)
-  uint64_t* tile_ready = bars + 2 * kMaxSlots;     // [2] a tile's coefficient box is ready (12 warps)
-  uint64_t* hold_bar = bars + 2 * kMaxSlots + 2;   // nothing arrives on it (timeout tests)
-  SlotHdr* hdr = reinterpret_cast<SlotHdr*>(smem + a.off_hdr);  // [nslots]
-  float* red = reinterpret_cast<float*>(smem + a.off_red);      // [2][kConsWarps][RW]
+  uint64_t* full = bars;                      // [kMaxSlots] a slot's copies landed (tx)
+  uint64_t* empty = bars + kMaxSlots;         // [kMaxSlots] consumers done with the slot (12 warps)
+  uint64_t* pro_full = bars + 2 * kMaxSlots;  // the next tile's prologue data is ready (helpers)
+  uint64_t* pro_free = pro_full + 1;          // the consumers have read it (12 warps)
+  uint64_t* band_ready = pro_full + 2;        // [2] a tile's box and bands are ready (helpers)
+  uint64_t* band_free = pro_full + 4;         // [2] the stager is done with them
+  uint64_t* hold_bar = pro_full + 6;          // nothing arrives on it (timeout tests)
+  SlotHdr* hdr = reinterpret_cast<SlotHdr*>(smem + a.off_hdr);                // [nslots]
+  WarpInfo* winfo = reinterpret_cast<WarpInfo*>(smem + a.off_info);          // [kConsWarps]
+  uint32_t* inboxm = reinterpret_cast<uint32_t*>(winfo + kConsWarps);         // [kCons] tracks decided in FP32
+  float* bpart = reinterpret_cast<float*>(inboxm + kCons);                    // [3][BW] box partials
   volatile int* flags = reinterpret_cast<volatile int*>(smem + a.off_flags);  // [0] abort
   uint32_t* issued = reinterpret_cast<uint32_t*>(smem + a.off_flags) + 4;    // [kMaxSlots] last use + 1
-  float* box = reinterpret_cast<float*>(issued + kMaxSlots);                  // [2*KP] floats, then 2 ints
-  int* band = reinterpret_cast<int*>(smem + a.off_band);                      // [kBandCap][2]
+  float* boxes = reinterpret_cast<float*>(issued + kMaxSlots);                // [2][BW]
+  int* bands = reinterpret_cast<int*>(smem + a.off_band);                     // [2][bcap][2]
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + a.off_queue);          // [kQT][kCons]
   float* corr = reinterpret_cast<float*>(smem + a.off_acc);                  // [R][kCons] sum of FP64-path values
   float* corrl = corr + R * kCons;                                            // [R][kCons] its rounding error
   float* tot = corrl + R * kCons;                                             // [R][kCons] sum of 32-segment blocks
   float* comp = tot + R * kCons;                                              // [R][kCons] its rounding error
   float* slots = reinterpret_cast<float*>(smem + a.off_slots);                // [nslots][scap]
+  // this CTA's prologue columns in global memory: FP32 coefficients [KP][kCR], then y0 [kCR]
+  float* cbuf = a.cbuf + (size_t)blockIdx.x * (KP + 1) * kCR;
   const int NS = a.nslots;
 
   const int tid = threadIdx.x;
@@ -400,7 +418,12 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], kConsWarps);
     }
-    for (int i = 0; i < 2; ++i) mbar_init(&tile_ready[i], kConsWarps);
+    mbar_init(pro_full, 1);
+    mbar_init(pro_free, kConsWarps);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&band_ready[i], 1);
+      mbar_init(&band_free[i], 1);
+    }
     mbar_init(hold_bar, 1);
     fence_mbar_init();
   }
@@ -409,115 +432,317 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
   if (tid < kProd) {
     // ================================================================ producer warpgroup
     setmaxnreg_dec<kProdRegs>();
-    const int pw = tid >> 5;  // 0: stager, 1..3: band helpers
-    uint32_t seq = 0;         // slots filled so far in this launch
-    if (a.hold && pw == 0) (void)warp_wait(hold_bar, 0u, flags, a.wait_ns);
-    int ltile = 0;
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
-      const int j = job_of(a, tile);
-      const JobDesc& J = a.jobs[j];
-      const int m = J.m;
-      long long tile0_unused;
-      int sp_unused, s0, s1;
-      tile_range(a, J, tile, j, &tile0_unused, &sp_unused, &s0, &s1);
-      const int ns = s1 - s0;  // this tile's segments
-      // -------------------------------------------------------------- tile set-up (all 128)
-      if (tid == 0) {
-        if (thread_wait(&tile_ready[ltile & 1], (uint32_t)((ltile >> 1) & 1), flags, a.wait_ns)) {
-          const float* rb = red + (ltile & 1) * kConsWarps * RW;
+    if (tid < 32) {
+      // ------------------------------------------------------------ stager warp
+      // per tile: wait for its bands, then fill slots; lane g stages segment sg + g of a slot,
+      // the slot taking the leading segments that fit
+      uint32_t seq = 0;  // slots filled so far in this launch
+      if (a.hold) (void)warp_wait(hold_bar, 0u, flags, a.wait_ns);
+      int ltile = 0;
+      for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
+        const int j = job_of(a, tile);
+        const JobDesc& J = a.jobs[j];
+        const int m = J.m;
+        long long tile0_unused;
+        int sp_unused, s0, s1;
+        tile_range(a, J, tile, j, &tile0_unused, &sp_unused, &s0, &s1);
+        const int ns = s1 - s0;
+        const int b = ltile & 1;
+        if (!warp_wait(&band_ready[b], (uint32_t)((ltile >> 1) & 1), flags, a.wait_ns)) break;
+        const float* box = boxes + b * BW;
+        const int* band = bands + b * 2 * a.bcap;
+        const int bm = reinterpret_cast<const int*>(box)[2 * KP];
+        const int bx = reinterpret_cast<const int*>(box)[2 * KP + 1];
+        bool go = true;
+        for (int sg = s0; sg < s1 && go;) {
+          const int s = (int)(seq % (uint32_t)NS);
+          if (seq >= (uint32_t)NS) go = warp_wait(&empty[s], ((seq / NS) - 1u) & 1u, flags, a.wait_ns);
+          else go = !__any_sync(0xffffffffu, flags[0] != 0);
+          if (!go) break;
+          // a slot never crosses a 32-segment block boundary, so that the consumers add a finished
+          // block's FP32 sums after the slot instead of testing every segment
+          const bool has = lane < a.group && sg + lane < s1 && lane < kSegTile - (sg % kSegTile);
+          int ilo = 0, len = 0, need = 0;
+          if (has) {
+            if (ns <= a.bcap) {
+              ilo = band[2 * (sg + lane - s0)];
+              len = band[2 * (sg + lane - s0) + 1];
+            } else {
+              band_of<KP>(J.segp + (size_t)(sg + lane) * a.nsp, box, box + KP, bm, bx, m, J.n_bin, a.pcap, &ilo,
+                          &len);
+            }
+            need = (len & (kTrunc - 1)) + kSent + a.nsp;
+          }
+          int incl = need;  // inclusive prefix sum of the floats each segment takes
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const unsigned fit = __ballot_sync(0xffffffffu, has && incl <= a.scap);  // a prefix of the lanes
+          const int n = __popc(fit);
+          const int total = __shfl_sync(0xffffffffu, incl, max(n - 1, 0));
+          const int off = incl - need;
+          const int ql = len & (kTrunc - 1);
+          if (lane < n) hdr[s].seg[lane] = make_int4(s * a.scap + off, ilo - m, ql, (len & kTrunc) ? 0 : 1);
+          if (lane == 0) hdr[s].nseg = n;
+          __syncwarp();
+          // the slot's previous contents were read through the generic proxy
+          fence_proxy_async_smem();
+          if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)total * 4u);
+          __syncwarp();
+          if (lane < n) {
+            const int seg = sg + lane;
+            float* dst = slots + (size_t)s * a.scap + off;
+            const bool ok =
+                dbg_ok(a.dbg, n >= 1 && off + need <= a.scap && ((off & 3) == 0) && ((a.scap & 3) == 0), 7, off,
+                       need) &&
+                dbg_ok(a.dbg, ilo >= 0 && (ilo & 3) == 0 && (ql & 3) == 0 && ilo + ql <= J.qpitch, 8, ilo, ql) &&
+                dbg_ok(a.dbg, (long long)a.off_slots + ((long long)s + 1) * a.scap * 4 <= a.smem_bytes, 9, s, a.scap);
+            if (ok) {
+              if (ql > 0) bulk_g2s(dst, J.q + (size_t)seg * J.qpitch + ilo, (uint32_t)ql * 4u, &full[s]);
+              bulk_g2s(dst + ql, g_zero4, (uint32_t)kSent * 4u, &full[s]);
+              bulk_g2s(dst + ql + kSent, J.segp + (size_t)seg * a.nsp, (uint32_t)a.nsp * 4u, &full[s]);
+            } else {
+              // a self-check failed (debug builds): complete the transaction without copying
+              asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])),
+                           "r"((uint32_t)need * 4u)
+                           : "memory");
+            }
+          }
+          if (lane == 0) issued[s] = seq + 1u;
+          __syncwarp();
+          sg += n;
+          ++seq;
+        }
+        if (!go) break;
+        if (lane == 0) mbar_arrive(&band_free[b]);
+      }
+    } else {
+      // ------------------------------------------------------------ helper warps (3)
+      // One tile ahead of the consumers, in FP64 where the bin decision needs it: each track's
+      // FP32 coefficients and offset y0 = x_mid - Bw, whether FP32 decides its bins, each
+      // consumer warp's base bin and decision limit, the tile's coefficient box and its bands.
+      const int hid = tid - 32;  // 0..95
+      const int hw = hid >> 5;   // 0..2
+      int ltile = 0;
+      for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
+        const int j = job_of(a, tile);
+        const JobDesc& J = a.jobs[j];
+        const int n_seg = J.n_seg, m = J.m, K = J.K;
+        long long tile0;
+        int sp_unused, s0, s1;
+        tile_range(a, J, tile, j, &tile0, &sp_unused, &s0, &s1);
+        const int ns = s1 - s0;
+        const long long tend = min(J.N, tile0 + J.tile_tracks);
+        const int b = ltile & 1;
+        // the consumers have read the previous tile's data
+        if (ltile > 0) (void)warp_wait(pro_free, (uint32_t)((ltile - 1) & 1), flags, a.wait_ns);
+        if (help_bar_or(flags[0] != 0)) break;
+        // the base bin of each consumer warp: from its first lane whose first track is usable
+        for (int w = hw; w < kConsWarps; w += 3) {
+          const long long t = tile0 + w * 32 + lane;
+          const bool active = t < tend;
+          double xm = 0.0;
+          bool ex = false;
+          if (active) {
+            double f = J.f_ref ? J.f_ref[t] : 0.0;
+            float A = 0.f;
+            const double* cp = J.coeffs + t * (long long)K;
+            for (int k = 0; k < K; ++k) {
+              const double cd = cp[k];
+              f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
+              A = fmaf(fabsf((float)cd), J.dmax[k], A);
+            }
+            A *= 1.0001f;
+            xm = f * J.T;
+            ex = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
+          }
+          const unsigned ok = __ballot_sync(0xffffffffu, active && !ex);
+          const int src = ok ? __ffs(ok) - 1 : 0;
+          const int Bw = __shfl_sync(0xffffffffu, (active && !ex) ? (int)rint(xm) : 0, src);
+          if (lane == 0) {
+            winfo[w].Bw = Bw;
+            winfo[w].ylo = CUTS ? (float)(kFLowHz * J.T - (double)Bw) : 0.f;
+          }
+        }
+        if (help_bar_or(flags[0] != 0)) break;
+        // every track: the helper lanes of round q hold the 32 lanes of consumer warp hw + 3q
+        int bmin = 0x7fffffff, bmax = -0x7fffffff;
+        for (int q = 0; q < 4; ++q) {
+          const int ctid = hid + 96 * q;
+          const int w = ctid >> 5;
+          const int Bw = winfo[w].Bw;
+          float wl = 0.5f, mzl = 0.f, mwl = 0.f;
+          bool ztl = false;
+          uint32_t ib = 0u;
+          for (int r = 0; r < R; ++r) {
+            const long long t = tile0 + ctid + r * kCons;
+            float* col = cbuf + r * kCons + ctid;  // coefficient k at col[k * kCR], y0 at col[KP * kCR]
+            if (!(t < tend)) {
+              // inactive slot: c = 0 and y far from the table (|y| < 2^22), never pending
+              for (int k = 0; k < KP; ++k) col[k * kCR] = 0.f;
+              col[KP * kCR] = Bw >= 0 ? 4194303.0f : -4194303.0f;
+              continue;
+            }
+            const double fr = J.f_ref ? J.f_ref[t] : 0.0;
+            double f = fr;
+            float A = 0.f, Um = fabsf((float)fr), Az = 0.f, Aw = 0.f;
+            const double* cp = J.coeffs + t * (long long)K;
+            for (int k = 0; k < KP; ++k) {
+              const double cd = (k < K) ? cp[k] : 0.0;
+              if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
+              const float cf = (float)cd;
+              col[k * kCR] = cf;
+              A = fmaf(fabsf(cf), J.dmax[k], A);
+              Um = fmaf(fabsf(cf), J.umax[k], Um);
+              if (CUTS) {
+                Az = fmaf(fabsf(cf), J.emax[k], Az);
+                Aw = fmaf(fabsf(cf), J.gmax[k], Aw);
+              }
+            }
+            A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
+            Um *= 1.0001f;
+            float ezt = 0.f, ewt = 0.f, zbt = 0.f;
+            if (CUTS) {
+              // z = fddot T^3/6 and w = fdot are linear in c: z = sum_k c_k E_k, w = sum_k c_k G_k.
+              // |fp32 z - oracle z| <= 2^-24 (K+2) sum|c_k| max|E_k| (c, E and the K FMAs rounded)
+              // + (4K+40) 2^-53 Um T/6 (the oracle's rounded frequencies, its second difference
+              // and the FP64 rounding of E); |fp32 w - oracle w| likewise with G and
+              // (2K+12) 2^-53 Um / T_SFT, plus the FP32 rounding of the 1e-13 threshold
+              ezt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Az * 1.0001f +
+                             (4.f * K + 40.f) * 1.1102230246251565e-16f * Um * (float)(J.T / 6.0)) + 1e-12f;
+              ewt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Aw * 1.0001f +
+                             (2.f * K + 12.f) * 1.1102230246251565e-16f * Um / (float)J.T) + 1e-20f;
+              zbt = Az * 1.0001f + ezt;  // bounds |oracle z| in every segment
+            }
+            const double xm = f * J.T;
+            // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
+            // FP32, K rounded FMAs on partial sums below |y0| + A, and the FP32 roundings of c and
+            // D; e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid,
+            // the deltas D, and the oracle's own evaluation).  With g = 1.25 (err + e64) + 4e-9,
+            // pairs closer than g to a half-integer are resolved in FP64; outside that band the
+            // exact, the oracle's and this bin coincide and none of them is a 1e-9 tie.
+            const float e64 = 7.105427357601002e-15f * (float)J.T * Um;
+            const float eb = 1.25f * (5.9604644775390625e-08f * ((K + 2.001f) * A) + 2.f * e64) + 4e-9f;
+            bool exact = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
+            float y0 = 0.5f;
+            if (!exact) {
+              const double yd = xm - (double)Bw;
+              const float yf = (float)yd;
+              const float g = eb + 1.25f * 5.9604644775390625e-08f * (float)(K + 1) * fabsf(yf) * 1.0001f;
+              exact = !(fabs(yd) < 2097152.0) || !(g < 0.25f);
+              if (!exact) {
+                y0 = yf;
+                wl = fminf(wl, __fsub_rd(0.5f, g));
+                if (CUTS) {
+                  mzl = fmaxf(mzl, ezt);
+                  mwl = fmaxf(mwl, ewt);
+                  ztl = ztl || !(zbt < 1.f);
+                }
+                const int Bd = (int)rint(xm);
+                bmin = min(bmin, Bd);
+                bmax = max(bmax, Bd);
+                ib |= 1u << r;
+              }
+            }
+            if (exact) {
+              // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
+              for (int k = 0; k < KP; ++k) col[k * kCR] = 0.f;
+            }
+            col[KP * kCR] = y0;
+          }
+          inboxm[ctid] = ib;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            wl = fminf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+            if (CUTS) {
+              mzl = fmaxf(mzl, __shfl_xor_sync(0xffffffffu, mzl, o));
+              mwl = fmaxf(mwl, __shfl_xor_sync(0xffffffffu, mwl, o));
+            }
+          }
+          ztl = __any_sync(0xffffffffu, ztl);
+          if (lane == 0) {
+            winfo[w].wlim = wl;
+            winfo[w].mz = mzl;
+            winfo[w].mw = mwl;
+            winfo[w].zt = ztl ? 1 : 0;
+          }
+        }
+        // the coefficient box of the tracks decided in FP32 (a partial per helper warp)
+        float* bp = bpart + hw * BW;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+          bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        }
+        if (lane == 0) {
+          reinterpret_cast<int*>(bp)[2 * KP] = bmin;
+          reinterpret_cast<int*>(bp)[2 * KP + 1] = bmax;
+        }
+        for (int k = 0; k < KP; ++k) {
+          float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+          for (int q = 0; q < 4; ++q) {
+            const int ctid = hid + 96 * q;
+            const uint32_t ib = inboxm[ctid];
+            for (int r = 0; r < R; ++r) {
+              if ((ib >> r) & 1u) {
+                const float v = cbuf[k * kCR + r * kCons + ctid];
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+              }
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+          }
+          if (lane == 0) {
+            bp[k] = lo;
+            bp[KP + k] = hi;
+          }
+        }
+        __threadfence_block();  // the columns in global memory, before the consumers are told
+        if (help_bar_or(flags[0] != 0)) break;
+        // this parity's box and bands are free once the stager is done with tile ltile - 2
+        if (ltile >= 2) (void)warp_wait(&band_free[b], (uint32_t)(((ltile - 2) >> 1) & 1), flags, a.wait_ns);
+        float* box = boxes + b * BW;
+        if (hid == 0) {
           int bm = 0x7fffffff, bx = -0x7fffffff;
           for (int k = 0; k < KP; ++k) {
             float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-            for (int w = 0; w < kConsWarps; ++w) {
-              lo = fminf(lo, rb[w * RW + k]);
-              hi = fmaxf(hi, rb[w * RW + KP + k]);
+            for (int h = 0; h < 3; ++h) {
+              lo = fminf(lo, bpart[h * BW + k]);
+              hi = fmaxf(hi, bpart[h * BW + KP + k]);
             }
             box[k] = lo;
             box[KP + k] = hi;
           }
-          for (int w = 0; w < kConsWarps; ++w) {
-            bm = min(bm, reinterpret_cast<const int*>(rb)[w * RW + 2 * KP]);
-            bx = max(bx, reinterpret_cast<const int*>(rb)[w * RW + 2 * KP + 1]);
+          for (int h = 0; h < 3; ++h) {
+            bm = min(bm, reinterpret_cast<const int*>(bpart + h * BW)[2 * KP]);
+            bx = max(bx, reinterpret_cast<const int*>(bpart + h * BW)[2 * KP + 1]);
           }
           reinterpret_cast<int*>(box)[2 * KP] = bm;
           reinterpret_cast<int*>(box)[2 * KP + 1] = bx;
         }
-      }
-      __syncwarp();
-      if (prod_bar_or(flags[0] != 0)) break;  // every producer thread leaves here, together
-      const int bm = reinterpret_cast<const int*>(box)[2 * KP];
-      const int bx = reinterpret_cast<const int*>(box)[2 * KP + 1];
-      if (ns <= kBandCap) {
-        for (int i = tid; i < ns; i += kProd) {
-          int lo, len;
-          band_of<KP>(J.segp + (size_t)(s0 + i) * a.nsp, box, box + KP, bm, bx, m, J.n_bin, a.pcap, &lo, &len);
-          band[2 * i] = lo;
-          band[2 * i + 1] = len;
-        }
-      }
-      prod_bar();
-      if (pw != 0) continue;
-      // ------------------------------------------------------------ stager warp
-      // lane g stages segment sg + g of the slot; the slot takes the leading segments that fit
-      for (int sg = s0; sg < s1;) {
-        const int s = (int)(seq % (uint32_t)NS);
-        bool go;
-        if (seq >= (uint32_t)NS) go = warp_wait(&empty[s], ((seq / NS) - 1u) & 1u, flags, a.wait_ns);
-        else go = !__any_sync(0xffffffffu, flags[0] != 0);
-        if (!go) break;
-        // a slot never crosses a 32-segment block boundary, so that the consumers add a finished
-        // block's FP32 sums after the slot instead of testing every segment
-        const bool has = lane < a.group && sg + lane < s1 && lane < kSegTile - (sg % kSegTile);
-        int ilo = 0, len = 0, need = 0;
-        if (has) {
-          if (ns <= kBandCap) {
-            ilo = band[2 * (sg + lane - s0)];
-            len = band[2 * (sg + lane - s0) + 1];
-          } else {
-            band_of<KP>(J.segp + (size_t)(sg + lane) * a.nsp, box, box + KP, bm, bx, m, J.n_bin, a.pcap, &ilo, &len);
-          }
-          need = (len & (kTrunc - 1)) + kSent + a.nsp;
-        }
-        int incl = need;  // inclusive prefix sum of the floats each segment takes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const unsigned fit = __ballot_sync(0xffffffffu, has && incl <= a.scap);  // a prefix of the lanes
-        const int n = __popc(fit);
-        const int total = __shfl_sync(0xffffffffu, incl, max(n - 1, 0));
-        const int off = incl - need;
-        const int ql = len & (kTrunc - 1);
-        if (lane < n) hdr[s].seg[lane] = make_int4(s * a.scap + off, ilo - m, ql, (len & kTrunc) ? 0 : 1);
-        if (lane == 0) hdr[s].nseg = n;
-        __syncwarp();
-        // the slot's previous contents were read through the generic proxy
-        fence_proxy_async_smem();
-        if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)total * 4u);
-        __syncwarp();
-        if (lane < n) {
-          const int seg = sg + lane;
-          float* dst = slots + (size_t)s * a.scap + off;
-          const bool ok =
-              dbg_ok(a.dbg, n >= 1 && off + need <= a.scap && ((off & 3) == 0) && ((a.scap & 3) == 0), 7, off, need) &&
-              dbg_ok(a.dbg, ilo >= 0 && (ilo & 3) == 0 && (ql & 3) == 0 && ilo + ql <= J.qpitch, 8, ilo, ql) &&
-              dbg_ok(a.dbg, (long long)a.off_slots + ((long long)s + 1) * a.scap * 4 <= a.smem_bytes, 9, s, a.scap);
-          if (ok) {
-            if (ql > 0) bulk_g2s(dst, J.q + (size_t)seg * J.qpitch + ilo, (uint32_t)ql * 4u, &full[s]);
-            bulk_g2s(dst + ql, g_zero4, (uint32_t)kSent * 4u, &full[s]);
-            bulk_g2s(dst + ql + kSent, J.segp + (size_t)seg * a.nsp, (uint32_t)a.nsp * 4u, &full[s]);
-          } else {
-            // a self-check failed (debug builds): complete the transaction without copying
-            asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])),
-                         "r"((uint32_t)need * 4u)
-                         : "memory");
+        if (help_bar_or(flags[0] != 0)) break;
+        if (ns <= a.bcap) {
+          const int bm = reinterpret_cast<const int*>(box)[2 * KP];
+          const int bx = reinterpret_cast<const int*>(box)[2 * KP + 1];
+          int* band = bands + b * 2 * a.bcap;
+          for (int i = hid; i < ns; i += 96) {
+            int lo, len;
+            band_of<KP>(J.segp + (size_t)(s0 + i) * a.nsp, box, box + KP, bm, bx, m, J.n_bin, a.pcap, &lo, &len);
+            band[2 * i] = lo;
+            band[2 * i + 1] = len;
           }
         }
-        if (lane == 0) issued[s] = seq + 1u;
-        __syncwarp();
-        sg += n;
-        ++seq;
+        if (help_bar_or(flags[0] != 0)) break;
+        if (hid == 0) {
+          mbar_arrive(pro_full);
+          mbar_arrive(&band_ready[b]);
+        }
       }
     }
   } else {
@@ -531,16 +756,18 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
     for (int tile = blockIdx.x; tile < a.n_tiles && !dead; tile += gridDim.x, ++ltile) {
       const int j = job_of(a, tile);
       const JobDesc& J = a.jobs[j];
-      const int n_seg = J.n_seg, m = J.m, K = J.K;
+      const int n_seg = J.n_seg, m = J.m;
       long long tile0;
       int sp, s0, s1;
       tile_range(a, J, tile, j, &tile0, &sp, &s0, &s1);
       const long long tend = min(J.N, tile0 + J.tile_tracks);
-      if (__any_sync(0xffffffffu, flags[0] != 0)) break;
       // -------------------------------------------------------------- tile prologue
       // Each track is evaluated relative to a warp-uniform base bin Bw (the FP64 mid-segment bin
       // of the warp's first track): y = (x_mid - Bw) + sum_k c_k D_k,alpha in FP32, and the bin
-      // is Bw + rint(y).  One base per warp keeps a register per track free.
+      // is Bw + rint(y).  One base per warp keeps a register per track free.  The helper warps
+      // prepared y0 = x_mid - Bw, the FP32 coefficients (0 for a track that FP32 cannot decide,
+      // whose y0 is 1/2), the warp's base and decision limit.
+      if (!warp_wait(pro_full, (uint32_t)(ltile & 1), flags, a.wait_ns)) break;
       // tracks in pairs for the packed FP32x2 arithmetic (an odd R gets an inactive partner):
       // track r is half (r & 1) of c2[r / 2][k] and y02[r / 2]
       constexpr int R2 = (R + 1) / 2;
@@ -559,175 +786,44 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         f2split(v, lo, hi);
         v = half ? f2pack(lo, x) : f2pack(x, hi);
       };
-      auto get = [](f32x2 v, int half) {
-        float lo, hi;
-        f2split(v, lo, hi);
-        return half ? hi : lo;
-      };
-      int Bw = 0;
-      // warp-uniform decision limit: min over the warp's tracks of 1/2 - g; at most 1/2, so the
-      // tracks that take the FP64 path for every pair (y = 1/2) are never decided in FP32
-      float wlim = 0.5f;
+      const WarpInfo wi = winfo[cwarp];
+      const int Bw = wi.Bw;
+      const float wlim = wi.wlim;  // at most 1/2: the tracks that FP32 cannot decide (y = 1/2) never are
+      int nq = 0;                  // entries in this thread's fix-up queue
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        acc[r] = 0.f;
+        corr[r * kCons + ctid] = 0.f;
+        corrl[r * kCons + ctid] = 0.f;
+        tot[r * kCons + ctid] = 0.f;
+        comp[r * kCons + ctid] = 0.f;
+        const float* col = cbuf + r * kCons + ctid;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) put(c2[r / 2][k], r & 1, col[k * kCR]);
+        put(y02[r / 2], r & 1, col[KP * kCR]);
+      }
       // segment cuts: warp-uniform margins of the second-order test (mz), the fdot test (mw)
-      // and the low-frequency test (mf, against ylo = 10^-3.5 T_SFT - Bw in bin units)
-      float mz = 0.f, mw = 0.f, mf = 0.f, ylo = 0.f;
-      // ... as thresholds: included below zin / above win, fin; excluded above zex / below wex, fex
+      // and the low-frequency test (mf, against ylo = 10^-3.5 T_SFT - Bw in bin units), as
+      // thresholds: included below zin / above win, fin; excluded above zex / below wex, fex
       float zin = 0.f, zex = 0.f, win = 0.f, wex = 0.f, fin = 0.f, fex = 0.f;
       unsigned cutm = 0u;  // tracks whose cuts are decided in FP32 (the others are always pending)
       bool zt = false;     // some track of the warp may reach the second-order cut
-      int nq = 0;          // entries in this thread's fix-up queue
-      {
-        int bmin = 0x7fffffff, bmax = -0x7fffffff;
-        unsigned inbox = 0u;  // tracks that enter the coefficient box (decided in FP32)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          acc[r] = 0.f;
-          put(y02[r / 2], r & 1, 0.f);
-          corr[r * kCons + ctid] = 0.f;
-          corrl[r * kCons + ctid] = 0.f;
-          tot[r * kCons + ctid] = 0.f;
-          comp[r * kCons + ctid] = 0.f;
-          const long long t = tile0 + ctid + r * kCons;
-          const bool active = t < tend;
-          double xm = 0.0;
-          float eb = 0.f, ezt = 0.f, ewt = 0.f, zbt = 0.f;
-          bool exact = false;
-          if (active) {
-            const double fr = J.f_ref ? J.f_ref[t] : 0.0;
-            double f = fr;
-            float A = 0.f, Um = fabsf((float)fr), Az = 0.f, Aw = 0.f;
-            const double* cp = J.coeffs + t * (long long)K;
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-              const double cd = (k < K) ? cp[k] : 0.0;
-              if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
-              const float cf = (float)cd;
-              put(c2[r / 2][k], r & 1, cf);
-              A = fmaf(fabsf(cf), J.dmax[k], A);
-              Um = fmaf(fabsf(cf), J.umax[k], Um);
-              if (CUTS) {
-                Az = fmaf(fabsf(cf), J.emax[k], Az);
-                Aw = fmaf(fabsf(cf), J.gmax[k], Aw);
-              }
-            }
-            A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
-            Um *= 1.0001f;
-            if (CUTS) {
-              // z = fddot T^3/6 and w = fdot are linear in c: z = sum_k c_k E_k, w = sum_k c_k G_k.
-              // |fp32 z - oracle z| <= 2^-24 (K+2) sum|c_k| max|E_k| (c, E and the K FMAs rounded)
-              // + (4K+40) 2^-53 Um T/6 (the oracle's rounded frequencies, its second difference
-              // and the FP64 rounding of E); |fp32 w - oracle w| likewise with G and
-              // (2K+12) 2^-53 Um / T_SFT, plus the FP32 rounding of the 1e-13 threshold
-              ezt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Az * 1.0001f +
-                             (4.f * K + 40.f) * 1.1102230246251565e-16f * Um * (float)(J.T / 6.0)) + 1e-12f;
-              ewt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Aw * 1.0001f +
-                             (2.f * K + 12.f) * 1.1102230246251565e-16f * Um / (float)J.T) + 1e-20f;
-              zbt = Az * 1.0001f + ezt;  // bounds |oracle z| in every segment
-            }
-            xm = f * J.T;
-            // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
-            // FP32, K rounded FMAs on partial sums below |y0| + A, and the FP32 roundings of c and
-            // D; e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid,
-            // the deltas D, and the oracle's own evaluation).  With g = 1.25 (err + e64) + 4e-9,
-            // pairs closer than g to a half-integer are resolved in FP64; outside that band the
-            // exact, the oracle's and this bin coincide and none of them is a 1e-9 tie.
-            const float e64 = 7.105427357601002e-15f * (float)J.T * Um;
-            eb = 1.25f * (5.9604644775390625e-08f * ((K + 2.001f) * A) + 2.f * e64) + 4e-9f;
-            exact = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
-          }
-          if (r == 0) {
-            // the warp's base bin: from the first lane whose first track is usable
-            const unsigned ok = __ballot_sync(0xffffffffu, active && !exact);
-            const int src = ok ? __ffs(ok) - 1 : 0;
-            Bw = __shfl_sync(0xffffffffu, (active && !exact) ? (int)rint(xm) : 0, src);
-          }
-          if (!active) {
-            // inactive slot: c = 0 and y far from the table (|y| < 2^22), never pending
-            put(y02[r / 2], r & 1, Bw >= 0 ? 4194303.0f : -4194303.0f);
-            continue;
-          }
-          if (!exact) {
-            const double yd = xm - (double)Bw;
-            const float yf = (float)yd;
-            const float g = eb + 1.25f * 5.9604644775390625e-08f * (float)(K + 1) * fabsf(yf) * 1.0001f;
-            exact = !(fabs(yd) < 2097152.0) || !(g < 0.25f);
-            if (!exact) {
-              put(y02[r / 2], r & 1, yf);
-              wlim = fminf(wlim, __fsub_rd(0.5f, g));
-              if (CUTS) {
-                mz = fmaxf(mz, ezt);
-                mw = fmaxf(mw, ewt);
-                zt = zt || !(zbt < 1.f);
-              }
-              const int Bd = (int)rint(xm);
-              bmin = min(bmin, Bd);
-              bmax = max(bmax, Bd);
-              inbox |= 1u << r;
-            }
-          }
-          if (exact) {
-            // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
-            put(y02[r / 2], r & 1, 0.5f);
-#pragma unroll
-            for (int k = 0; k < KP; ++k) put(c2[r / 2][k], r & 1, 0.f);
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wlim = fminf(wlim, __shfl_xor_sync(0xffffffffu, wlim, o));
-        if (CUTS) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            mz = fmaxf(mz, __shfl_xor_sync(0xffffffffu, mz, o));
-            mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
-          }
-          const double ylo64 = kFLowHz * J.T - (double)Bw;
-          ylo = (float)ylo64;
-          // 1/2 - wlim bounds |y - (f T_SFT - Bw)| for every decided track of the warp; add the
-          // roundings of ylo (FP32, and FP64 below 1e-6 for |10^-3.5 T_SFT| < 2^29)
-          mf = (0.5f - wlim) + fabsf(ylo) * 2.4e-7f + 1e-6f;
-          cutm = inbox;
-          zt = __any_sync(0xffffffffu, zt);
-          zin = __fsub_rd(1.f, mz);
-          zex = __fadd_ru(1.f, mz);
-          win = __fadd_ru(1e-13f, mw);
-          wex = __fsub_rd(1e-13f, mw);
-          fin = __fadd_ru(ylo, mf);
-          fex = __fsub_rd(ylo, mf);
-        }
-        // the warp's coefficient box, one coefficient at a time (few live registers)
-        float* rb = red + (ltile & 1) * kConsWarps * RW + cwarp * RW;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-          float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            if ((inbox >> r) & 1u) {
-              lo = fminf(lo, get(c2[r / 2][k], r & 1));
-              hi = fmaxf(hi, get(c2[r / 2][k], r & 1));
-            }
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-          }
-          if (lane == 0) {
-            rb[k] = lo;
-            rb[KP + k] = hi;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
-          bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-        }
-        if (lane == 0) {
-          reinterpret_cast<int*>(rb)[2 * KP] = bmin;
-          reinterpret_cast<int*>(rb)[2 * KP + 1] = bmax;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tile_ready[ltile & 1]);
+      if (CUTS) {
+        const float mz = wi.mz, mw = wi.mw, ylo = wi.ylo;
+        // 1/2 - wlim bounds |y - (f T_SFT - Bw)| for every decided track of the warp; add the
+        // roundings of ylo (FP32, and FP64 below 1e-6 for |10^-3.5 T_SFT| < 2^29)
+        const float mf = (0.5f - wlim) + fabsf(ylo) * 2.4e-7f + 1e-6f;
+        cutm = inboxm[ctid];
+        zt = wi.zt != 0;
+        zin = __fsub_rd(1.f, mz);
+        zex = __fadd_ru(1.f, mz);
+        win = __fadd_ru(1e-13f, mw);
+        wex = __fsub_rd(1e-13f, mw);
+        fin = __fadd_ru(ylo, mf);
+        fex = __fsub_rd(ylo, mf);
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(pro_free);
       const f32x2 kC2 = f2pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23 in both lanes
       // -------------------------------------------------------------- segments, a slot at a time
       const unsigned nin = (unsigned)(J.n_bin + 2 * m);
