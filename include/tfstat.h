@@ -479,6 +479,19 @@ int tfs_set_wait_limit(int64_t limit_ns, int hold);
  * 8 KB plus 4 bytes per 4096 elements) is allocated stream-ordered per call. */
 int tfs_topk(const float* val_in, int64_t N, int k, int64_t* idx, float* val, int mem, void* stream);
 
+/* ---- step 5 over many arrays at once ---------------------------------------
+ * The top-k of n independent arrays (paper Sec. II.D keeps the best walkers of
+ * every data chunk): vals[i] [Ns[i]] device floats, ks[i] in [0, 1024] (0 or
+ * Ns[i] = 0 skips array i), idx[i] / val[i] device outputs of min(ks[i], Ns[i])
+ * entries, each exactly what tfs_topk gives for that array alone (same order,
+ * ties, -0 and NaN rules).  The host arrays vals, Ns, ks, idx, val (n entries)
+ * are read during the call.  One set of 13 kernel launches covers up to 64
+ * arrays (more take one set per 64), instead of 13 per array.  Device scratch
+ * (about 600 KB plus 4 bytes per 4096 elements) is stream-ordered; the call
+ * returns without waiting unless stream is NULL. */
+int tfs_topk_batch(const float* const* vals, const int64_t* Ns, const int* ks, int n, int64_t* const* idx,
+                   float* const* val, void* stream);
+
 /* ---- top-k that allocates nothing -----------------------------------------
  * The paper has no counterpart; this is a service for callers that must not
  * allocate device memory themselves or through the library: for example a

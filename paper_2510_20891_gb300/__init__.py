@@ -553,3 +553,27 @@ def topk(values, k: int, stream=None):
     val = np.empty(kk, dtype=np.float32)
     check(lib().tfs_topk(_ptr(v), v.size, k, _ptr(idx), _ptr(val), MEM_HOST, None))
     return idx, val
+
+
+def topk_batch(arrays, ks, stream=None):
+    """Top-k of many CUDA float32 arrays at once (tfs_topk_batch): one set of passes covers up to
+    64 arrays; returns [(idx, val), ...], each equal to topk() of that array alone."""
+    torch = _torch()
+    n = len(arrays)
+    outs = []
+    vals = (ctypes.c_void_p * max(n, 1))()
+    Ns = (ctypes.c_int64 * max(n, 1))()
+    kk = (ctypes.c_int * max(n, 1))()
+    oi = (ctypes.c_void_p * max(n, 1))()
+    ov = (ctypes.c_void_p * max(n, 1))()
+    for i, (a, k) in enumerate(zip(arrays, ks)):
+        if not (_is_torch_cuda(a) and a.dtype == torch.float32 and a.is_contiguous()):
+            raise ValueError("topk_batch takes contiguous CUDA float32 tensors")
+        m = min(int(k), a.numel())
+        idx = torch.empty(m, dtype=torch.int64, device=a.device)
+        val = torch.empty(m, dtype=torch.float32, device=a.device)
+        outs.append((idx, val))
+        vals[i], Ns[i], kk[i] = _ptr(a).value, a.numel(), int(k)
+        oi[i], ov[i] = _ptr(idx).value if m else None, _ptr(val).value if m else None
+    check(lib().tfs_topk_batch(vals, Ns, kk, n, oi, ov, _stream_ptr(stream)))
+    return outs

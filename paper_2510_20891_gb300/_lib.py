@@ -35,6 +35,7 @@ SIGNATURES = {
     "tfs_eval_bins": (I, [P, P, P, P, I64, I, P, I, P]),
     "tfs_kernel_launches": (ctypes.c_longlong, []),
     "tfs_topk_noalloc": (I, [P, I64, I, P, P, P]),
+    "tfs_topk_batch": (I, [P, P, P, I, P, P, P]),
     "tfs_eval_batch": (I, [P, I, P, P]),
     "tfs_autotune_batch": (I, [P, I, I, P, P, P, P]),
     "tfs_set_wait_limit": (I, [I64, I]),

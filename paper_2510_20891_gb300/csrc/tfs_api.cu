@@ -806,11 +806,14 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
     if (rc) return rc;
   }
   size_t need = round256(8) + round256(4) + round256(8) + round256(4);
-  size_t ws_max = 0;
+  std::vector<TopkTask> tasks;  // every job's top-k, selected together after the statistic
   for (int i = 0; i < n_jobs; ++i) {
     if (!jobs[i].stat) need += round256((size_t)jobs[i].N * 4);
-    if (jobs[i].topk > 0 && jobs[i].N > 0) ws_max = std::max(ws_max, topk_workspace_bytes(jobs[i].N));
+    if (jobs[i].topk > 0 && jobs[i].N > 0)
+      tasks.push_back(TopkTask{nullptr, jobs[i].N, (int)std::min<int64_t>(jobs[i].topk, jobs[i].N), jobs[i].top_idx,
+                               jobs[i].top_val});
   }
+  const size_t ws_max = tasks.empty() ? 0 : topk_batch_workspace_bytes(tasks.data(), (int)tasks.size());
   need += round256(ws_max);
   Arena ar;
   int rc = ar.init(need, st);
@@ -860,11 +863,12 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
   TFS_CHECK(g_dbg_last[0] == 0, TFS_ERR_CUDA, "debug self-check failed %llu times, first at site %llu (%lld, %lld)",
             g_dbg_last[0], g_dbg_last[1], (long long)g_dbg_last[2], (long long)g_dbg_last[3]);
 #endif
-  // top-k per job, one after another on the stream (they share the scratch)
-  for (int i = 0; i < n_jobs; ++i) {
-    const tfs_job& j = jobs[i];
-    if (j.topk == 0 || j.N == 0) continue;
-    rc = topk_device(ej[i].stat, j.N, (int)std::min<int64_t>(j.topk, j.N), j.top_idx, j.top_val, ws, st);
+  // every job's top-k in one set of passes (kTkJobs jobs per set)
+  if (!tasks.empty()) {
+    size_t ti = 0;
+    for (int i = 0; i < n_jobs; ++i)
+      if (jobs[i].topk > 0 && jobs[i].N > 0) tasks[ti++].val = ej[i].stat;
+    rc = topk_batch_device(tasks.data(), (int)tasks.size(), ws, st);
     if (rc) return rc;
   }
   if (!dev_status) {
@@ -1019,6 +1023,32 @@ int tfs_tuning_load(const char* path) {
 int tfs_tuning_clear(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+  return TFS_OK;
+}
+
+int tfs_topk_batch(const float* const* vals, const int64_t* Ns, const int* ks, int n, int64_t* const* idx,
+                   float* const* val, void* stream) {
+  clear_error();
+  TFS_CHECK(n >= 0 && n <= 65536, TFS_ERR_INVALID_ARG, "need 0 <= n <= 65536 arrays");
+  if (n == 0) return TFS_OK;
+  TFS_CHECK(vals && Ns && ks && idx && val, TFS_ERR_INVALID_ARG, "null argument");
+  std::vector<TopkTask> tasks;
+  for (int i = 0; i < n; ++i) {
+    TFS_CHECK(Ns[i] >= 0 && Ns[i] < ((int64_t)1 << 31), TFS_ERR_INVALID_ARG, "array %d: N must be in [0, 2^31)", i);
+    TFS_CHECK(ks[i] >= 0 && ks[i] <= 1024, TFS_ERR_INVALID_ARG, "array %d: k must be in [0, 1024]", i);
+    if (Ns[i] == 0 || ks[i] == 0) continue;
+    TFS_CHECK(vals[i] && idx[i] && val[i], TFS_ERR_INVALID_ARG, "array %d: null pointer", i);
+    tasks.push_back(TopkTask{vals[i], Ns[i], (int)std::min<int64_t>(ks[i], Ns[i]), idx[i], val[i]});
+  }
+  if (tasks.empty()) return TFS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arena ar;
+  const size_t wsb = topk_batch_workspace_bytes(tasks.data(), (int)tasks.size());
+  int rc = ar.init(round256(wsb), st);
+  if (rc) return rc;
+  rc = topk_batch_device(tasks.data(), (int)tasks.size(), ar.take<char>(wsb), st);
+  if (rc) return rc;
+  if (st == nullptr) TFS_CUDA(cudaStreamSynchronize(st));
   return TFS_OK;
 }
 

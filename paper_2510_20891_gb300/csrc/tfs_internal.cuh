@@ -186,6 +186,19 @@ void set_eval_wait(uint64_t ns, int hold);
 size_t topk_workspace_bytes(int64_t N);
 int topk_device(const float* val, int64_t N, int k, int64_t* idx_out, float* val_out, void* ws, cudaStream_t st);
 
+// top-k of many arrays at once (one set of passes over all of them; each result equals
+// topk_device on that array alone); scratch from topk_batch_workspace_bytes
+constexpr int kTkJobs = 64;  // arrays per pass set (more are done in groups)
+struct TopkTask {
+  const float* val;
+  int64_t N;
+  int k;
+  int64_t* idx_out;
+  float* val_out;
+};
+size_t topk_batch_workspace_bytes(const TopkTask* tasks, int n);
+int topk_batch_device(const TopkTask* tasks, int n, void* ws, cudaStream_t st);
+
 // quantise an FP64 device table P [n_seg][n_bin] (row pitch `ld`) into a table's storage
 int quantise_into(const double* P, int64_t ld, tfs_table* t, cudaStream_t st);
 

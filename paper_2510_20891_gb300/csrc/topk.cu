@@ -264,3 +264,279 @@ extern "C" int tfs_topk_noalloc(const float* val_in, int64_t N, int k, int64_t* 
   const int kk = (int)std::min<int64_t>(k, N);
   return topk_device(val_in, N, kk, idx, val, ws, static_cast<cudaStream_t>(stream));
 }
+
+// ---------------------------------------------------------------- segmented top-k over many jobs
+// The same selection for up to kTkJobs independent arrays at once (the per-chunk top-k of a batched
+// statistic launch, paper Sec. II.D keeping the best walkers of every chunk): every pass covers all
+// jobs, so a batch takes 13 launches whatever its number of jobs, and each job's result is that of
+// topk_device on the job alone (same passes, same order), bit for bit.
+namespace tfs {
+namespace {
+
+struct TkJob {
+  const float* v;
+  long long N;
+  int64_t* idx;
+  float* val;
+  int k;
+  int nch;  // chunks of kChunk elements
+};
+struct TkArgs {
+  TkJob jobs[kTkJobs];
+  long long chunk0[kTkJobs + 1];  // first chunk of each job in the flattened chunk list
+  int n;
+  // scratch: hist [n][256], state [n], cand [n][1024], cnt [total chunks]
+  uint32_t* hist;
+  TopkState* state;
+  unsigned long long* cand;
+  uint32_t* cnt;
+};
+
+__device__ __forceinline__ int tk_job_of(const TkArgs& a, long long chunk) {
+  int lo = 0, hi = a.n - 1;  // the last job whose first chunk is <= chunk
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.chunk0[mid] <= chunk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void tkb_init(const __grid_constant__ TkArgs a) {
+  const int j = blockIdx.x;
+  if (threadIdx.x == 0) {
+    TopkState& s = a.state[j];
+    s.prefix = 0;
+    s.mask = 0;
+    s.krem = (uint32_t)a.jobs[j].k;
+    s.ngt = 0;
+  }
+  a.hist[j * 256 + threadIdx.x] = 0;
+}
+
+// one CTA per chunk of one job (flattened over all jobs)
+__global__ void tkb_hist(const __grid_constant__ TkArgs a, int shift) {
+  __shared__ uint32_t h[256];
+  const int j = tk_job_of(a, blockIdx.x);
+  const TkJob& J = a.jobs[j];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t prefix = a.state[j].prefix, mask = a.state[j].mask;
+  const long long base = (long long)(blockIdx.x - a.chunk0[j]) * kChunk;
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    const long long i = base + t;
+    if (i < J.N) {
+      const uint32_t key = mono_key(J.v[i]);
+      if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&a.hist[j * 256 + threadIdx.x], h[threadIdx.x]);
+}
+
+// one CTA of 256 threads per job: pick the digit that holds the job's k_rem-th largest key
+__global__ void tkb_select(const __grid_constant__ TkArgs a, int shift) {
+  __shared__ uint32_t suf[257];
+  const int j = blockIdx.x;
+  uint32_t* hist = a.hist + j * 256;
+  TopkState* s = a.state + j;
+  const int d = threadIdx.x;
+  suf[d] = hist[d];
+  if (d == 0) suf[256] = 0;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const uint32_t add = (d + o < 256) ? suf[d + o] : 0u;
+    __syncthreads();
+    suf[d] += add;
+    __syncthreads();
+  }
+  const uint32_t krem = s->krem;
+  const uint32_t above = suf[d + 1];
+  __syncthreads();
+  if (above < krem && krem <= suf[d]) {
+    s->prefix |= (uint32_t)d << shift;
+    s->mask |= 255u << shift;
+    s->krem = krem - above;
+  }
+  hist[d] = 0;
+}
+
+__global__ void tkb_eqcount(const __grid_constant__ TkArgs a) {
+  __shared__ uint32_t tot;
+  const int j = tk_job_of(a, blockIdx.x);
+  const TkJob& J = a.jobs[j];
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  const uint32_t kstar = a.state[j].prefix;
+  const long long base = (long long)(blockIdx.x - a.chunk0[j]) * kChunk;
+  uint32_t c = 0;
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    const long long i = base + t;
+    if (i < J.N && mono_key(J.v[i]) == kstar) ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&tot, c);
+  __syncthreads();
+  if (threadIdx.x == 0) a.cnt[blockIdx.x] = tot;
+}
+
+// one CTA of 1024 threads per job: exclusive scan of the job's chunk counts
+__global__ void tkb_scan(const __grid_constant__ TkArgs a) {
+  __shared__ uint32_t part[1024];
+  const int j = blockIdx.x;
+  uint32_t* cnt = a.cnt + a.chunk0[j];
+  const int n = a.jobs[j].nch;
+  const int per = (n + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < n) sum += cnt[b0 + i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t add = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < n) {
+      const uint32_t c = cnt[b0 + i];
+      cnt[b0 + i] = run;
+      run += c;
+    }
+}
+
+__global__ void tkb_collect(const __grid_constant__ TkArgs a) {
+  __shared__ uint32_t wsum[kChunkThreads / 32];
+  const int j = tk_job_of(a, blockIdx.x);
+  const TkJob& J = a.jobs[j];
+  TopkState* s = a.state + j;
+  unsigned long long* cand = a.cand + (size_t)j * 1024;
+  const uint32_t kstar = s->prefix;
+  const uint32_t need = s->krem;
+  const uint32_t ngt = (uint32_t)J.k - need;
+  const long long chunk = blockIdx.x - a.chunk0[j];
+  const long long base = chunk * kChunk + (long long)threadIdx.x * kPer;
+  uint32_t myeq = 0;
+  for (int q = 0; q < kPer; ++q) {
+    const long long i = base + q;
+    if (i < J.N && mono_key(J.v[i]) == kstar) ++myeq;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = myeq;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  uint32_t woff = 0;
+  for (int w = 0; w < warp; ++w) woff += wsum[w];
+  uint32_t rank = a.cnt[blockIdx.x] + woff + x - myeq;
+  for (int q = 0; q < kPer; ++q) {
+    const long long i = base + q;
+    if (i >= J.N) break;
+    const uint32_t key = mono_key(J.v[i]);
+    const unsigned long long comp = ((unsigned long long)key << 32) | (0xffffffffull - (unsigned long long)i);
+    if (key > kstar) {
+      const uint32_t pos = atomicAdd(&s->ngt, 1u);
+      if (pos < ngt) cand[pos] = comp;
+    } else if (key == kstar) {
+      if (rank < need) cand[ngt + rank] = comp;
+      ++rank;
+    }
+  }
+}
+
+// one CTA of 1024 threads per job: bitonic sort of its k candidates, descending
+__global__ void tkb_sort(const __grid_constant__ TkArgs a) {
+  __shared__ unsigned long long x[1024];
+  const int j = blockIdx.x;
+  const TkJob& J = a.jobs[j];
+  const unsigned long long* cand = a.cand + (size_t)j * 1024;
+  const int t = threadIdx.x;
+  x[t] = t < J.k ? cand[t] : 0ull;
+  __syncthreads();
+  for (int size = 2; size <= 1024; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int p = t ^ stride;
+      if (p > t) {
+        const bool desc = (t & size) == 0;
+        const unsigned long long u = x[t], w = x[p];
+        if (desc ? (u < w) : (u > w)) {
+          x[t] = w;
+          x[p] = u;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (t < J.k) {
+    const long long i = (long long)(0xffffffffull - (x[t] & 0xffffffffull));
+    const bool ok = i >= 0 && i < J.N;
+    J.idx[t] = ok ? i : -1;
+    J.val[t] = ok ? J.v[i] : __int_as_float(0x7fc00000);
+  }
+}
+
+}  // namespace
+
+size_t topk_batch_workspace_bytes(const TopkTask* tasks, int n) {
+  size_t chunks = 0;
+  for (int i = 0; i < n; ++i) chunks += (size_t)((tasks[i].N + kChunk - 1) / kChunk);
+  const size_t per_group = (size_t)kTkJobs * (256 * 4 + sizeof(TopkState) + 1024 * 8);
+  return per_group + chunks * 4 + 256;
+}
+
+int topk_batch_device(const TopkTask* tasks, int n, void* ws, cudaStream_t st) {
+  // groups of up to kTkJobs jobs; the scratch of one group is reused by the next (stream order)
+  char* w = static_cast<char*>(ws);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(w);
+  TopkState* state = reinterpret_cast<TopkState*>(w + (size_t)kTkJobs * 256 * 4);
+  unsigned long long* cand =
+      reinterpret_cast<unsigned long long*>(w + (size_t)kTkJobs * (256 * 4 + sizeof(TopkState)));
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(w + (size_t)kTkJobs * (256 * 4 + sizeof(TopkState) + 1024 * 8));
+  int g0 = 0;
+  while (g0 < n) {
+    TkArgs a;
+    a.n = 0;
+    a.chunk0[0] = 0;
+    a.hist = hist;
+    a.state = state;
+    a.cand = cand;
+    a.cnt = cnt;
+    int g = g0;
+    for (; g < n && a.n < kTkJobs; ++g) {
+      const TopkTask& T = tasks[g];
+      if (T.N <= 0 || T.k <= 0) continue;
+      TkJob& J = a.jobs[a.n];
+      J.v = T.val;
+      J.N = T.N;
+      J.idx = T.idx_out;
+      J.val = T.val_out;
+      J.k = (int)std::min<int64_t>(T.k, T.N);
+      J.nch = (int)((T.N + kChunk - 1) / kChunk);
+      a.chunk0[a.n + 1] = a.chunk0[a.n] + J.nch;
+      ++a.n;
+    }
+    g0 = g;
+    if (a.n == 0) continue;
+    const unsigned chunks = (unsigned)a.chunk0[a.n];
+    tkb_init<<<a.n, 256, 0, st>>>(a);
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      tkb_hist<<<chunks, kChunkThreads, 0, st>>>(a, shift);
+      tkb_select<<<a.n, 256, 0, st>>>(a, shift);
+    }
+    tkb_eqcount<<<chunks, kChunkThreads, 0, st>>>(a);
+    tkb_scan<<<a.n, 1024, 0, st>>>(a);
+    tkb_collect<<<chunks, kChunkThreads, 0, st>>>(a);
+    tkb_sort<<<a.n, 1024, 0, st>>>(a);
+    count_launch(13);
+    TFS_CUDA(cudaGetLastError());
+  }
+  return TFS_OK;
+}
+
+}  // namespace tfs

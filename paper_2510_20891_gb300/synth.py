@@ -299,3 +299,43 @@ def served_requests(n: int, rate_hz: float, n_datasets: int, seed: int = 0,
     dt = rng.integers(0, len(dtypes), n)
     return [(float(t[i]), int(ds[i]), int(N[i]), dtypes[int(dt[i])]) for i in range(n)]
 
+
+
+def make_strain_device(w: Workload, seed: int, snr: float = 30.0):
+    """The same draw as ``make_strain`` for a coloured-noise workload (noise of the workload's PSD
+    plus one power-law harmonic at the given SNR), made on the current CUDA device with torch so
+    that many long datasets can be drawn quickly: Philox normal draws stand in for PCG64's (not
+    the same numbers; the same distributions and structure).  Returns (device strain, injection)."""
+    import torch
+
+    assert w.psd == "oneyear", "make_strain_device draws the one-year PSD's noise"
+    dev = torch.device("cuda")
+    n, dt = w.n_samples, w.dt
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    nf = n // 2 + 1
+    f = torch.arange(nf, dtype=torch.float64, device=dev) / (n * dt)
+    s = 1e-40 * (1.0 + (2e-3 / f.clamp_min(1e-300)) ** 4) * (1.0 + (f / 2.5e-2) ** 2)
+    s[0] = 0.0
+    var = s * (n / (2.0 * dt))
+    sd = torch.sqrt(var / 2.0)
+    X = torch.complex(sd * torch.randn(nf, generator=g, dtype=torch.float64, device=dev),
+                      sd * torch.randn(nf, generator=g, dtype=torch.float64, device=dev))
+    X[0] = 0.0
+    if n % 2 == 0:
+        X[-1] = torch.sqrt(var[-1]) * torch.randn(1, generator=g, dtype=torch.float64, device=dev)[0]
+    del f, s, var, sd
+    x = torch.fft.irfft(X, n=n)
+    del X
+    rng = np.random.default_rng(seed)
+    f0, tau, p = powerlaw_params(1, rng, tau_yr=w.tau_yr)
+    f0, tau, p = float(f0[0]), float(tau[0]), float(p[0])
+    t = torch.arange(n, dtype=torch.float64, device=dev) * dt
+    u = 1.0 - t / tau
+    fr = f0 * u ** (-p)
+    shape = (fr / f0) ** (2.0 / 3.0)
+    # SNR^2 = int a^2 / S_n(f(t)) dt (rectangle rule), as powerlaw_amplitude_for_snr
+    sn = 1e-40 * (1.0 + (2e-3 / fr) ** 4) * (1.0 + (fr / 2.5e-2) ** 2)
+    a0 = snr / math.sqrt(float(torch.sum(shape * shape / sn)) * dt)
+    x += a0 * shape * torch.cos(2.0 * math.pi * f0 * tau / (1.0 - p) * (1.0 - u ** (1.0 - p)))
+    return x, dict(kind="powerlaw", f0=f0, tau=tau, p=p, snr=snr, a0=a0)

@@ -223,3 +223,63 @@ def test_table_save_and_load_round_trip(T, tmp_path):
         a = T.eval_stat(table, basis, c, f, m=1).stat
         b = T.eval_stat(back, basis, c, f, m=1).stat
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_topk_batch_equals_each_array_alone(T):
+    """The segmented top-k (tfs_topk_batch): 70 arrays (two pass sets) of ragged sizes across the
+    4096-element chunks, with NaN, -0, -inf and heavy ties; each result is the oracle's top-k of
+    that array and, bit for bit, tfs_topk's result on the array alone."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(61)
+    sizes = [0, 1, 2, 5, 4095, 4096, 4097, 8191, 12288, 100000, 1000003] * 6 + [3, 70000, 1, 4096]
+    ks = [int(rng.choice([0, 1, 7, 128, 1024])) for _ in sizes]
+    arrs, hosts = [], []
+    for n in sizes:
+        v = rng.integers(0, 40, n).astype(np.float32) * 0.25
+        if n > 20:
+            v[rng.choice(n, 5, replace=False)] = np.nan
+            v[rng.choice(n, 5, replace=False)] = -0.0
+            v[rng.choice(n, 3, replace=False)] = -np.inf
+        hosts.append(v)
+        arrs.append(torch.from_numpy(v).cuda())
+    outs = T.topk_batch(arrs, ks)
+    torch.cuda.synchronize()
+    assert len(outs) == len(sizes)
+    for v, a, k, (idx, val) in zip(hosts, arrs, ks, outs):
+        m = min(k, v.size)
+        assert idx.numel() == m and val.numel() == m
+        if m == 0:
+            continue
+        ri, rv = O.topk(v.astype(np.float64), m)
+        assert np.array_equal(idx.cpu().numpy(), ri)
+        assert np.array_equal(val.cpu().numpy().astype(np.float64), rv, equal_nan=True)
+        i1, v1 = T.topk(a, m)
+        assert np.array_equal(i1.cpu().numpy(), idx.cpu().numpy())
+        assert np.array_equal(v1.cpu().numpy().view(np.uint32), val.cpu().numpy().view(np.uint32))
+
+
+def test_batch_of_64_jobs_launches_few_kernels(T):
+    """A 64-job batched call with a top-k per job: one statistic launch and one set of 13
+    top-k passes (not 13 per job), each job's top-k the top of its own statistic."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(62)
+    table, basis, U = _dataset(T, rng, 40, 600, 1.0e4, "f32", 4)
+    jobs = []
+    for i in range(64):
+        N = int(rng.integers(1, 3000))
+        c, f = _tracks(rng, N, 4, 40, 600, 1.0e4)
+        jobs.append(T.Job(table, basis, torch.tensor(c, device="cuda"), torch.tensor(f, device="cuda"), m=1,
+                          topk=int(rng.integers(1, 40))))
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    T.eval_batch(jobs, dev_status=status)  # warm: cached per-segment data and window sums
+    torch.cuda.synchronize()
+    k0 = T.lib().tfs_kernel_launches()
+    T.eval_batch(jobs, dev_status=status)
+    torch.cuda.synchronize()
+    launches = T.lib().tfs_kernel_launches() - k0
+    assert int(status.item()) == 0
+    assert launches <= 16, launches
+    for j in jobs:
+        s = j.stat.cpu().numpy().astype(np.float64)
+        ri, _ = O.topk(s, j.topk)
+        assert np.array_equal(j.top_idx.cpu().numpy(), ri)
