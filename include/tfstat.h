@@ -250,22 +250,27 @@ int tfs_eval_batch(const tfs_job* jobs, int n_jobs, int* dev_status, void* strea
  * pcap is the number of window sums of one segment's band staged per tile
  * (wider bands are cut to it and their pairs outside it take the slower exact
  * path); tile_div (1, 2, 4 or 8) divides the tracks per tile (smaller tiles:
- * more of them, better balance for small jobs).  Zeros select the defaults
- * (group 32, slots 2, pcap 2048, tile_div 1).  tfs_autotune_batch evaluates
+ * more of them, better balance for small jobs); tile_class picks the tracks
+ * each consumer thread carries (1: the large class, 12 for K <= 6; 2: the small
+ * class, 4 for K <= 8, whose tiles are a third as large; 0: automatic, the
+ * small class when a launch has fewer tracks than one round of large tiles
+ * over the SMs).  Zeros select the defaults (group 32, slots 2, pcap 2048,
+ * tile_div 1, automatic tile class).  tfs_autotune_batch evaluates
  * `jobs` (as tfs_eval_batch, overwriting their outputs) under candidate shapes,
- * `reps` times each, by coordinate descent from the default shape (each axis
- * in turn, two passes, a move must gain 0.5%), and keeps the fastest for every
+ * `reps` times each, by coordinate descent from the default shape (each of the
+ * five axes in turn, two passes, a move must gain 0.5%), and keeps the fastest for every
  * launch of this kind (coefficient slots, widest row and longest job in powers
  * of two, single job or batch); later tfs_eval_stat / tfs_eval_batch calls of
  * that kind use it.  best_ms and default_ms (either may be NULL) receive the
  * time per call of the chosen and of the default shape.  Synchronous.  The
  * choices live in the process; save and load them as a small JSON object
- * {"key": [pcap, tile_div, slots, group], ...}. */
+ * {"key": [pcap, tile_div, slots, group, tile_class], ...}. */
 typedef struct tfs_tuning {
   int32_t pcap;
   int32_t tile_div;
   int32_t slots;
   int32_t group;
+  int32_t tile_class;
 } tfs_tuning;
 
 int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* best, double* best_ms,

@@ -438,7 +438,7 @@ def _job_array(jobs):
 
 
 def autotune(jobs, reps: int = 3, stream=None):
-    """Choose the statistic kernel's launch shape for `jobs` by coordinate descent over its four
+    """Choose the statistic kernel's launch shape for `jobs` by coordinate descent over its five
     axes and keep it for launches of this kind (tfs_autotune_batch); returns
     ({"pcap": .., "tile_div": .., "slots": .., "group": ..}, ms per batch, ms per batch with the
     default shape)."""
@@ -448,7 +448,8 @@ def autotune(jobs, reps: int = 3, stream=None):
     ms0 = ctypes.c_double()
     check(lib().tfs_autotune_batch(arr, len(jobs), int(reps), ctypes.byref(best), ctypes.byref(ms),
                                    ctypes.byref(ms0), _stream_ptr(stream)))
-    return {"pcap": best.pcap, "tile_div": best.tile_div, "slots": best.slots, "group": best.group}, ms.value, ms0.value
+    return ({"pcap": best.pcap, "tile_div": best.tile_div, "slots": best.slots, "group": best.group,
+             "tile_class": best.tile_class}, ms.value, ms0.value)
 
 
 def set_wait_limit(limit_ns: int = 0, hold: bool = False):

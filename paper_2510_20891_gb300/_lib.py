@@ -70,7 +70,7 @@ class TfsTuning(ctypes.Structure):
     """struct tfs_tuning (include/tfstat.h)."""
 
     _fields_ = [("pcap", ctypes.c_int32), ("tile_div", ctypes.c_int32), ("slots", ctypes.c_int32),
-                ("group", ctypes.c_int32)]
+                ("group", ctypes.c_int32), ("tile_class", ctypes.c_int32)]
 
 
 class TfsServerStats(ctypes.Structure):

@@ -7,6 +7,7 @@
 // (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014)
 // keyed by a seed and an iteration number kept on the device, so that a captured graph of one
 // iteration draws afresh on every replay.
+#include <algorithm>
 #include <cstdint>
 
 #include "tfs_internal.cuh"
@@ -42,12 +43,12 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-// One block: every thread reads the iteration number, the block draws for all walkers, and
-// thread 0 advances the number after the block's last read.
-__global__ void de_draw_kernel(uint64_t seed, int32_t* __restrict__ iter, int64_t n, int W, float f_lo, float f_hi,
-                               int32_t* __restrict__ r1, int32_t* __restrict__ r2, float* __restrict__ F) {
+// Every block reads the iteration number and draws for its walkers; a second one-thread kernel
+// advances the number afterwards (stream order), so that a replayed graph draws afresh each time.
+__global__ void de_draw_kernel(uint64_t seed, const int32_t* __restrict__ iter, int64_t n, int W, float f_lo,
+                               float f_hi, int32_t* __restrict__ r1, int32_t* __restrict__ r2, float* __restrict__ F) {
   const uint64_t it = (uint64_t)(uint32_t)iter[0];
-  for (int64_t g = threadIdx.x; g < n; g += blockDim.x) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = 3u * (it * (uint64_t)n + (uint64_t)g);
     const uint64_t z0 = splitmix64_at(seed, k + 1u), z1 = splitmix64_at(seed, k + 2u), z2 = splitmix64_at(seed, k + 3u);
     const int64_t c0 = g - g % W, t = g % W;
@@ -59,10 +60,8 @@ __global__ void de_draw_kernel(uint64_t seed, int32_t* __restrict__ iter, int64_
     const float u = (float)(uint32_t)(z2 >> 40) * 0x1p-24f;  // [0, 1), exact
     F[g] = __fadd_rn(f_lo, __fmul_rn(__fsub_rn(f_hi, f_lo), u));
   }
-  __syncthreads();
-  if (threadIdx.x == 0) iter[0] = (int32_t)(it + 1u);
 }
-
+__global__ void de_advance_kernel(int32_t* __restrict__ iter) { iter[0] = (int32_t)((uint32_t)iter[0] + 1u); }
 __global__ void de_accept_kernel(double* __restrict__ c, float* __restrict__ s, const double* __restrict__ ct,
                                  const float* __restrict__ st, const int32_t* __restrict__ in_prior, int64_t N,
                                  int K) {
@@ -119,8 +118,10 @@ extern "C" int tfs_de_draw(uint64_t seed, int32_t* iter, int64_t n_chunks, int W
   const int64_t n = n_chunks * (int64_t)W;
   TFS_CHECK(n == 0 || (r1 && r2 && F), TFS_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  de_draw_kernel<<<1, 1024, 0, st>>>(seed, iter, n, W, f_lo, f_hi, r1, r2, F);
-  count_launch();
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024));
+  de_draw_kernel<<<blocks, 256, 0, st>>>(seed, iter, n, W, f_lo, f_hi, r1, r2, F);
+  de_advance_kernel<<<1, 1, 0, st>>>(iter);
+  count_launch(2);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TFS_OK : cuda_fail(e, "de_draw");
 }

@@ -46,7 +46,7 @@ static __global__ void sum_parts_kernel(const __grid_constant__ PartArgs p) {
 // Tracks that one round of full tiles over all SMs holds (a single job's launch cuts its
 // tracks into whole rounds of equal tiles of at most this many tracks per SM).
 long long eval_round_tracks(int KP, bool cuts, int tile_div) {
-  const long long R = cuts ? r_of_kp_cuts(KP) : r_of_kp(KP);
+  const long long R = r_of(KP, cuts, false);
   return (long long)kCons * R / std::max(1, std::min(tile_div, 8)) * sm_count();
 }
 
@@ -55,7 +55,17 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   int KP = 0;
   for (int i = 0; i < L.n_jobs; ++i) KP = std::max(KP, L.jobs[i].sp->KP);
   const bool cuts = L.jobs[0].cuts != 0;
-  const int R = cuts ? r_of_kp_cuts(KP) : r_of_kp(KP);
+  // tracks per consumer thread: the small class when the launch holds less than one round of
+  // large tiles (tuning: 1 large, 2 small, 0 automatic); the verification launch keeps the large
+  bool bins = false;
+  long long n_all = 0;
+  for (int i = 0; i < L.n_jobs; ++i) {
+    bins = bins || L.jobs[i].bins_out != nullptr;
+    n_all += L.jobs[i].N;
+  }
+  const bool small = !bins && (tune.rsel == 2 ||
+                               (tune.rsel == 0 && n_all < (long long)sm_count() * kCons * r_of(KP, cuts, false)));
+  const int R = r_of(KP, cuts, small);
   const int nsp = segrow_floats(KP, cuts);
 
   EvalArgs<MJ> a{};
@@ -71,7 +81,6 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   const long long tile = (long long)kCons * R / std::max(1, std::min(tune.tile_div, 8));
   long long nt = 0;
   int seg_max = 0, qpitch_max = 0;
-  bool bins = false;
   for (int i = 0; i < L.n_jobs; ++i) {
     const EvalJob& E = L.jobs[i];
     const tfs_table* tb = E.table;
@@ -120,7 +129,6 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     nt += tt > 0 ? (E.N + tt - 1) / tt : 0;
     seg_max = std::max(seg_max, (int)tb->n_seg);
     qpitch_max = std::max(qpitch_max, D.qpitch);
-    bins = bins || E.bins_out != nullptr;
   }
   if (nt == 0) return TFS_OK;
   // Few track tiles (small jobs): split each job's segments over several tiles so that every
@@ -224,12 +232,12 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   }
   int rc;
   switch (KP) {
-    case 2: rc = launch_kp<2, MJ>(a, bins, cuts, grid, smem, st); break;
-    case 4: rc = launch_kp<4, MJ>(a, bins, cuts, grid, smem, st); break;
-    case 6: rc = launch_kp<6, MJ>(a, bins, cuts, grid, smem, st); break;
-    case 8: rc = launch_kp<8, MJ>(a, bins, cuts, grid, smem, st); break;
-    case 16: rc = launch_kp<16, MJ>(a, bins, cuts, grid, smem, st); break;
-    case 32: rc = launch_kp<32, MJ>(a, bins, cuts, grid, smem, st); break;
+    case 2: rc = launch_kp<2, MJ>(a, bins, cuts, small, grid, smem, st); break;
+    case 4: rc = launch_kp<4, MJ>(a, bins, cuts, small, grid, smem, st); break;
+    case 6: rc = launch_kp<6, MJ>(a, bins, cuts, small, grid, smem, st); break;
+    case 8: rc = launch_kp<8, MJ>(a, bins, cuts, small, grid, smem, st); break;
+    case 16: rc = launch_kp<16, MJ>(a, bins, cuts, small, grid, smem, st); break;
+    case 32: rc = launch_kp<32, MJ>(a, bins, cuts, small, grid, smem, st); break;
     default:
       set_error("unsupported coefficient slot count %d", KP);
       rc = TFS_ERR_INVALID_ARG;

@@ -194,41 +194,52 @@ __device__ __forceinline__ void report_tie(const EvalArgs<MJ>& a, long long t, i
   }
 }
 
-// FP64 frequency of track t at segment seg in the oracle's operation order.
-__device__ __forceinline__ double track_freq(const JobDesc& J, long long t, int seg) {
-  double f = J.f_ref ? J.f_ref[t] : 0.0;
-  const double* c = J.coeffs + t * (long long)J.K;
-  for (int k = 0; k < J.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], J.U[(size_t)k * J.n_seg + seg]));
-  return f;
-}
-
-// Segment exclusions of (track t, segment seg) in FP64, in the oracle's operation order
-// (finite differences of the track at the segment midpoints; see segment_validity there).
-static __device__ __noinline__ bool segment_excluded(const JobDesc& J, long long t, int seg, double f) {
-  const int n = J.n_seg;
-  const double T = J.T;
-  double fd = 0.0, z = 0.0;
-  if (n >= 2) {
-    if (seg == 0) fd = __ddiv_rn(__dsub_rn(track_freq(J, t, 1), f), T);
-    else if (seg == n - 1) fd = __ddiv_rn(__dsub_rn(f, track_freq(J, t, n - 2)), T);
-    else fd = __ddiv_rn(__dsub_rn(track_freq(J, t, seg + 1), track_freq(J, t, seg - 1)), __dmul_rn(2.0, T));
-  }
-  if (n >= 3) {
-    const int cc = seg == 0 ? 1 : (seg == n - 1 ? n - 2 : seg);
-    const double fc = cc == seg ? f : track_freq(J, t, cc);
-    const double dd = __dadd_rn(__dsub_rn(track_freq(J, t, cc + 1), __dmul_rn(2.0, fc)), track_freq(J, t, cc - 1));
-    z = __dmul_rn(dd, __ddiv_rn(T, 6.0));
-  }
-  return z > 1.0 || f < kFLowHz || fd < kFdotLow;
-}
-
 // FP64 bin of (track t, segment seg) of job J in the oracle's operation order, and its window
-// sum from the window-sum array in global memory (0 for an excluded segment when CUTS).
-template <bool BINS, bool CUTS, int MJ>
+// sum from the window-sum array in global memory.  With CUTS the segment exclusions are decided
+// first, in FP64 in the oracle's operation order, from the track's frequencies at the segments its
+// finite differences use (0 for an excluded segment).  (Loading every operand up front and keeping
+// the function out of line made the pair loop spill: 2.84 -> 5.4 ms on the one-year launch.)
+template <int KP, bool BINS, bool CUTS, int MJ>
 __device__ float exact_pair(const EvalArgs<MJ>& a, const JobDesc& J, long long t, int seg) {
   if (!dbg_ok(a.dbg, t >= 0 && t < J.N && seg >= 0 && seg < J.n_seg, 1, t, seg)) return 0.f;
-  const double f = track_freq(J, t, seg);
-  if (CUTS && segment_excluded(J, t, seg, f)) return 0.f;
+  double f;
+  if (!CUTS) {
+    f = J.f_ref ? J.f_ref[t] : 0.0;
+    const double* c = J.coeffs + t * (long long)J.K;
+    for (int k = 0; k < J.K; ++k) f = __dadd_rn(f, __dmul_rn(c[k], J.U[(size_t)k * J.n_seg + seg]));
+  } else {
+    // the frequencies at the (at most three) segments s0 .. s0 + 2 that the finite differences
+    // use, in one pass over the coefficients (each sum in the oracle's order: f_ref, then the K
+    // products left to right): one memory wait per coefficient rather than per segment
+    const int n = J.n_seg;
+    const double T = J.T;
+    const int s0 = n >= 3 ? min(max(seg - 1, 0), n - 3) : 0;
+    const int n3 = min(n, 3);
+    const double fr = J.f_ref ? J.f_ref[t] : 0.0;
+    double fs[3] = {fr, fr, fr};
+    const double* c = J.coeffs + t * (long long)J.K;
+    for (int k = 0; k < J.K; ++k) {
+      const double ck = c[k];
+      const double* u = J.U + (size_t)k * n + s0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < n3) fs[i] = __dadd_rn(fs[i], __dmul_rn(ck, u[i]));
+    }
+    auto F = [&](int s) { return fs[s - s0]; };
+    f = F(seg);
+    double fd = 0.0, z = 0.0;
+    if (n >= 2) {
+      if (seg == 0) fd = __ddiv_rn(__dsub_rn(F(1), f), T);
+      else if (seg == n - 1) fd = __ddiv_rn(__dsub_rn(f, F(n - 2)), T);
+      else fd = __ddiv_rn(__dsub_rn(F(seg + 1), F(seg - 1)), __dmul_rn(2.0, T));
+    }
+    if (n >= 3) {
+      const int cc = seg == 0 ? 1 : (seg == n - 1 ? n - 2 : seg);
+      const double dd = __dadd_rn(__dsub_rn(F(cc + 1), __dmul_rn(2.0, F(cc))), F(cc - 1));
+      z = __dmul_rn(dd, __ddiv_rn(T, 6.0));
+    }
+    if (z > 1.0 || f < kFLowHz || fd < kFdotLow) return 0.f;
+  }
   const double x = __dmul_rn(f, J.T);
   int* bo = BINS ? J.bins_out + t * (long long)J.n_seg + seg : nullptr;
   if (!isfinite(x)) {
@@ -844,7 +855,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
               const uint32_t e = queue[i * kCons + ctid];
               const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
               {
-              const float y = exact_pair<BINS, CUTS>(a, J, tile0 + ctid + r2 * kCons, s2);
+              const float y = exact_pair<KP, BINS, CUTS>(a, J, tile0 + ctid + r2 * kCons, s2);
               const float x = corr[r2 * kCons + ctid];
               const float sm = x + y, yv = sm - x;
               corrl[r2 * kCons + ctid] += (x - (sm - yv)) + (y - yv);
@@ -1064,7 +1075,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         const uint32_t e = queue[i * kCons + ctid];
         const int r2 = (int)(e & 31u), s2 = (int)(e >> 5);
         {
-              const float y = exact_pair<BINS, CUTS>(a, J, tile0 + ctid + r2 * kCons, s2);
+              const float y = exact_pair<KP, BINS, CUTS>(a, J, tile0 + ctid + r2 * kCons, s2);
               const float x = corr[r2 * kCons + ctid];
               const float sm = x + y, yv = sm - x;
               corrl[r2 * kCons + ctid] += (x - (sm - yv)) + (y - yv);
@@ -1113,9 +1124,16 @@ inline int sm_count() {
   return n;
 }
 
-inline int r_of_kp(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 4 : 2)); }
-// with segment cuts each track also carries the two cut forms: fewer tracks per thread
-inline int r_of_kp_cuts(int KP) { return KP <= 6 ? 8 : (KP <= 8 ? 6 : 2); }
+// Tracks per consumer thread: the large classes fill the registers (no spills at any K); the small
+// class (4 for K <= 8) serves launches with fewer tracks than one round of large tiles, whose large
+// tiles would be mostly empty slots that still cost their per-segment arithmetic.
+constexpr int r_big(int KP) { return KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 4 : 2)); }
+constexpr int r_big_cuts(int KP) { return KP <= 6 ? 8 : (KP <= 8 ? 6 : 2); }
+constexpr int r_small(int KP) { return KP <= 8 ? 4 : r_big(KP); }
+constexpr int r_small_cuts(int KP) { return KP <= 8 ? 4 : r_big_cuts(KP); }
+inline int r_of(int KP, bool cuts, bool small) {
+  return small ? (cuts ? r_small_cuts(KP) : r_small(KP)) : (cuts ? r_big_cuts(KP) : r_big(KP));
+}
 
 template <int KP, int R, bool BINS, bool CUTS, int MJ>
 int launch_one(const EvalArgs<MJ>& a0, int grid, size_t smem, cudaStream_t st) {
@@ -1135,19 +1153,21 @@ int launch_one(const EvalArgs<MJ>& a0, int grid, size_t smem, cudaStream_t st) {
 
 // Launch the kernel instantiation for KP coefficient slots (one translation unit per KP pair).
 template <int KP, int MJ>
-int launch_kp(const EvalArgs<MJ>& a, bool bins, bool cuts, int grid, size_t smem, cudaStream_t st) {
-  constexpr int RV = KP <= 6 ? 12 : (KP <= 8 ? 9 : (KP <= 16 ? 4 : 2));
-  constexpr int RC = KP <= 6 ? 8 : (KP <= 8 ? 6 : 2);
-  if (cuts) return launch_one<KP, RC, false, true, MJ>(a, grid, smem, st);
-  if constexpr (MJ == 1) {
-    if (bins) return launch_one<KP, RV, true, false, MJ>(a, grid, smem, st);
+int launch_kp(const EvalArgs<MJ>& a, bool bins, bool cuts, bool small, int grid, size_t smem, cudaStream_t st) {
+  if (small && r_small(KP) != r_big(KP)) {
+    if (cuts) return launch_one<KP, r_small_cuts(KP), false, true, MJ>(a, grid, smem, st);
+    return launch_one<KP, r_small(KP), false, false, MJ>(a, grid, smem, st);
   }
-  return launch_one<KP, RV, false, false, MJ>(a, grid, smem, st);
+  if (cuts) return launch_one<KP, r_big_cuts(KP), false, true, MJ>(a, grid, smem, st);
+  if constexpr (MJ == 1) {
+    if (bins) return launch_one<KP, r_big(KP), true, false, MJ>(a, grid, smem, st);
+  }
+  return launch_one<KP, r_big(KP), false, false, MJ>(a, grid, smem, st);
 }
 
 #define TFS_DECLARE_KP(KPV)                                                                            \
-  extern template int launch_kp<KPV, 1>(const EvalArgs<1>&, bool, bool, int, size_t, cudaStream_t);  \
-  extern template int launch_kp<KPV, kMaxJobs>(const EvalArgs<kMaxJobs>&, bool, bool, int, size_t, cudaStream_t);
+  extern template int launch_kp<KPV, 1>(const EvalArgs<1>&, bool, bool, bool, int, size_t, cudaStream_t);  \
+  extern template int launch_kp<KPV, kMaxJobs>(const EvalArgs<kMaxJobs>&, bool, bool, bool, int, size_t, cudaStream_t);
 TFS_DECLARE_KP(2)
 TFS_DECLARE_KP(4)
 TFS_DECLARE_KP(6)
@@ -1157,7 +1177,7 @@ TFS_DECLARE_KP(32)
 #undef TFS_DECLARE_KP
 
 #define TFS_INSTANTIATE_KP(KPV)                                                                 \
-  template int launch_kp<KPV, 1>(const EvalArgs<1>&, bool, bool, int, size_t, cudaStream_t); \
-  template int launch_kp<KPV, kMaxJobs>(const EvalArgs<kMaxJobs>&, bool, bool, int, size_t, cudaStream_t);
+  template int launch_kp<KPV, 1>(const EvalArgs<1>&, bool, bool, bool, int, size_t, cudaStream_t); \
+  template int launch_kp<KPV, kMaxJobs>(const EvalArgs<kMaxJobs>&, bool, bool, bool, int, size_t, cudaStream_t);
 
 }  // namespace tfs

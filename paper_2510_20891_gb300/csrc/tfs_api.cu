@@ -264,7 +264,7 @@ int launch_eval(const EvalLaunch& L, const EvalTuning& tune_in, cudaStream_t st)
   if (g_force_tuning) {
     tune = *g_force_tuning;
     g_last_keys.push_back(key);
-  } else if (tune.cap == 0 && tune.tile_div == 0 && tune.slots == 0 && tune.group == 0) {
+  } else if (tune.cap == 0 && tune.tile_div == 0 && tune.slots == 0 && tune.group == 0 && tune.rsel == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
@@ -272,6 +272,7 @@ int launch_eval(const EvalLaunch& L, const EvalTuning& tune_in, cudaStream_t st)
       tune.tile_div = it->second.tile_div;
       tune.slots = it->second.slots;
       tune.group = it->second.group;
+      tune.rsel = it->second.tile_class;
     }
   }
   return launch_eval_shape(L, tune, st);
@@ -935,14 +936,15 @@ int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* be
   static const int slots[] = {2, 3, 4, 6, 8};
   static const int caps[] = {512, 1024, 2048, 3072, 4096};
   static const int divs[] = {1, 2, 4, 8};
+  static const int classes[] = {1, 2};
   for (int pass = 0; pass < 2 && rc == TFS_OK; ++pass) {
     bool moved = false;
-    for (int axis = 0; axis < 4 && rc == TFS_OK; ++axis) {
-      const int* vals = axis == 0 ? groups : axis == 1 ? slots : axis == 2 ? caps : divs;
-      const int nv = axis == 3 ? 4 : 5;
+    for (int axis = 0; axis < 5 && rc == TFS_OK; ++axis) {
+      const int* vals = axis == 0 ? groups : axis == 1 ? slots : axis == 2 ? caps : axis == 3 ? divs : classes;
+      const int nv = axis == 3 ? 4 : (axis == 4 ? 2 : 5);
       for (int i = 0; i < nv && rc == TFS_OK; ++i) {
         EvalTuning t = cur;
-        int& f = axis == 0 ? t.group : axis == 1 ? t.slots : axis == 2 ? t.cap : t.tile_div;
+        int& f = axis == 0 ? t.group : axis == 1 ? t.slots : axis == 2 ? t.cap : axis == 3 ? t.tile_div : t.rsel;
         if (f == vals[i]) continue;
         f = vals[i];
         std::vector<std::string> k2;
@@ -962,7 +964,7 @@ int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* be
   cudaFree(d_status);
   if (rc == TFS_ERR_INVALID_ARG) set_error("the default launch shape does not fit these jobs");
   if (rc != TFS_OK) return rc;
-  const tfs_tuning win{cur.cap, cur.tile_div, cur.slots, cur.group};
+  const tfs_tuning win{cur.cap, cur.tile_div, cur.slots, cur.group, cur.rsel};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const std::string& k : keys) g_tune[k] = win;
@@ -982,8 +984,8 @@ int tfs_tuning_save(const char* path) {
   fprintf(f, "{\n");
   size_t i = 0;
   for (const auto& kv : g_tune)
-    fprintf(f, "  \"%s\": [%d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second.pcap, kv.second.tile_div,
-            kv.second.slots, kv.second.group, ++i < g_tune.size() ? "," : "");
+    fprintf(f, "  \"%s\": [%d, %d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second.pcap, kv.second.tile_div,
+            kv.second.slots, kv.second.group, kv.second.tile_class, ++i < g_tune.size() ? "," : "");
   fprintf(f, "}\n");
   fclose(f);
   return TFS_OK;
@@ -1005,13 +1007,14 @@ int tfs_tuning_load(const char* path) {
     const size_t end = txt.find('"', pos + 1);
     if (end == std::string::npos) break;
     const std::string key = txt.substr(pos + 1, end - pos - 1);
-    int cap = 0, div = 0, ns = 0, grp = 0;
-    const int got_n = sscanf(txt.c_str() + end + 1, " : [%d , %d , %d , %d]", &cap, &div, &ns, &grp);
-    if (got_n != 4 || cap < 0 || cap > (1 << 20) || div < 0 || div > 8 || ns < 0 || ns > 8 || grp < 0 || grp > 32) {
+    int cap = 0, div = 0, ns = 0, grp = 0, cls = 0;
+    const int got_n = sscanf(txt.c_str() + end + 1, " : [%d , %d , %d , %d , %d]", &cap, &div, &ns, &grp, &cls);
+    if (got_n != 5 || cap < 0 || cap > (1 << 20) || div < 0 || div > 8 || ns < 0 || ns > 8 || grp < 0 || grp > 32 ||
+        cls < 0 || cls > 2) {
       set_error("malformed tuning entry for %s", key.c_str());
       return TFS_ERR_INVALID_ARG;
     }
-    got[key] = tfs_tuning{cap, div, ns, grp};
+    got[key] = tfs_tuning{cap, div, ns, grp, cls};
     pos = txt.find(']', end);
     if (pos == std::string::npos) break;
   }

@@ -169,6 +169,7 @@ struct EvalTuning {       // launch shape; zeros select defaults
   int tile_div = 0;       // tiles of (consumer threads x R) / tile_div tracks at most
   int slots = 0;          // staging slots (ring depth)
   int group = 0;          // segments per staging slot at most (one hand-off per slot)
+  int rsel = 0;           // tracks per consumer thread: 0 automatic, 1 the large class, 2 the small class
 };
 constexpr int kMaxJobs = 64;  // jobs per statistic launch (larger batches are split)
 int launch_eval(const EvalLaunch& L, const EvalTuning& tune, cudaStream_t st);

@@ -120,6 +120,7 @@ class DESearch:
         self.cuts = segment_cuts  # the paper's exclusions (Sec. II.B, II.D)
         self.statistic = statistic  # "nearest" (nearest-bin power sums) or "chirp" (the paper's S_alpha)
         self.uncounted_launches = 0  # kernels of graph replays beyond the captured one (set by run)
+        self.t_setup = self.t_iter = 0.0  # wall seconds of the last run's set-up and iterations
 
     def _initial(self, U_chunk):
         """n_init candidates uniform in the prior box, each track shifted by a constant so that
@@ -184,6 +185,8 @@ class DESearch:
             check(L.tfs_de_accept(c.data_ptr(), st.data_ptr(), ct.data_ptr(), s_trial.data_ptr(), inp.data_ptr(),
                                   n, K, sp))
 
+        self.t_setup = time.perf_counter() - t0  # initial population, its selection, buffers
+        t_it = time.perf_counter()
         if n_iter > 0:
             side.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(side):
@@ -208,6 +211,7 @@ class DESearch:
             if int(status.item()) != 0:
                 raise RuntimeError("a bounded device wait gave up during the search")
         torch.cuda.synchronize()
+        self.t_iter = time.perf_counter() - t_it  # the iterations (capture included), synchronised
         secs = time.perf_counter() - t0
         st_h = st.cpu().numpy().reshape(n_ch, W)
         c_h = c.cpu().numpy().reshape(n_ch, W, K)

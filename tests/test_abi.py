@@ -95,17 +95,17 @@ def test_host_validation_without_device(L):
 def test_tuning_cache_round_trip(L, tmp_path):
     """The tuner's cache: load a JSON object, save it back, reject malformed entries (host only)."""
     src = tmp_path / "tune.json"
-    src.write_text('{\n  "0:6:14:9:0": [1024, 2, 4, 16],\n  "1:8:12:12:1": [4096, 1, 8, 2]\n}\n')
+    src.write_text('{\n  "0:6:14:9:0": [1024, 2, 4, 16, 0],\n  "1:8:12:12:1": [4096, 1, 8, 2, 2]\n}\n')
     assert L.tfs_tuning_clear() == 0
     assert L.tfs_tuning_load(str(src).encode()) == 0
     out = tmp_path / "out.json"
     assert L.tfs_tuning_save(str(out).encode()) == 0
     import json
 
-    assert json.loads(out.read_text()) == {"0:6:14:9:0": [1024, 2, 4, 16], "1:8:12:12:1": [4096, 1, 8, 2]}
+    assert json.loads(out.read_text()) == {"0:6:14:9:0": [1024, 2, 4, 16, 0], "1:8:12:12:1": [4096, 1, 8, 2, 2]}
     bad = tmp_path / "bad.json"
-    for txt in ('{"0:6:14:9:0": [1024]}', '{"0:6:14:9:0": [1024, 2]}', '{"0:6:14:9:0": [1024, 2, 9, 16]}',
-                '{"0:6:14:9:0": [1024, 2, 4, 33]}'):
+    for txt in ('{"0:6:14:9:0": [1024]}', '{"0:6:14:9:0": [1024, 2, 4, 16]}', '{"0:6:14:9:0": [1024, 2, 9, 16, 0]}',
+                '{"0:6:14:9:0": [1024, 2, 4, 33, 0]}', '{"0:6:14:9:0": [1024, 2, 4, 32, 3]}'):
         bad.write_text(txt)
         assert L.tfs_tuning_load(str(bad).encode()) == -1
     assert L.tfs_tuning_load(str(tmp_path / "missing.json").encode()) == -6

@@ -197,6 +197,7 @@ def test_autotuned_launch_shape(T):
     shape, ms, ms0 = T.autotune(jobs, reps=2)
     assert shape["pcap"] in (512, 1024, 2048, 3072, 4096) and shape["tile_div"] in (1, 2, 4, 8) and ms > 0
     assert shape["slots"] in (2, 3, 4, 6, 8) and shape["group"] in (1, 4, 8, 16, 32) and 0 < ms <= ms0
+    assert shape["tile_class"] in (0, 1, 2)
     jobs2 = _batch(T, torch, data)
     for d, j in zip(data, jobs2):
         Pq, _ = d["table"].to_host()
@@ -283,3 +284,43 @@ def test_batch_of_64_jobs_launches_few_kernels(T):
         s = j.stat.cpu().numpy().astype(np.float64)
         ri, _ = O.topk(s, j.topk)
         assert np.array_equal(j.top_idx.cpu().numpy(), ri)
+
+
+def _force_tile_class(T, tmp_path, table, K, multi, cls, cuts=False):
+    """Load a tuning entry that forces the tile class of launches of this kind (the key the library
+    derives: table dtype, coefficient slots, log2 of the row pitch and of the segments, batch)."""
+    kp = next(v for v in (2, 4, 6, 8, 16, 32) if K <= v)
+    dt = {"f32": 0, "bf16": 1, "f16": 2, "f8e4m3": 3}[table.dtype]
+    row = (table.n_bin + 31) // 32 * 32
+    key = f"{dt}:{kp}:{math.ceil(math.log2(row))}:{math.ceil(math.log2(max(table.n_seg, 1)))}:{int(multi)}"
+    if cuts:
+        key += ":c"
+    path = tmp_path / "force.json"
+    path.write_text('{"%s": [0, 0, 0, 0, %d]}' % (key, cls))
+    T.lib().tfs_tuning_clear()
+    T.tuning_load(str(path))
+
+
+@pytest.mark.parametrize("dtype,K,m", [("f32", 3, 0), ("f32", 6, 1), ("bf16", 8, 3), ("f8e4m3", 5, 1), ("f16", 2, 2)])
+def test_both_tile_classes_match_the_oracle(T, tmp_path, dtype, K, m):
+    """The large (12 or 9 tracks per thread) and the small (4) tile classes give the same bins
+    and, within FP32 rounding of the sum (1e-6), the same statistic; both match the oracle."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(71 + K + m)
+    n_seg, n_bin, Tsft, N = 97, 1200, 2.0e4, 30000
+    table, basis, U = _dataset(T, rng, n_seg, n_bin, Tsft, dtype, K)
+    c, f = _tracks(rng, N, K, n_seg, n_bin, Tsft, 3)
+    Pq, _ = table.to_host()
+    S, *_ = O.eval_stat(Pq, U, c, f, Tsft, m, 0)
+    got = []
+    try:
+        for cls in (1, 2):
+            _force_tile_class(T, tmp_path, table, K, False, cls)
+            r = T.eval_stat(table, basis, c, f, m=m, ties_capacity=64)
+            assert O.stat_relative_error(r.stat.astype(np.float64), S) <= 1e-5
+            got.append(r)
+    finally:
+        T.lib().tfs_tuning_clear()
+    a, b = got
+    assert a.tie_count == b.tie_count
+    assert O.stat_relative_error(a.stat.astype(np.float64), b.stat.astype(np.float64)) <= 1e-6
