@@ -183,6 +183,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def chirp_flops_pair(M: int, P: int) -> int:
+    """FP32 work of the chirp statistic per (track, segment) pair: the M-point complex FFT of the
+    template (5 M log2 M), its M windowed samples (6 flops each) and the 2P + 1 complex products
+    with the data and norms (8 + 4 flops per bin)."""
+    return 5 * M * int(math.log2(M)) + 6 * M + 12 * (2 * P + 1)
+
+
 # --------------------------------------------------------------------------- CPU oracle arm
 _W = {}
 _THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
@@ -450,6 +457,15 @@ def run_ours(args):
         cpu = {"value": cpu_val, "unit": UNIT, "cores": ncores, "kind": "oracle",
                "sample": f"FP64 SFT of the full strain ({t_sft:.2f} s, 1 process) + statistic of {sample} tracks "
                          f"on {ncores} processes ({t_eval:.2f} s), scaled to {N} tracks per step"}
+        # the same oracle on one core (one single-threaded process), on a smaller sample
+        sample1 = max(1, sample // 16)
+        arm1 = OracleArm(x, psd, w, U, 1, cuts=args.segment_cuts)
+        t_sft1, t_eval1 = arm1.step(coeffs_h[:sample1])
+        arm1.close()
+        cpu["single_core"] = {"value": N / (t_sft1 + N * (t_eval1 / sample1)), "unit": UNIT, "cores": 1,
+                              "sample": f"FP64 SFT of the full strain ({t_sft1:.2f} s) + statistic of {sample1} "
+                                        f"tracks ({t_eval1:.2f} s) in one single-threaded process, scaled to {N} "
+                                        f"tracks per step"}
     stat_err = None
     if rank == 0 and args.stat_error > 0:
         import oracle.tfstat_oracle as O
@@ -585,10 +601,10 @@ def run_chirp(args):
         e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
 
-    # roofline: FP32 work per (track, segment) pair = the 512-point complex FFT of the template
+    # roofline: FP32 work per (track, segment) pair = the M-point complex FFT of the template
     # (5 M log2 M), the windowed samples (6 flops each) and the 2P + 1 complex products and norms
     # (8 + 4 flops per bin); peak = 152 SMs x 128 FP32 lanes x 2 flops x the sampled SM clock
-    flops_pair = 5 * 512 * 9 + 6 * 512 + 12 * (2 * P + 1)
+    flops_pair = chirp_flops_pair(T.CHIRP_M, P)
     achieved = N * w.n_seg * flops_pair / (kern_ms / 1e3) / 1e12
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
@@ -685,7 +701,7 @@ def run_tpl_search(args):
     pairs = W * sum(cs.sizes)
     bytes_batch = sum(W * (n * (2 * w.m + 1) * 4 + 8 * w.K + 4) for n in cs.sizes)
     if chirp:
-        flops_pair = 5 * 512 * 9 + 6 * 512 + 12 * (2 * T.CHIRP_P + 1)
+        flops_pair = chirp_flops_pair(T.CHIRP_M, T.CHIRP_P)
         achieved = pairs * flops_pair / (batch_ms / 1e3) / 1e12
         sm_mhz = 2070.0
         roof = {"bound": "alu", "achieved": achieved, "peak": 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "unit": "TFLOP/s",

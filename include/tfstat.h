@@ -407,9 +407,10 @@ int tfs_de_draw(uint64_t seed, int32_t* iter, int64_t n_chunks, int W, float f_l
  * S_n is not finite and positive left out); S_alpha = 0 when b itself lies
  * outside the table or no bin is left.
  * d~ is the Hann-windowed SFT of the strain (Sec. II.B); h~ the template's SFT,
- * evaluated as the Fourier integral of the windowed chirp at 512 points (equal
- * to the sampled SFT within 1e-7 of its peak for L >= 512, P <= 111 and
- * |fdot| T_sft^2 <= 100).  The paper uses P = 100 (TFS_CHIRP_P).
+ * evaluated as the Fourier integral of the windowed chirp at TFS_CHIRP_M = 256
+ * points (equal to the sampled SFT within about 1e-6 of its peak for P <= 111
+ * and |fdot| T_sft^2 <= 100: the aliasing of the Hann-windowed template's
+ * tails).  The paper uses P = 100 (TFS_CHIRP_P).
  *
  * tfs_build_chirp_table: strain [n] (host or device per mem, FP64), dt,
  * T_sft (L = T_sft/dt an even 2,3,5-smooth integer in [512, 2^20]), psd [L/2+1]
@@ -428,6 +429,7 @@ int tfs_de_draw(uint64_t seed, int32_t* iter, int64_t n_chunks, int W, float f_l
  * (scratch by cudaMallocAsync). */
 typedef struct tfs_ctable tfs_ctable; /* device-resident linear-chirp table */
 #define TFS_CHIRP_P 100
+#define TFS_CHIRP_M 256
 int tfs_build_chirp_table(const double* strain, int64_t n, double dt, double T_sft, const double* psd, int mem,
                           void* stream, tfs_ctable** out);
 int tfs_ctable_info(const tfs_ctable* t, int64_t* n_seg, int64_t* n_bin, double* T_sft, double* dt, double* s_ref);

@@ -261,6 +261,7 @@ class ChirpTable:
 
 
 CHIRP_P = 100  # TFS_CHIRP_P: the paper's 2P + 1 = 201 bins
+CHIRP_M = 256  # TFS_CHIRP_M: samples of the template's Fourier integral per segment
 
 
 def build_chirp_table(strain, dt: float, T_sft: float, psd, stream=None) -> ChirpTable:

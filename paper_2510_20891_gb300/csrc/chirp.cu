@@ -5,17 +5,18 @@
 // midpoint t_a and fdot its finite difference; S_alpha is |sum_k d~*_k h~_k / S_k|^2 over
 // sum_k |h~_k|^2 / S_k on the 2P + 1 bins around the nearest bin b, times 4 / (dt sum w^2).
 //
-// GB300 layout: one warp per track at a time, segments in order.  The track's frequency,
-// derivatives and bin are evaluated in FP64 in the oracle's operation order, 32 segments at
-// a time with one segment per lane (GB300's FP64 rate is a small fraction of FP32), so b is
-// bit-identical.  The template is the Fourier
-// integral of the Hann-windowed chirp over the segment, sampled at 512 points and
-// transformed by a warp-wide 512-point FFT (16 per lane, a lane-local 16-point DFT, a
-// shared-memory transpose, a second 16-point DFT and one radix-2 exchange between lane
-// pairs): with the Hann window the sampled transform equals the sampled SFT of the
-// template within aliasing of order 1 / (2 pi (512 - P - beta / 2)^3) of its peak.  The
-// scaled complex table (L2-resident) supplies the data bins; sums in FP32, S_alpha summed
-// over segments in FP64.
+// GB300 layout: one warp per track at a time.  The track's frequency, derivatives and bin
+// are evaluated in FP64 in the oracle's operation order, 32 segments at a time with one
+// segment per lane (GB300's FP64 rate is a small fraction of FP32), so b is bit-identical.
+// The template is the Fourier integral of the Hann-windowed chirp over the segment, sampled
+// at 256 points and transformed by a 256-point FFT on each half of the warp (16 samples per
+// lane, a lane-local 16-point DFT, twiddles, a transpose through shared memory and a second
+// lane-local 16-point DFT), so that the two halves take two segments of the track at once
+// (the segments the exclusions keep, packed in pairs).  With the Hann window the sampled
+// transform equals the sampled SFT of the template within aliasing of order
+// 1 / (2 pi (256 - P - beta / 2)^3) of its peak.  The scaled complex table (L2-resident)
+// supplies the data bins; sums in FP32, S_alpha summed over segments in FP64 (each half its
+// own segments, the two sums added at the end).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -26,10 +27,10 @@
 namespace tfs {
 namespace {
 
-constexpr int kM = 512;           // template samples per segment
+constexpr int kM = 256;           // template samples per segment
 constexpr int kCW = 8;            // warps per block
 constexpr int kCThreads = 32 * kCW;
-constexpr int kChirpPMax = 111;   // the output mapping covers |j| <= 111
+constexpr int kChirpPMax = 111;   // the outputs kept cover -112 <= j <= 111
 constexpr double kFLow = 0x1.4b96be9c2da2cp-12;  // 10^-3.5 Hz, the nearest double
 
 constexpr int kChirpMaxJobs = 64;  // jobs per launch
@@ -123,25 +124,26 @@ __device__ __forceinline__ double track_f(const ChirpJob& a, const double* c, do
   return f;
 }
 
-__global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_constant__ ChirpBatch B) {
-  __shared__ float s_win[kM];                 // sin^2(pi m / 512)
-  __shared__ float2 s_buf[kCW][16][33];       // per-warp transpose (padded rows)
+__global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_constant__ ChirpBatch B) {
+  __shared__ float s_win[kM];                 // sin^2(pi m / 256)
+  __shared__ float2 s_buf[kCW][2][16][17];    // per half-warp transpose (padded rows)
   __shared__ double s_c[kCW][32];             // the warp's track coefficients
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int hf = lane >> 4, l16 = lane & 15;  // half of the warp, lane within it
   for (int i = tid; i < kM; i += kCThreads) {
     const float s = sinpif((float)i / (float)kM);
     s_win[i] = s * s;
   }
-  // e^{-2 pi i lane j0 / 512}, j0 = 0..15 (exact arguments)
+  // e^{-2 pi i l16 j0 / 256}, j0 = 1..15 (exact arguments; j0 = 0 is 1)
   float2 tw[16];
+  tw[0] = make_float2(1.f, 0.f);
 #pragma unroll
-  for (int j0 = 0; j0 < 16; ++j0) {
+  for (int j0 = 1; j0 < 16; ++j0) {
     float sn, cs;
-    sincospif(-(float)(2 * lane * j0) / (float)kM, &sn, &cs);
+    sincospif(-(float)(2 * l16 * j0) / (float)kM, &sn, &cs);
     tw[j0] = make_float2(cs, sn);
   }
   __syncthreads();
-  const int h = lane & 1, j0p = lane >> 1;
   const long long nw = (long long)gridDim.x * kCW;
   int jb = 0;  // the job of the current track (tracks are visited in increasing order)
   for (long long gt = (long long)blockIdx.x * kCW + w; gt < B.start[B.n_jobs]; gt += nw) {
@@ -156,11 +158,18 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_cons
     __syncwarp();
     const double* c = s_c[w];
     const double fr = a.f_ref ? a.f_ref[t] : 0.0;
-    double sacc = 0.0;
+    // outputs j1 of this lane (j = l16 + 16 j1, less 256 from j1 = 9) with |j| <= P
+    unsigned pmask = 0u;
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) {
+      const int jj = l16 + 16 * j1 - (j1 >= 9 ? kM : 0);
+      if (j1 != 7 && j1 != 8 && jj >= -a.P && jj <= a.P) pmask |= 1u << j1;
+    }
+    double sacc = 0.0;  // this half's segments
     for (int al0 = 0; al0 < n; al0 += 32) {
       // lane s prepares segment al0 + s in FP64, in the oracle's operation order: its frequency
       // and neighbours, fdot by finite differences (one-sided at the ends), the bin, the cuts,
-      // and the FP32 phase parameters; the warp then takes the segments one by one
+      // and the FP32 phase parameters; the halves then take the kept segments two at a time
       const int sg = al0 + lane;
       bool p_skip = true;
       int p_b = 0;
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_cons
         if (!skip) {
           p_b = (int)bz;
           p_d2 = (float)(2.0 * __dsub_rn(x, bz));  // 2 delta0, delta0 in [-1/2, 1/2]
-          // beta = fdot T^2 split so that beta_hi * y^2 is exact in FP32 (7 + 16 significant bits)
+          // beta = fdot T^2 split so that beta_hi * y^2 is exact in FP32 (7 + 14 significant bits)
           const double beta = fd * T * T;
           double bh64 = 0.0;
           if (beta != 0.0 && isfinite(beta)) {
@@ -216,19 +225,25 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_cons
         }
         p_skip = skip;
       }
-      const int cnt = min(32, n - al0);
-      for (int sl = 0; sl < cnt; ++sl) {
-        if (__shfl_sync(0xffffffffu, (int)p_skip, sl)) continue;  // warp-uniform
-        const int al = al0 + sl;
-        const int b = __shfl_sync(0xffffffffu, p_b, sl);
-        const float d2 = __shfl_sync(0xffffffffu, p_d2, sl);
-        const float bh = __shfl_sync(0xffffffffu, p_bh, sl);
-        const float bl = __shfl_sync(0xffffffffu, p_bl, sl);
-        // samples m = lane + 32 i of g(y) = w(y) e^{i pi (2 delta0 y + beta y^2)}, y = m / 512 - 1/2
+      unsigned todo = __ballot_sync(0xffffffffu, !p_skip);  // the kept segments (warp-uniform)
+      while (todo) {
+        const int s0 = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int s1 = todo ? __ffs(todo) - 1 : -1;
+        if (s1 >= 0) todo &= todo - 1;
+        // half 0 takes segment s0, half 1 segment s1 (or repeats s0 without counting it)
+        const bool live = hf == 0 || s1 >= 0;
+        const int src = (hf && s1 >= 0) ? s1 : s0;
+        const int al = al0 + src;
+        const int b = __shfl_sync(0xffffffffu, p_b, src);
+        const float d2 = __shfl_sync(0xffffffffu, p_d2, src);
+        const float bh = __shfl_sync(0xffffffffu, p_bh, src);
+        const float bl = __shfl_sync(0xffffffffu, p_bl, src);
+        // samples m = l16 + 16 i of g(y) = w(y) e^{i pi (2 delta0 y + beta y^2)}, y = m / 256 - 1/2
         float2 v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int m = lane + 32 * i;
+          const int m = l16 + 16 * i;
           const int mc = m - kM / 2;
           const float y = (float)mc * (1.f / kM);
           const float q = (float)(mc * mc) * (1.f / (kM * kM));  // y^2, exact
@@ -243,39 +258,45 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_cons
           const float wv = s_win[m];
           v[i] = make_float2(wv * cs, wv * sn);
         }
-        // 512 = 16 (lane-local) x 32 (across lanes)
+        // 256 = 16 (lane-local, i) x 16 (across the half's lanes): output j0 + 16 j1 is
+        // sum_l W16^{l j1} W256^{l j0} sum_i v_l[i] W16^{i j0}
         dft16(v);
 #pragma unroll
-        for (int j0 = 0; j0 < 16; ++j0) s_buf[w][j0][lane] = c_mul(v[at16(j0)], tw[j0]);
+        for (int j0 = 0; j0 < 16; ++j0) s_buf[w][hf][j0][l16] = j0 ? c_mul(v[at16(j0)], tw[j0]) : v[0];
         __syncwarp();
 #pragma unroll
-        for (int qq = 0; qq < 16; ++qq) v[qq] = s_buf[w][j0p][2 * qq + h];
+        for (int l = 0; l < 16; ++l) v[l] = s_buf[w][hf][l16][l];
         __syncwarp();
-        dft16(v);  // E (even lanes) or O (odd lanes) of the 32-point DFT over the lanes
-        // radix-2 exchange: G[j0 + 16 j1] = E(j1) + W32^j1 O(j1) (j1 < 16), E - W32 O above.
-        // Even lanes produce j1 = 0..6 (j = j0 + 16 j1 <= 111), odd lanes j1 = 25..31 (j - 512 >= -112).
+        dft16(v);  // lane j0 = l16 now holds G[j0 + 16 j1] in v[at16(j1)]
+        // kept outputs: j1 = 0..6 (j = j0 + 16 j1 <= 111) and j1 = 9..15 (j - 256 >= -112), those
+        // with |j| <= P (the lane's mask) and, near the table's edges, inside it
+        const unsigned use = live ? pmask : 0u;
+        const float2* zb = a.z + (size_t)al * a.n_bin + b + l16;  // bin b + l16 of the segment's row
+        const float* wb = a.wt + b + l16;
         float re = 0.f, im = 0.f, nr = 0.f;
+        const auto acc = [&](const float2 G, const float2 zz, const float wv) {
+          re = fmaf(zz.x, G.x, fmaf(zz.y, G.y, re));
+          im = fmaf(zz.x, G.y, fmaf(-zz.y, G.x, im));
+          nr = fmaf(wv, fmaf(G.x, G.x, G.y * G.y), nr);
+        };
+        if (b >= 112 && b + 111 < a.n_bin) {  // every kept output lies in the table
 #pragma unroll
-        for (int s = 0; s < 7; ++s) {
-          const float2 lo = v[at16(s)], hi = v[at16(9 + s)];
-          const float2 send = h ? c_mul(w32(s), lo) : hi;
-          const float2 keep = h ? c_mul(w32(9 + s), hi) : lo;
-          float2 recv;
-          recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-          recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
-          const float2 G = h ? c_sub(recv, keep) : c_add(keep, recv);
-          const int jj = h ? j0p + 16 * (25 + s) - kM : j0p + 16 * s;
-          const int kb = b + jj;
-          if (jj >= -a.P && jj <= a.P && kb >= 0 && kb < a.n_bin) {
-            const float2 zz = a.z[(size_t)al * a.n_bin + kb];
-            const float wv = a.wt[kb];
-            re = fmaf(zz.x, G.x, fmaf(zz.y, G.y, re));
-            im = fmaf(zz.x, G.y, fmaf(-zz.y, G.x, im));
-            nr = fmaf(wv, fmaf(G.x, G.x, G.y * G.y), nr);
+          for (int j1 = 0; j1 < 16; ++j1) {
+            if (j1 == 7 || j1 == 8) continue;
+            const int o = 16 * j1 - (j1 >= 9 ? kM : 0);
+            if (use >> j1 & 1u) acc(v[at16(j1)], zb[o], wb[o]);
+          }
+        } else {
+#pragma unroll
+          for (int j1 = 0; j1 < 16; ++j1) {
+            if (j1 == 7 || j1 == 8) continue;
+            const int o = 16 * j1 - (j1 >= 9 ? kM : 0);
+            const int kb = b + l16 + o;
+            if ((use >> j1 & 1u) && kb >= 0 && kb < a.n_bin) acc(v[at16(j1)], zb[o], wb[o]);
           }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 8; o > 0; o >>= 1) {  // within the half
           re += __shfl_xor_sync(0xffffffffu, re, o);
           im += __shfl_xor_sync(0xffffffffu, im, o);
           nr += __shfl_xor_sync(0xffffffffu, nr, o);
@@ -283,7 +304,8 @@ __global__ void __launch_bounds__(kCThreads) chirp_stat_kernel(const __grid_cons
         if (nr > 0.f) sacc += (double)(fmaf(re, re, im * im) / nr);
       }
     }
-    if (lane == 0) a.stat[t] = (float)sacc;
+    const double tot = __shfl_sync(0xffffffffu, sacc, 0) + __shfl_sync(0xffffffffu, sacc, 16);
+    if (lane == 0) a.stat[t] = (float)tot;
   }
 }
 

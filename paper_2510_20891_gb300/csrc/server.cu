@@ -8,13 +8,15 @@
 // One worker thread per server owns all device work.  It keeps two batches in
 // flight on two streams: while one batch runs, arriving requests are admitted
 // (device buffers allocated, inputs uploaded) and launched as the next batch,
-// so work from different requests overlaps on the device.  Admission is FIFO:
+// so work from different requests overlaps on the device.  A second thread
+// watches the batches in flight and completes each as soon as its last kernel
+// has run, so that neither admission nor completion waits on the other.  Admission is FIFO:
 // a request waits until its input/output buffers, plus its dataset's table if
 // that is not resident, fit under the budget; idle tables (no admitted or
 // running request uses them) are evicted least recently used first to make
 // room (their bytes are kept in host memory and copied back on the next use).
-// Results are copied out by tfs_server_wait in the caller's thread, through pinned buffers
-// the server keeps (one per concurrent waiter).
+// Results are copied out by tfs_server_wait in the caller's thread, on one of the
+// server's copy streams (one per concurrent waiter).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -68,13 +70,10 @@ struct SrvReq {
   std::string err;
 };
 
-// A stream and a pinned buffer through which tfs_server_wait copies results out.  A copy into
-// pageable memory is staged by the driver, and under the worker's concurrent uploads (also
-// staged) a few MB took milliseconds; a pinned destination is a plain DMA.
-constexpr size_t kCopyChunk = (size_t)8 << 20;
+// A stream on which tfs_server_wait copies a request's results into the caller's memory
+// (all of them enqueued, then one synchronisation).
 struct CopySlot {
   cudaStream_t st = nullptr;
-  void* pinned = nullptr;
 };
 
 struct SrvBatch {
@@ -101,6 +100,10 @@ struct tfs_server {
   int64_t used = 0;  // resident tables + admitted/running/uncollected request buffers
   int64_t use_clock = 0;
   SrvBatch batch[2];
+  std::deque<SrvBatch*> inflight;    // launched batches, oldest first (completed by `completer`)
+  std::condition_variable cv_inflight;
+  std::thread completer;
+  bool stop_completer = false;
   std::mutex copy_mu;                // guards copy_free (slots are created on demand)
   std::vector<CopySlot*> copy_free, copy_all;
   std::thread worker;
@@ -304,28 +307,52 @@ void worker_main(tfs_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    bool progressed = false;
-    for (SrvBatch& b : s->batch) {
-      if (b.busy && cudaEventQuery(b.ev) != cudaErrorNotReady) {
-        finish_batch(s, b);
-        s->cv_done.notify_all();
-        progressed = true;
-      }
-    }
     if (s->stop && s->queue.empty() && !s->batch[0].busy && !s->batch[1].busy) break;
+    bool progressed = false;
     for (SrvBatch& b : s->batch) {
       if (!b.busy && !s->queue.empty()) {
         const size_t before = s->queue.size();
         launch(s, b, lk);
+        if (b.busy) {
+          s->inflight.push_back(&b);
+          s->cv_inflight.notify_one();
+        }
         progressed = progressed || s->queue.size() != before;
       }
     }
-    if (!progressed) {
-      if (s->batch[0].busy || s->batch[1].busy)
-        s->cv_work.wait_for(lk, std::chrono::microseconds(20));
-      else
-        s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    // submissions, completions, collected results and shutdown all notify cv_work
+    if (!progressed) s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+  }
+}
+
+// Completes batches as their events fire, whichever of the batches in flight ends first.  It polls
+// the events of a snapshot of the batches in flight without the lock (only this thread finishes a
+// batch, and a batch's event is recorded again only after it has been finished), taking the lock
+// again every 50 us to pick up batches launched meanwhile.
+void completer_main(tfs_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    while (s->inflight.empty() && !s->stop_completer) s->cv_inflight.wait(lk);
+    if (s->inflight.empty()) break;
+    const std::vector<SrvBatch*> v(s->inflight.begin(), s->inflight.end());
+    lk.unlock();
+    SrvBatch* done = nullptr;
+    const auto t0 = Clock::now();
+    while (!done && Clock::now() - t0 < std::chrono::microseconds(50)) {
+      for (SrvBatch* b : v)
+        if (cudaEventQuery(b->ev) != cudaErrorNotReady) {
+          done = b;
+          break;
+        }
+      if (!done) std::this_thread::yield();
     }
+    lk.lock();
+    if (!done) continue;
+    finish_batch(s, *done);
+    s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), done));
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();
   }
 }
 
@@ -358,6 +385,7 @@ int tfs_server_create(int64_t budget_bytes, int max_batch_jobs, tfs_server** out
     }
   }
   s->worker = std::thread(worker_main, s);
+  s->completer = std::thread(completer_main, s);
   *out = s;
   return TFS_OK;
 }
@@ -437,9 +465,7 @@ cudaError_t take_copy_slot(tfs_server* s, CopySlot** out) {
   }
   CopySlot* c = new CopySlot();
   cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, kCopyChunk);
   if (e != cudaSuccess) {
-    if (c->st) cudaStreamDestroy(c->st);
     delete c;
     return e;
   }
@@ -452,18 +478,6 @@ cudaError_t take_copy_slot(tfs_server* s, CopySlot** out) {
 void give_copy_slot(tfs_server* s, CopySlot* c) {
   std::lock_guard<std::mutex> g(s->copy_mu);
   s->copy_free.push_back(c);
-}
-
-// device -> caller's host memory through the slot's pinned buffer, a chunk at a time
-cudaError_t copy_out(CopySlot* c, void* dst, const void* src, size_t bytes) {
-  for (size_t o = 0; o < bytes; o += kCopyChunk) {
-    const size_t n = std::min(kCopyChunk, bytes - o);
-    cudaError_t e = cudaMemcpyAsync(c->pinned, static_cast<const char*>(src) + o, n, cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-    if (e != cudaSuccess) return e;
-    std::memcpy(static_cast<char*>(dst) + o, c->pinned, n);
-  }
-  return cudaSuccess;
 }
 
 }  // namespace
@@ -491,9 +505,13 @@ int tfs_server_wait(tfs_server* s, int64_t ticket, int timeout_ms, float* stat, 
     cudaSetDevice(s->device);
     CopySlot* c = nullptr;
     cudaError_t e = take_copy_slot(s, &c);
-    if (e == cudaSuccess && stat) e = copy_out(c, stat, r->d_stat, (size_t)r->N * 4);
-    if (e == cudaSuccess && r->topk && top_idx) e = copy_out(c, top_idx, r->d_ti, (size_t)r->topk * 8);
-    if (e == cudaSuccess && r->topk && top_val) e = copy_out(c, top_val, r->d_tv, (size_t)r->topk * 4);
+    if (e == cudaSuccess && stat)
+      e = cudaMemcpyAsync(stat, r->d_stat, (size_t)r->N * 4, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && r->topk && top_idx)
+      e = cudaMemcpyAsync(top_idx, r->d_ti, (size_t)r->topk * 8, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && r->topk && top_val)
+      e = cudaMemcpyAsync(top_val, r->d_tv, (size_t)r->topk * 4, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (c) {
       if (e == cudaSuccess) e = cudaFreeAsync(r->dev, c->st);
       else cudaFree(r->dev);
@@ -568,6 +586,12 @@ int tfs_server_free(tfs_server* s) {
     s->cv_work.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_completer = true;
+    s->cv_inflight.notify_all();
+  }
+  if (s->completer.joinable()) s->completer.join();
   for (auto& kv : s->reqs) {
     if (kv.second->dev) cudaFree(kv.second->dev);
     delete kv.second;
@@ -579,7 +603,6 @@ int tfs_server_free(tfs_server* s) {
   for (CopySlot* c : s->copy_all) {
     cudaStreamSynchronize(c->st);
     cudaStreamDestroy(c->st);
-    cudaFreeHost(c->pinned);
     delete c;
   }
   for (SrvBatch& b : s->batch) {

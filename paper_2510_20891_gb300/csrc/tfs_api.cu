@@ -922,7 +922,7 @@ int tfs_autotune_batch(const tfs_job* jobs, int n_jobs, int reps, tfs_tuning* be
     if (k_out) *k_out = g_last_keys;
     return (double)ms / reps;
   };
-  // coordinate descent over the four axes from the default shape, two passes; a move must gain
+  // coordinate descent over the five axes from the default shape, two passes; a move must gain
   // at least 0.5% so that timing noise does not wander
   EvalTuning cur;
   cur.cap = 2048;

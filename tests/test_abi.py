@@ -35,6 +35,18 @@ def test_binding_declares_exactly_the_header(L):
     assert set(_lib.SIGNATURES) == set(_lib.header_symbols())
 
 
+def test_binding_constants_equal_the_header():
+    import os
+    import re
+
+    import paper_2510_20891_gb300 as T
+
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "tfstat.h")).read()
+    defs = dict(re.findall(r"#define (TFS_[A-Z0-9_]+) (-?\d+)", hdr))
+    assert int(defs["TFS_CHIRP_P"]) == T.CHIRP_P
+    assert int(defs["TFS_CHIRP_M"]) == T.CHIRP_M
+
+
 def test_library_targets_sm103a(L):
     out = subprocess.run(["cuobjdump", "--list-elf", _lib.LIB_PATH], capture_output=True, text=True).stdout
     assert "sm_103a" in out

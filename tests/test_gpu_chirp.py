@@ -2,8 +2,9 @@
 against the FP64 oracle (``chirp_statistic``: the template's SFT as the L-point DFT of the
 sampled Hann-windowed chirp, every sum in FP64).
 
-The GPU evaluates the template as the Fourier integral of the windowed chirp at 512
-points (aliasing below 1e-7 of the template's peak), the data bins in FP32 and the sums in
+The GPU evaluates the template as the Fourier integral of the windowed chirp at 256
+points (aliasing below about 1e-7 of the template's peak for the drifts tested here, up to
+60 bins per segment), the data bins in FP32 and the sums in
 FP32 per segment, so the statistic agrees with the oracle within 2e-5 relative per track
 (max over tracks), stated here; the bins are the oracle's FP64 bins (made observable with
 P = 0 and tracks exactly on half-integer x).
