@@ -79,8 +79,43 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   a.hold = eval_hold();
   a.nsp = nsp;
   const long long tile = (long long)kCons * R / std::max(1, std::min(tune.tile_div, 8));
+  // A single job of more than one round of tiles whose last round would run on few SMs: its last
+  // tiles' segments are split over several tiles (whole 32-segment blocks each, partial sums
+  // added in segment order), so that the last round's work spreads over the SMs.  Two jobs of one
+  // launch: the full rounds, then the tail.  (Not with tie reports, whose track indices are those
+  // of one job, nor for the verification launch.)
+  if (MJ == 1 && L.n_jobs == 1 && !bins && L.tie_cap == 0 && L.jobs[0].split == 0) {
+    const EvalJob& E = L.jobs[0];
+    const long long sms = sm_count();
+    const long long ntj = (E.N + tile - 1) / tile;
+    const long long full = ntj / sms * sms, rem = ntj - full;
+    const int n_seg = (int)E.table->n_seg;
+    if (full > 0 && rem > 0) {
+      const int S = (int)std::min<long long>(8, sms / rem);
+      const int chunk = ((n_seg + S - 1) / std::max(S, 1) + kSegTile - 1) / kSegTile * kSegTile;
+      const int S2 = S >= 2 ? (n_seg + chunk - 1) / chunk : 1;
+      if (S2 >= 2) {
+        EvalJob J2[2] = {E, E};
+        const int64_t nA = full * tile;
+        J2[0].N = nA;
+        J2[1].N = E.N - nA;
+        J2[1].coeffs = E.coeffs + nA * E.basis->K;
+        J2[1].f_ref = E.f_ref ? E.f_ref + nA : nullptr;
+        J2[1].stat = E.stat + nA;
+        J2[1].split = S2;
+        J2[0].split = 1;
+        EvalLaunch L2 = L;
+        L2.jobs = J2;
+        L2.n_jobs = 2;
+        return launch_eval_jobs<kMaxJobs>(L2, tune, st);
+      }
+    }
+  }
   long long nt = 0;
   int seg_max = 0, qpitch_max = 0;
+  size_t part_floats = 0;
+  bool split_jobs = false;
+  for (int i = 0; i < L.n_jobs; ++i) split_jobs = split_jobs || L.jobs[i].split > 1;
   for (int i = 0; i < L.n_jobs; ++i) {
     const EvalJob& E = L.jobs[i];
     const tfs_table* tb = E.table;
@@ -125,8 +160,13 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     D.seg_split = 1;
     D.seg_chunk = (int)tb->n_seg;
     D.part = nullptr;
+    if (E.split > 1) {
+      D.seg_chunk = ((D.n_seg + E.split - 1) / E.split + kSegTile - 1) / kSegTile * kSegTile;
+      D.seg_split = (D.n_seg + D.seg_chunk - 1) / D.seg_chunk;
+      if (D.seg_split > 1) part_floats += (size_t)D.seg_split * D.N;
+    }
     a.tile_start[i] = (int)nt;
-    nt += tt > 0 ? (E.N + tt - 1) / tt : 0;
+    nt += (tt > 0 ? (E.N + tt - 1) / tt : 0) * D.seg_split;
     seg_max = std::max(seg_max, (int)tb->n_seg);
     qpitch_max = std::max(qpitch_max, D.qpitch);
   }
@@ -134,12 +174,12 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   // Few track tiles (small jobs): split each job's segments over several tiles so that every
   // SM gets work, at least 16 segments per tile; the tiles' partial sums are added in segment
   // order by a second small kernel.
-  size_t part_floats = 0;
   const long long sms_all = sm_count();
-  if (!bins && nt < sms_all) {
+  if (!bins && nt < sms_all && !split_jobs) {
     const int S = (int)std::min<long long>(8, sms_all / nt);
     if (S > 1) {
       nt = 0;
+      part_floats = 0;
       for (int i = 0; i < L.n_jobs; ++i) {
         JobDesc& D = a.jobs[i];
         const long long ntj = D.N > 0 ? (D.N + D.tile_tracks - 1) / D.tile_tracks : 0;

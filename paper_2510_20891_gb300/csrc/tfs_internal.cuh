@@ -153,6 +153,7 @@ struct EvalJob {          // one dataset's part of a statistic launch
   float* stat;            // device [N]
   int* bins_out = nullptr;  // device [N][n_seg] or null: the bin of every pair (verification only)
   int cuts = 0;           // apply the segment exclusions (TFS_JOB_SEGMENT_CUTS)
+  int split = 0;          // > 1: split every track tile's segments over this many tiles (a launch's tail)
 };
 struct EvalLaunch {
   const EvalJob* jobs;    // host array

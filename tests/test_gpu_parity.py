@@ -142,6 +142,29 @@ def test_table_rebuild_equals_build(T, tiny):
     assert np.array_equal(table.to_host()[0], fresh.to_host()[0])
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f8e4m3"])
+def test_statistic_after_rebuild_uses_the_new_strain(T, tiny, dtype):
+    """The statistic reads per-table window sums built on the first evaluation with each m: a
+    rebuild from new strain must refresh them (for every m used so far), so the statistic after
+    the rebuild equals that of a fresh table of the new strain and the oracle's."""
+    w = tiny["w"]
+    coeffs = synth.uniform_coeffs(3000, tiny["cmin"], tiny["cmax"], np.random.default_rng(11))
+    table = T.build_sfts(tiny["x"], w.dt, w.T_sft, tiny["psd"], "hann", dtype)
+    basis = T.basis_from_host(tiny["V"])
+    before = {m: T.eval_stat(table, basis, coeffs, None, m=m).stat for m in (1, 3)}
+    x2 = np.random.default_rng(12).standard_normal(w.n_samples)
+    x2 += synth.chirp_signal(w.n_samples, w.dt, 5.2e-3, 1e-9, 0.2)
+    T.check(T.lib().tfs_table_rebuild(table.handle, x2.ctypes.data, x2.size, 0, None))
+    fresh = T.build_sfts(x2, w.dt, w.T_sft, tiny["psd"], "hann", dtype)
+    Pq = fresh.to_host()[0]
+    for m in (1, 3):
+        got = T.eval_stat(table, basis, coeffs, None, m=m).stat
+        assert not np.array_equal(got, before[m])
+        assert np.array_equal(got, T.eval_stat(fresh, basis, coeffs, None, m=m).stat)
+        ref, *_ = O.eval_stat(Pq, tiny["V"], coeffs, np.zeros(len(coeffs)), w.T_sft, m, 0)
+        assert O.stat_relative_error(got, ref) <= STAT_TOL_SAME_TABLE
+
+
 def test_table_rebuild_host_strain_on_a_stream(T, tiny):
     """Host strain and a stream: the call returns once the strain has been copied (the buffer
     may be overwritten at once) and the transform completes on the stream."""
@@ -268,6 +291,36 @@ def test_eval_stat_full_size_sampled(T, oneyear):
     assert np.array_equal(res.top_idx.cpu().numpy(), gi)
     St, *_ = O.eval_stat(Pq, oneyear["V"], coeffs[gi], np.zeros(gi.size), w.T_sft, 1)
     assert O.stat_relative_error(res.top_val.cpu().numpy(), St) <= STAT_TOL_SAME_TABLE
+
+
+@pytest.mark.parametrize("extra", [1, 13 * 4608 - 5, 151 * 4608])
+def test_eval_stat_last_round_split(T, oneyear, extra):
+    """One round of full tiles over the SMs (152 x 384 x 12 tracks at K = 6) plus a tail: the
+    tail's tiles split their segments over several tiles (partial sums added in segment order)
+    so that the last round spreads over the SMs.  Tracks on both sides of the boundary, the
+    first ones and the last ones match the oracle and, within FP32 rounding of the sums, the
+    same tracks evaluated in a launch of their own."""
+    torch = pytest.importorskip("torch")
+    w = oneyear["w"]
+    full = 152 * 384 * 12
+    N = full + extra
+    rng = np.random.default_rng(27)
+    coeffs = synth.uniform_coeffs(N, oneyear["cmin"], oneyear["cmax"], rng)
+    table = T.table_from_power(oneyear["P64"], w.T_sft, "f32")
+    basis = T.basis_from_host(oneyear["V"])
+    dc = torch.from_numpy(coeffs).cuda()
+    res = T.eval_stat(table, basis, dc, None, m=1, topk=16)
+    torch.cuda.synchronize()
+    stat = res.stat.cpu().numpy()
+    pick = np.unique(np.concatenate([np.arange(0, 3000), np.arange(full - 3000, min(N, full + 3000)),
+                                     np.arange(max(0, N - 3000), N)]))
+    Pq, _ = O.quantise_table(oneyear["P64"], "f32")
+    S, *_ = O.eval_stat(Pq, oneyear["V"], coeffs[pick], np.zeros(pick.size), w.T_sft, 1)
+    assert O.stat_relative_error(stat[pick].astype(np.float64), S) <= STAT_TOL_SAME_TABLE
+    tail = T.eval_stat(table, basis, dc[full:], None, m=1).stat.cpu().numpy()
+    assert O.stat_relative_error(stat[full:].astype(np.float64), tail.astype(np.float64)) <= 1e-6
+    gi, _ = O.topk(stat.astype(np.float64), 16)
+    assert np.array_equal(res.top_idx.cpu().numpy(), gi)
 
 
 def test_eval_stat_full_size_host_chunks(T, oneyear):
