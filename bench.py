@@ -61,7 +61,7 @@ def parse():
                     help="apply the segment exclusions (second-order, low-frequency and low-fdot cuts)")
     ap.add_argument("--batch-jobs", type=int, default=64, help="datasets of the batched workload")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default launch shape")
-    ap.add_argument("--requests", type=int, default=1000, help="requests of the served workload")
+    ap.add_argument("--requests", type=int, default=2000, help="requests of the served workload")
     ap.add_argument("--rate", type=float, default=200.0, help="request arrival rate (Hz) of the served workload")
     ap.add_argument("--datasets", type=int, default=32, help="resident datasets of the served workload")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="device-memory budget of the served workload")
@@ -939,11 +939,12 @@ def run_served(args):
     todo = queue.Queue()
 
     def collect():
+        out = np.empty(max(r[2] for r in reqs), np.float32)  # this collector's result buffer, reused
         while True:
             i = todo.get()
             if i is None:
                 return
-            srv.wait(tickets[i], 600000)
+            srv.wait(tickets[i], 600000, stat=out)
             done_t[i] = time.perf_counter()
 
     n_coll = 16

@@ -321,8 +321,10 @@ int tfs_server_submit(tfs_server* s, int ds_id, const double* coeffs, const doub
 /* Wait for a ticket (timeout_ms < 0: no limit) and copy its results to host
  * stat [N], top_idx / top_val [min(topk, N)] (any may be NULL).  The statistic
  * is the one tfs_eval_stat gives within FP32 rounding (the bins are identical).
- * The results pass through a pinned buffer of the server (8 MB per concurrent
- * waiter, kept until tfs_server_free), so the destinations may be pageable.
+ * The copies run on a stream of the server (one per concurrent waiter, kept
+ * until tfs_server_free) straight into the destinations, pageable or pinned;
+ * stat's pages are written (zeros) on the host first, so that the device does
+ * not take page faults on memory that was never touched.
  * TFS_ERR_TIMEOUT leaves the ticket valid; any other return consumes it. */
 int tfs_server_wait(tfs_server* s, int64_t ticket, int timeout_ms, float* stat, int64_t* top_idx, float* top_val);
 

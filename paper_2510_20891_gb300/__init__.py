@@ -10,7 +10,7 @@ marshals arguments.  Functions keep the C names without the ``tfs_`` prefix:
 * ``eval_stat(table, basis, coeffs, f_ref=None, m=0, topk=0, ...)`` -> ``EvalResult``
 * ``eval_batch([Job(table, basis, coeffs, ...), ...], dev_status=None)`` -> the jobs, outputs filled
 * ``Server(budget_bytes)``: ``add_dataset(table, basis)``, ``submit(ds, coeffs, ...)`` -> ticket,
-  ``wait(ticket)`` -> (stat, top_idx, top_val), ``stats()``
+  ``wait(ticket, stat=None)`` -> (stat, top_idx, top_val), ``stats()``
 * ``autotune(jobs)`` -> (launch shape, ms, default ms); ``tuning_save(path)`` / ``tuning_load(path)``
 * ``topk(values, k)`` -> (idx, val)
 
@@ -506,10 +506,18 @@ class Server:
             self._shape[t.value] = (N, min(int(topk), N))
         return t.value
 
-    def wait(self, ticket: int, timeout_ms: int = -1):
+    def wait(self, ticket: int, timeout_ms: int = -1, stat=None):
+        """(stat, top_idx, top_val) of a ticket.  `stat` may be the caller's own float32 buffer of
+        at least N elements (reused from request to request); the values fill its first N."""
         with self._lock:
             N, kk = self._shape[ticket]
-        stat = np.empty(N, dtype=np.float32)
+        if stat is None:
+            stat = np.empty(N, dtype=np.float32)
+        else:
+            if not (isinstance(stat, np.ndarray) and stat.dtype == np.float32 and stat.ndim == 1
+                    and stat.flags.c_contiguous and stat.size >= N):
+                raise ValueError(f"stat must be a contiguous float32 vector of at least {N} elements")
+            stat = stat[:N]
         ti = np.empty(kk, dtype=np.int64)
         tv = np.empty(kk, dtype=np.float32)
         rc = lib().tfs_server_wait(self._h, int(ticket), int(timeout_ms), _ptr(stat), _ptr(ti) if kk else None,

@@ -125,14 +125,15 @@ __device__ __forceinline__ double track_f(const ChirpJob& a, const double* c, do
 }
 
 __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_constant__ ChirpBatch B) {
-  __shared__ float s_win[kM];                 // sin^2(pi m / 256)
-  __shared__ float2 s_buf[kCW][2][16][17];    // per half-warp transpose (padded rows)
+  __shared__ float4 s_wyq[16][16];            // sample m = l + 16 i at [i][l]: w(y), y, y^2 (exact)
+  __shared__ __align__(16) float2 s_buf[kCW][2][16][18];  // per half-warp transpose (rows padded to 16 B)
   __shared__ double s_c[kCW][32];             // the warp's track coefficients
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int hf = lane >> 4, l16 = lane & 15;  // half of the warp, lane within it
-  for (int i = tid; i < kM; i += kCThreads) {
-    const float s = sinpif((float)i / (float)kM);
-    s_win[i] = s * s;
+  for (int m = tid; m < kM; m += kCThreads) {
+    const float s = sinpif((float)m / (float)kM);
+    const int mc = m - kM / 2;
+    s_wyq[m >> 4][m & 15] = make_float4(s * s, (float)mc * (1.f / kM), (float)(mc * mc) * (1.f / (kM * kM)), 0.f);
   }
   // e^{-2 pi i l16 j0 / 256}, j0 = 1..15 (exact arguments; j0 = 0 is 1)
   float2 tw[16];
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
     const int n = a.n_seg;
     const double T = a.T;
     const double T6 = __ddiv_rn(T, 6.0);
+    const double invT = 1.0 / T;
     __syncwarp();
     if (lane < a.K) s_c[w][lane] = a.coeffs[t * a.K + lane];
     __syncwarp();
@@ -174,15 +176,23 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
       bool p_skip = true;
       int p_b = 0;
       float p_d2 = 0.f, p_bh = 0.f, p_bl = 0.f;
+      // each lane its segment's frequency, the neighbours' from the adjacent lanes (the edge
+      // lanes evaluate theirs): the same FP64 operations whichever lane does them
+      const double F0 = sg < n ? track_f(a, c, fr, sg) : 0.0;
+      double Fm = __shfl_up_sync(0xffffffffu, F0, 1);
+      double Fp = __shfl_down_sync(0xffffffffu, F0, 1);
+      if (lane == 0) Fm = (sg > 0 && sg < n) ? track_f(a, c, fr, sg - 1) : 0.0;
+      if (lane == 31) Fp = sg + 1 < n ? track_f(a, c, fr, sg + 1) : 0.0;
       if (sg < n) {
-        const double F0 = track_f(a, c, fr, sg);
-        const double Fm = sg > 0 ? track_f(a, c, fr, sg - 1) : 0.0;
-        const double Fp = sg + 1 < n ? track_f(a, c, fr, sg + 1) : 0.0;
         double fd = 0.0;
         if (n >= 2) {
-          if (sg == 0) fd = __ddiv_rn(__dsub_rn(Fp, F0), T);
-          else if (sg == n - 1) fd = __ddiv_rn(__dsub_rn(F0, Fm), T);
-          else fd = __ddiv_rn(__dsub_rn(Fp, Fm), __dmul_rn(2.0, T));
+          const double dF = sg == 0 ? __dsub_rn(Fp, F0) : (sg == n - 1 ? __dsub_rn(F0, Fm) : __dsub_rn(Fp, Fm));
+          if (a.cuts) {
+            // the exclusion compares fdot with its threshold: the oracle's division, exactly
+            fd = (sg == 0 || sg == n - 1) ? __ddiv_rn(dF, T) : __ddiv_rn(dF, __dmul_rn(2.0, T));
+          } else {
+            fd = dF * ((sg == 0 || sg == n - 1) ? invT : 0.5 * invT);  // only the template's beta
+          }
         }
         const double x = __dmul_rn(F0, T);
         const double bz = floor(__dadd_rn(x, 0.5));
@@ -239,23 +249,35 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
         const float d2 = __shfl_sync(0xffffffffu, p_d2, src);
         const float bh = __shfl_sync(0xffffffffu, p_bh, src);
         const float bl = __shfl_sync(0xffffffffu, p_bl, src);
-        // samples m = l16 + 16 i of g(y) = w(y) e^{i pi (2 delta0 y + beta y^2)}, y = m / 256 - 1/2
+        // samples m = l16 + 16 i of g(y) = w(y) e^{i pi (2 delta0 y + beta y^2)}, y = m / 256 - 1/2,
+        // with the hardware sine and cosine on [-pi, pi] (absolute error about 2^-21.4: far below
+        // the FP32 rounding of the template's sums)
         float2 v[16];
+        const float bs = bh + bl;
+        // the phases first (in v[i].x, units of pi, reduced to [-1, 1]), then sine and cosine
+        if (__all_sync(0xffffffffu, fabsf(bs) <= 2.f)) {
+          // |beta| <= 2: 2 delta0 y + beta y^2 lies in [-1, 1] as it is
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float4 wyq = s_wyq[i][l16];
+            v[i].x = fmaf(bs, wyq.z, d2 * wyq.y);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float4 wyq = s_wyq[i][l16];
+            const float y = wyq.y, q = wyq.z;                      // y and y^2, exact
+            const float p1 = bh * q;                               // exact
+            const float r1 = p1 - 2.f * rintf(0.5f * p1);          // exact reduction modulo 2
+            const float ph = r1 + fmaf(bl, q, d2 * y);
+            v[i].x = ph - 2.f * rintf(0.5f * ph);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int m = l16 + 16 * i;
-          const int mc = m - kM / 2;
-          const float y = (float)mc * (1.f / kM);
-          const float q = (float)(mc * mc) * (1.f / (kM * kM));  // y^2, exact
-          const float p1 = bh * q;                               // exact
-          const float r1 = p1 - 2.f * rintf(0.5f * p1);          // exact reduction modulo 2
-          const float ph = r1 + fmaf(bl, q, d2 * y);
-          // the hardware sine and cosine on [-pi, pi] (absolute error about 2^-21.4): far below
-          // the FP32 rounding of the template's sums
-          const float phr = ph - 2.f * rintf(0.5f * ph);   // [-1, 1]
+          const float wv = s_wyq[i][l16].x;
           float sn, cs;
-          __sincosf(3.14159265358979f * phr, &sn, &cs);
-          const float wv = s_win[m];
+          __sincosf(3.14159265358979f * v[i].x, &sn, &cs);
           v[i] = make_float2(wv * cs, wv * sn);
         }
         // 256 = 16 (lane-local, i) x 16 (across the half's lanes): output j0 + 16 j1 is
@@ -265,7 +287,11 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
         for (int j0 = 0; j0 < 16; ++j0) s_buf[w][hf][j0][l16] = j0 ? c_mul(v[at16(j0)], tw[j0]) : v[0];
         __syncwarp();
 #pragma unroll
-        for (int l = 0; l < 16; ++l) v[l] = s_buf[w][hf][l16][l];
+        for (int l = 0; l < 16; l += 2) {  // two at a time: 16-byte loads
+          const float4 p = *reinterpret_cast<const float4*>(&s_buf[w][hf][l16][l]);
+          v[l] = make_float2(p.x, p.y);
+          v[l + 1] = make_float2(p.z, p.w);
+        }
         __syncwarp();
         dft16(v);  // lane j0 = l16 now holds G[j0 + 16 j1] in v[at16(j1)]
         // kept outputs: j1 = 0..6 (j = j0 + 16 j1 <= 111) and j1 = 9..15 (j - 256 >= -112), those

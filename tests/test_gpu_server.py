@@ -163,6 +163,27 @@ def test_budget_evicts_and_reloads_tables(T):
     srv.close()
 
 
+def test_results_into_a_callers_buffer(T):
+    """wait(stat=buf) fills the first N elements of the caller's (larger, reused) buffer with the
+    same values a fresh array gets, and leaves the rest alone."""
+    data = _datasets(T, 9)[:2]
+    srv = T.Server(8 << 30)
+    ids = [srv.add_dataset(T.table_from_power(d["P"], d["Tsft"], d["dtype"]), d["basis"]) for d in data]
+    rng = np.random.default_rng(10)
+    buf = np.full(50000, -7.0, np.float32)
+    for di, N in ((0, 20000), (1, 777), (0, 50000)):
+        c, f = _tracks(rng, data[di], N)
+        fresh = srv.wait(srv.submit(ids[di], c, f, m=1, topk=4))
+        buf[:] = -7.0
+        got = srv.wait(srv.submit(ids[di], c, f, m=1, topk=4), stat=buf)
+        assert got[0].base is buf or got[0] is buf or np.shares_memory(got[0], buf)
+        assert np.array_equal(got[0], fresh[0]) and np.array_equal(got[1], fresh[1])
+        assert np.all(buf[N:] == -7.0)
+    with pytest.raises(ValueError):
+        srv.wait(srv.submit(ids[0], c[:10], f[:10]), stat=np.empty(5, np.float32))
+    srv.close()
+
+
 def test_rejections(T):
     data = _datasets(T, 7)[:1]
     srv = T.Server(64 << 20)
