@@ -6,11 +6,15 @@
 // independent searches at once has no counterpart in the paper.
 //
 // One worker thread per server owns all device work.  It keeps two batches in
-// flight on two streams: while one batch runs, arriving requests are admitted
-// (device buffers allocated, inputs uploaded) and launched as the next batch,
-// so work from different requests overlaps on the device.  A second thread
-// watches the batches in flight and completes each as soon as its last kernel
-// has run, so that neither admission nor completion waits on the other.  Admission is FIFO:
+// flight: while one batch runs, arriving requests are admitted (device buffers
+// allocated, inputs uploaded on the batch's own stream) and launched as the next
+// batch, so the uploads of one batch overlap the kernels of the other.  The
+// kernels of all batches run in launch order on one compute stream: the
+// statistic kernel holds a whole SM per block, so a later batch's kernel
+// started beside an earlier batch's top-k passes would hold those back until it
+// ended.  A second thread watches the batches in flight and completes each as
+// soon as its last kernel has run, so that neither admission nor completion
+// waits on the other.  Admission is FIFO:
 // a request waits until its input/output buffers, plus its dataset's table if
 // that is not resident, fit under the budget; idle tables (no admitted or
 // running request uses them) are evicted least recently used first to make
@@ -37,9 +41,10 @@ struct SrvDataset {
   tfs_table* table = nullptr;        // owned; data == nullptr while evicted
   const tfs_basis* basis = nullptr;  // borrowed
   size_t data_bytes = 0, scale_bytes = 0;
-  std::vector<unsigned char> host;   // table bytes kept while evicted
+  std::vector<unsigned char> host;   // the table's bytes, copied when the dataset is added
   std::vector<float> host_scales;
   bool resident = true;
+  bool pooled = false;               // the device copy came from the stream-ordered pool (a reload)
   int pins = 0;                      // admitted or running requests using the table
   int64_t last_use = 0;
   std::vector<int> wsum_m;           // m values whose window sums are counted in the budget
@@ -77,8 +82,9 @@ struct CopySlot {
 };
 
 struct SrvBatch {
-  cudaStream_t st = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaStream_t st = nullptr;     // allocations, table reloads and uploads
+  cudaEvent_t up = nullptr;      // the uploads are done
+  cudaEvent_t ev = nullptr;      // the batch's last kernel and status copy are done
   int* d_status = nullptr;
   int* h_status = nullptr;  // pinned
   std::vector<SrvReq*> reqs;
@@ -100,6 +106,7 @@ struct tfs_server {
   int64_t used = 0;  // resident tables + admitted/running/uncollected request buffers
   int64_t use_clock = 0;
   SrvBatch batch[2];
+  cudaStream_t cst = nullptr;        // the batches' kernels, in launch order
   std::deque<SrvBatch*> inflight;    // launched batches, oldest first (completed by `completer`)
   std::condition_variable cv_inflight;
   std::thread completer;
@@ -117,44 +124,55 @@ struct tfs_server {
 namespace tfs {
 namespace {
 
-// Free the device copy of an idle table, keeping its bytes in host memory.  cudaFree
-// waits for the device, so evictions also wait for running batches.
-int evict(SrvDataset* d) {
+// Keep the table's bytes in host memory (once, when the dataset is added).
+int keep_host_copy(SrvDataset* d) {
   tfs_table* t = d->table;
-  if (d->host.size() != d->data_bytes) {
-    d->host.resize(d->data_bytes);
-    TFS_CUDA(cudaMemcpy(d->host.data(), t->data, d->data_bytes, cudaMemcpyDeviceToHost));
-    if (t->scales) {
-      d->host_scales.resize((size_t)t->n_seg);
-      TFS_CUDA(cudaMemcpy(d->host_scales.data(), t->scales, d->scale_bytes, cudaMemcpyDeviceToHost));
-    }
-  }
-  wsum_free(t);
-  TFS_CUDA(cudaFree(t->data));
-  t->data = nullptr;
+  d->host.resize(d->data_bytes);
+  TFS_CUDA(cudaMemcpy(d->host.data(), t->data, d->data_bytes, cudaMemcpyDeviceToHost));
   if (t->scales) {
-    TFS_CUDA(cudaFree(t->scales));
-    t->scales = nullptr;
+    d->host_scales.resize((size_t)t->n_seg);
+    TFS_CUDA(cudaMemcpy(d->host_scales.data(), t->scales, d->scale_bytes, cudaMemcpyDeviceToHost));
   }
+  return TFS_OK;
+}
+
+// Free the device copy of an idle table (no request in flight reads it) and its window sums, in
+// the order of `st`: a reloaded copy goes back to the pool without waiting for the device; the
+// table's first allocation (made when it was built) is freed once with cudaFree.
+int evict(SrvDataset* d, cudaStream_t st) {
+  tfs_table* t = d->table;
+  wsum_free_idle(t, st);
+  if (d->pooled) {
+    TFS_CUDA(cudaFreeAsync(t->data, st));
+    if (t->scales) TFS_CUDA(cudaFreeAsync(t->scales, st));
+  } else {
+    TFS_CUDA(cudaFree(t->data));
+    if (t->scales) TFS_CUDA(cudaFree(t->scales));
+  }
+  t->data = nullptr;
+  t->scales = nullptr;
   d->resident = false;
   return TFS_OK;
 }
 
+// Bring an evicted table back from its host copy, in the order of `st` (the copy is never
+// written again, so nothing waits for the upload here).
 int reload(SrvDataset* d, cudaStream_t st) {
   tfs_table* t = d->table;
-  TFS_CUDA(cudaMalloc(&t->data, d->data_bytes));
+  retain_pool_memory();
+  TFS_CUDA(cudaMallocAsync(&t->data, d->data_bytes, st));
   TFS_CUDA(cudaMemcpyAsync(t->data, d->host.data(), d->data_bytes, cudaMemcpyHostToDevice, st));
   if (d->scale_bytes) {
-    TFS_CUDA(cudaMalloc(&t->scales, d->scale_bytes));
+    TFS_CUDA(cudaMallocAsync((void**)&t->scales, d->scale_bytes, st));
     TFS_CUDA(cudaMemcpyAsync(t->scales, d->host_scales.data(), d->scale_bytes, cudaMemcpyHostToDevice, st));
   }
-  TFS_CUDA(cudaStreamSynchronize(st));  // the host copy is pageable: finish before it can change
+  d->pooled = true;
   d->resident = true;
   return TFS_OK;
 }
 
 // Evict idle tables, least recently used first, until `need` more bytes fit (keep `keep`).
-bool make_room(tfs_server* s, int64_t need, int keep) {
+bool make_room(tfs_server* s, int64_t need, int keep, cudaStream_t st) {
   while (s->used + need > s->budget) {
     SrvDataset* victim = nullptr;
     for (size_t i = 0; i < s->ds.size(); ++i) {
@@ -164,7 +182,7 @@ bool make_room(tfs_server* s, int64_t need, int keep) {
     }
     if (!victim) return false;
     const int64_t freed = victim->dev_bytes();
-    if (evict(victim) != TFS_OK) return false;
+    if (evict(victim, st) != TFS_OK) return false;
     s->used -= freed;
     victim->wsum_m.clear();
     victim->wsum_bytes = 0;
@@ -204,7 +222,7 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
     const bool new_w = std::find(d->wsum_m.begin(), d->wsum_m.end(), r->m) == d->wsum_m.end();
     const int64_t w_bytes = new_w ? wsum_bytes(d->table, r->m) : 0;
     const int64_t need = (int64_t)r->dev_bytes + (d->resident ? 0 : d->dev_bytes()) + w_bytes;
-    if (s->used + need > s->budget && !make_room(s, need, r->ds)) break;
+    if (s->used + need > s->budget && !make_room(s, need, r->ds, b.st)) break;
     if (!d->resident) {
       const int rc = reload(d, b.st);
       if (rc != TFS_OK) {
@@ -268,6 +286,11 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
     if (e == cudaSuccess && r->f_ref)
       e = cudaMemcpyAsync(r->d_f, r->f_ref, (size_t)r->N * 8, cudaMemcpyHostToDevice, b.st);
     if (e != cudaSuccess) rc = cuda_fail(e, "request upload");
+    // the window sums this launch reads, built here on the batch's stream if new (their first
+    // build waits for that stream only, not for the compute stream)
+    const float* q = nullptr;
+    int qp = 0;
+    if (rc == TFS_OK) rc = wsum_get(r->dsp->table, r->m, b.st, &q, &qp);
     tfs_job& j = jobs[i];
     std::memset(&j, 0, sizeof(j));
     j.table = r->dsp->table;
@@ -281,14 +304,22 @@ void launch(tfs_server* s, SrvBatch& b, std::unique_lock<std::mutex>& lk) {
     j.top_idx = r->d_ti;
     j.top_val = r->d_tv;
   }
-  if (rc == TFS_OK) rc = tfs_eval_batch(jobs.data(), (int)jobs.size(), b.d_status, b.st);
   if (rc == TFS_OK) {
-    cudaError_t e = cudaMemcpyAsync(b.h_status, b.d_status, sizeof(int), cudaMemcpyDeviceToHost, b.st);
-    if (e == cudaSuccess) e = cudaEventRecord(b.ev, b.st);
+    cudaError_t e = cudaEventRecord(b.up, b.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cst, b.up, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "batch upload event");
+  }
+  if (rc == TFS_OK) rc = tfs_eval_batch(jobs.data(), (int)jobs.size(), b.d_status, s->cst);
+  if (rc == TFS_OK) {
+    cudaError_t e = cudaMemcpyAsync(b.h_status, b.d_status, sizeof(int), cudaMemcpyDeviceToHost, s->cst);
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev, s->cst);
     if (e != cudaSuccess) rc = cuda_fail(e, "batch completion event");
   }
   const std::string msg = rc == TFS_OK ? std::string() : std::string(tfs_last_error());
-  if (rc != TFS_OK) cudaStreamSynchronize(b.st);
+  if (rc != TFS_OK) {
+    cudaStreamSynchronize(b.st);
+    cudaStreamSynchronize(s->cst);
+  }
   lk.lock();
   if (rc != TFS_OK) {
     for (SrvReq* r : adm) {
@@ -374,8 +405,16 @@ int tfs_server_create(int64_t budget_bytes, int max_batch_jobs, tfs_server** out
   s->device = dev;
   s->budget = budget_bytes;
   s->max_jobs = max_batch_jobs;
+  {
+    const cudaError_t e = cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      tfs_server_free(s);
+      return cuda_fail(e, "server set-up");
+    }
+  }
   for (SrvBatch& b : s->batch) {
     cudaError_t e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.up, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b.d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b.h_status, sizeof(int));
@@ -403,12 +442,17 @@ int tfs_server_add_dataset(tfs_server* s, tfs_table* table, const tfs_basis* bas
   d->basis = basis;
   d->data_bytes = (size_t)table->n_seg * table->row_stride * esize_of(table->dtype);
   d->scale_bytes = table->scales ? (size_t)table->n_seg * sizeof(float) : 0;
+  const int rc = keep_host_copy(d);
+  if (rc != TFS_OK) {
+    delete d;
+    return rc;
+  }
   d->last_use = ++s->use_clock;
   s->ds.push_back(d);
   s->used += d->dev_bytes();
   *ds_id = (int)s->ds.size() - 1;
   // over budget: evict idle tables, least recently used first (possibly an older one)
-  if (s->used > s->budget) make_room(s, 0, -1);
+  if (s->used > s->budget) make_room(s, 0, -1, s->batch[0].st);
   return TFS_OK;
 }
 
@@ -505,6 +549,11 @@ int tfs_server_wait(tfs_server* s, int64_t ticket, int timeout_ms, float* stat, 
     cudaSetDevice(s->device);
     CopySlot* c = nullptr;
     cudaError_t e = take_copy_slot(s, &c);
+    // Touch the destination's pages first: a device write into pageable pages that were never
+    // touched waits on page faults served one by one (about 1 ms for 4 MB of fresh memory, far
+    // more with several copies at once); a store per 4 KB maps them on the host beforehand.
+    if (stat)
+      for (size_t o = 0; o < (size_t)r->N * 4; o += 4096) reinterpret_cast<volatile char*>(stat)[o] = 0;
     if (e == cudaSuccess && stat)
       e = cudaMemcpyAsync(stat, r->d_stat, (size_t)r->N * 4, cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess && r->topk && top_idx)
@@ -596,7 +645,14 @@ int tfs_server_free(tfs_server* s) {
     if (kv.second->dev) cudaFree(kv.second->dev);
     delete kv.second;
   }
+  cudaDeviceSynchronize();
   for (SrvDataset* d : s->ds) {
+    if (d->pooled && d->table->data) {  // a reloaded copy goes back to the pool
+      cudaFreeAsync(d->table->data, 0);
+      if (d->table->scales) cudaFreeAsync(d->table->scales, 0);
+      d->table->data = nullptr;
+      d->table->scales = nullptr;
+    }
     tfs_table_free(d->table);
     delete d;
   }
@@ -605,9 +661,14 @@ int tfs_server_free(tfs_server* s) {
     cudaStreamDestroy(c->st);
     delete c;
   }
+  if (s->cst) {
+    cudaStreamSynchronize(s->cst);
+    cudaStreamDestroy(s->cst);
+  }
   for (SrvBatch& b : s->batch) {
     if (b.ev) cudaEventDestroy(b.ev);
     if (b.st) cudaStreamDestroy(b.st);
+    if (b.up) cudaEventDestroy(b.up);
     if (b.d_status) cudaFree(b.d_status);
     if (b.h_status) cudaFreeHost(b.h_status);
   }

@@ -77,7 +77,7 @@ struct WSum {
   int m = 0;
   int64_t pitch = 0;
   int64_t bytes = 0;
-  float* q = nullptr;
+  float* q = nullptr;   // from the device's stream-ordered pool
 };
 
 }  // namespace tfs
@@ -133,8 +133,11 @@ int64_t wsum_bytes(const tfs_table* t, int m);
 int64_t wsum_cached_bytes(const tfs_table* t);
 bool wsum_cached(const tfs_table* t, int m);
 int wsum_get(const tfs_table* t, int m, cudaStream_t st, const float** q, int* pitch);
+// Keeps up to 8 GB of freed stream-ordered memory reserved in the device's pool (tfs_api.cu).
+void retain_pool_memory();
 int wsum_refresh(tfs_table* t, cudaStream_t st);
 void wsum_free(tfs_table* t);
+void wsum_free_idle(tfs_table* t, cudaStream_t st);  // no kernel of any stream reads them any more
 
 // Cached FP32 filter parameters of a basis for a given T_sft, with at least kp_min coefficient
 // slots (built on first use; rebuilt for another T_sft or a wider slot count).

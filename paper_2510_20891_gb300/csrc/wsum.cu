@@ -104,7 +104,8 @@ int wsum_get(const tfs_table* t, int m, cudaStream_t st, const float** q, int* p
   w.pitch = wsum_pitch(o->n_bin, m);
   w.bytes = o->n_seg * w.pitch * (int64_t)sizeof(float);
   TFS_CHECK(w.pitch < (1 << 30), TFS_ERR_INVALID_ARG, "table row too wide");
-  TFS_CUDA(cudaMalloc(&w.q, (size_t)w.bytes));
+  retain_pool_memory();
+  TFS_CUDA(cudaMallocAsync((void**)&w.q, (size_t)w.bytes, st));
   int rc = launch_wsum(o, m, w.pitch, w.q, st);
   // one-off per (table, m): later calls may run on other streams without waiting for this one
   if (rc == TFS_OK) {
@@ -112,7 +113,7 @@ int wsum_get(const tfs_table* t, int m, cudaStream_t st, const float** q, int* p
     if (e != cudaSuccess) rc = cuda_fail(e, "window sums");
   }
   if (rc) {
-    cudaFree(w.q);
+    cudaFreeAsync(w.q, st);
     return rc;
   }
   o->wsums.push_back(w);
@@ -130,9 +131,20 @@ int wsum_refresh(tfs_table* t, cudaStream_t st) {
   return TFS_OK;
 }
 
+// Work of any stream may still read the sums: wait for the device, then return them to the pool.
 void wsum_free(tfs_table* t) {
   std::lock_guard<std::mutex> lk(t->wmu);
-  for (const WSum& w : t->wsums) cudaFree(w.q);
+  if (t->wsums.empty()) return;
+  cudaDeviceSynchronize();
+  for (const WSum& w : t->wsums) cudaFreeAsync(w.q, 0);
+  t->wsums.clear();
+}
+
+// The caller knows that nothing reads the sums any more (a served table with no request in
+// flight): freed in the order of `st`, without waiting for the device.
+void wsum_free_idle(tfs_table* t, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(t->wmu);
+  for (const WSum& w : t->wsums) cudaFreeAsync(w.q, st);
   t->wsums.clear();
 }
 
