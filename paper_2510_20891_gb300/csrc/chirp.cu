@@ -125,7 +125,8 @@ __device__ __forceinline__ double track_f(const ChirpJob& a, const double* c, do
 }
 
 __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_constant__ ChirpBatch B) {
-  __shared__ float4 s_wyq[16][16];            // sample m = l + 16 i at [i][l]: w(y), y, y^2 (exact)
+  __shared__ float4 s_wyq[16][16];            // sample m = l + 16 i at [i][l]: w(y), pi y, pi y^2
+  __shared__ float2 s_yq[16][16];             // y, y^2 (exact)
   __shared__ __align__(16) float2 s_buf[kCW][2][16][18];  // per half-warp transpose (rows padded to 16 B)
   __shared__ double s_c[kCW][32];             // the warp's track coefficients
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -133,7 +134,9 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
   for (int m = tid; m < kM; m += kCThreads) {
     const float s = sinpif((float)m / (float)kM);
     const int mc = m - kM / 2;
-    s_wyq[m >> 4][m & 15] = make_float4(s * s, (float)mc * (1.f / kM), (float)(mc * mc) * (1.f / (kM * kM)), 0.f);
+    const float y = (float)mc * (1.f / kM), q = (float)(mc * mc) * (1.f / (kM * kM));
+    s_wyq[m >> 4][m & 15] = make_float4(s * s, 3.14159265358979f * y, 3.14159265358979f * q, 0.f);
+    s_yq[m >> 4][m & 15] = make_float2(y, q);
   }
   // e^{-2 pi i l16 j0 / 256}, j0 = 1..15 (exact arguments; j0 = 0 is 1)
   float2 tw[16];
@@ -254,9 +257,9 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
         // the FP32 rounding of the template's sums)
         float2 v[16];
         const float bs = bh + bl;
-        // the phases first (in v[i].x, units of pi, reduced to [-1, 1]), then sine and cosine
+        // the phases first (in v[i].x, radians in [-pi, pi]), then sine and cosine
         if (__all_sync(0xffffffffu, fabsf(bs) <= 2.f)) {
-          // |beta| <= 2: 2 delta0 y + beta y^2 lies in [-1, 1] as it is
+          // |beta| <= 2: pi (2 delta0 y + beta y^2) lies in [-pi, pi] as it is
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const float4 wyq = s_wyq[i][l16];
@@ -265,19 +268,19 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
         } else {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float4 wyq = s_wyq[i][l16];
-            const float y = wyq.y, q = wyq.z;                      // y and y^2, exact
+            const float2 yq = s_yq[i][l16];
+            const float y = yq.x, q = yq.y;                        // y and y^2, exact
             const float p1 = bh * q;                               // exact
             const float r1 = p1 - 2.f * rintf(0.5f * p1);          // exact reduction modulo 2
             const float ph = r1 + fmaf(bl, q, d2 * y);
-            v[i].x = ph - 2.f * rintf(0.5f * ph);
+            v[i].x = 3.14159265358979f * (ph - 2.f * rintf(0.5f * ph));
           }
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const float wv = s_wyq[i][l16].x;
           float sn, cs;
-          __sincosf(3.14159265358979f * v[i].x, &sn, &cs);
+          __sincosf(v[i].x, &sn, &cs);
           v[i] = make_float2(wv * cs, wv * sn);
         }
         // 256 = 16 (lane-local, i) x 16 (across the half's lanes): output j0 + 16 j1 is
