@@ -250,15 +250,24 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     return TFS_ERR_INVALID_ARG;
   }
   const int grid = (int)std::min<long long>(nt, (long long)sm_count());
-  // the helper warps' prologue columns, one block per CTA (stream-ordered scratch)
-  float* cbuf = nullptr;
-  TFS_CUDA(cudaMallocAsync((void**)&cbuf, (size_t)grid * (KP + 1) * kCons * R * sizeof(float), st));
-  a.cbuf = cbuf;
+  // the tile counter, then the helper warps' prologue columns, one block per CTA (stream-ordered
+  // scratch)
+  char* scratch = nullptr;
+  TFS_CUDA(cudaMallocAsync((void**)&scratch, 256 + (size_t)grid * (KP + 1) * kCons * R * sizeof(float), st));
+  a.tile_ctr = reinterpret_cast<int*>(scratch);
+  a.cbuf = reinterpret_cast<float*>(scratch + 256);
+  {
+    const cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(scratch, st);
+      return cuda_fail(e, "tile counter");
+    }
+  }
   double* parts = nullptr;
   if (part_floats) {
     const cudaError_t e = cudaMallocAsync((void**)&parts, part_floats * sizeof(double), st);
     if (e != cudaSuccess) {
-      cudaFreeAsync(cbuf, st);
+      cudaFreeAsync(scratch, st);
       return cuda_fail(e, "partial sums");
     }
     size_t o = 0;
@@ -301,7 +310,7 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     if (e != cudaSuccess) rc = cuda_fail(e, "partial sums");
   }
   if (parts) cudaFreeAsync(parts, st);
-  cudaFreeAsync(cbuf, st);
+  cudaFreeAsync(scratch, st);
   return rc;
 }
 

@@ -102,6 +102,7 @@ struct EvalArgs {
   int group;     // segments per slot at most (<= kMaxGroup)
   int bcap;      // segments whose bands are precomputed per tile (<= kBandCap); longer tiles compute them as they stage
   float* cbuf;   // [grid][KP + 1][consumer threads * R] prologue columns (FP32 coefficients, then y0)
+  int* tile_ctr; // tiles claimed beyond each CTA's first (zero at launch)
   int n_tiles;
   int n_jobs;
   // shared-memory carve-up (byte offsets)
@@ -405,7 +406,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
   WarpInfo* winfo = reinterpret_cast<WarpInfo*>(smem + a.off_info);          // [kConsWarps]
   uint32_t* inboxm = reinterpret_cast<uint32_t*>(winfo + kConsWarps);         // [kCons] tracks decided in FP32
   float* bpart = reinterpret_cast<float*>(inboxm + kCons);                    // [3][BW] box partials
-  volatile int* flags = reinterpret_cast<volatile int*>(smem + a.off_flags);  // [0] abort
+  // [0] abort, [1] the tile the helpers claimed, [2 + b] the tile of parity b for the stager and
+  // the consumers (n_tiles or more: no more tiles)
+  volatile int* flags = reinterpret_cast<volatile int*>(smem + a.off_flags);
   uint32_t* issued = reinterpret_cast<uint32_t*>(smem + a.off_flags) + 4;    // [kMaxSlots] last use + 1
   float* boxes = reinterpret_cast<float*>(issued + kMaxSlots);                // [2][BW]
   int* bands = reinterpret_cast<int*>(smem + a.off_band);                     // [2][bcap][2]
@@ -449,8 +452,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       // the slot taking the leading segments that fit
       uint32_t seq = 0;  // slots filled so far in this launch
       if (a.hold) (void)warp_wait(hold_bar, 0u, flags, a.wait_ns);
-      int ltile = 0;
-      for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
+      for (int ltile = 0;; ++ltile) {
+        const int b = ltile & 1;
+        if (!warp_wait(&band_ready[b], (uint32_t)((ltile >> 1) & 1), flags, a.wait_ns)) break;
+        const int tile = reinterpret_cast<const int*>(const_cast<const int*>(flags))[2 + b];
+        if (tile >= a.n_tiles) break;
         const int j = job_of(a, tile);
         const JobDesc& J = a.jobs[j];
         const int m = J.m;
@@ -458,8 +464,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         int sp_unused, s0, s1;
         tile_range(a, J, tile, j, &tile0_unused, &sp_unused, &s0, &s1);
         const int ns = s1 - s0;
-        const int b = ltile & 1;
-        if (!warp_wait(&band_ready[b], (uint32_t)((ltile >> 1) & 1), flags, a.wait_ns)) break;
         const float* box = boxes + b * BW;
         const int* band = bands + b * 2 * a.bcap;
         const int bm = reinterpret_cast<const int*>(box)[2 * KP];
@@ -536,8 +540,27 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       // consumer warp's base bin and decision limit, the tile's coefficient box and its bands.
       const int hid = tid - 32;  // 0..95
       const int hw = hid >> 5;   // 0..2
-      int ltile = 0;
-      for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++ltile) {
+      // Tiles are handed out as CTAs get to them: each CTA's first is its own index, every later
+      // one is claimed from a launch-wide counter when the helpers start its prologue (one tile
+      // ahead of the consumers), so that faster SMs take more tiles and the launch ends together.
+      for (int ltile = 0;; ++ltile) {
+        const int b = ltile & 1;
+        // the consumers have read the previous tile's data
+        if (ltile > 0) (void)warp_wait(pro_free, (uint32_t)((ltile - 1) & 1), flags, a.wait_ns);
+        if (ltile > 0 && hid == 0) flags[1] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);
+        if (help_bar_or(flags[0] != 0)) break;
+        const int tile = ltile == 0 ? (int)blockIdx.x : flags[1];
+        if (tile >= a.n_tiles) {
+          // no more tiles: tell the stager and the consumers (once the stager is done with this
+          // parity's slot of the tile ids)
+          if (ltile >= 2) (void)warp_wait(&band_free[b], (uint32_t)(((ltile - 2) >> 1) & 1), flags, a.wait_ns);
+          if (hid == 0) {
+            flags[2 + b] = tile;
+            mbar_arrive(pro_full);
+            mbar_arrive(&band_ready[b]);
+          }
+          break;
+        }
         const int j = job_of(a, tile);
         const JobDesc& J = a.jobs[j];
         const int n_seg = J.n_seg, m = J.m, K = J.K;
@@ -546,10 +569,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         tile_range(a, J, tile, j, &tile0, &sp_unused, &s0, &s1);
         const int ns = s1 - s0;
         const long long tend = min(J.N, tile0 + J.tile_tracks);
-        const int b = ltile & 1;
-        // the consumers have read the previous tile's data
-        if (ltile > 0) (void)warp_wait(pro_free, (uint32_t)((ltile - 1) & 1), flags, a.wait_ns);
-        if (help_bar_or(flags[0] != 0)) break;
         // the base bin of each consumer warp: from its first lane whose first track is usable
         for (int w = hw; w < kConsWarps; w += 3) {
           const long long t = tile0 + w * 32 + lane;
@@ -720,6 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         if (ltile >= 2) (void)warp_wait(&band_free[b], (uint32_t)(((ltile - 2) >> 1) & 1), flags, a.wait_ns);
         float* box = boxes + b * BW;
         if (hid == 0) {
+          flags[2 + b] = tile;
           int bm = 0x7fffffff, bx = -0x7fffffff;
           for (int k = 0; k < KP; ++k) {
             float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
@@ -763,8 +783,17 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
     const int cwarp = ctid >> 5;
     uint32_t seq = 0;
     bool dead = false;
-    int ltile = 0;
-    for (int tile = blockIdx.x; tile < a.n_tiles && !dead; tile += gridDim.x, ++ltile) {
+    for (int ltile = 0; !dead; ++ltile) {
+      // -------------------------------------------------------------- tile prologue
+      // Each track is evaluated relative to a warp-uniform base bin Bw (the FP64 mid-segment bin
+      // of the warp's first track): y = (x_mid - Bw) + sum_k c_k D_k,alpha in FP32, and the bin
+      // is Bw + rint(y).  One base per warp keeps a register per track free.  The helper warps
+      // prepared y0 = x_mid - Bw, the FP32 coefficients (0 for a track that FP32 cannot decide,
+      // whose y0 is 1/2), the warp's base and decision limit, and named the tile.
+      if (!warp_wait(pro_full, (uint32_t)(ltile & 1), flags, a.wait_ns)) break;
+      // (a plain load: the wait above acquired the helpers' write)
+      const int tile = reinterpret_cast<const int*>(const_cast<const int*>(flags))[2 + (ltile & 1)];
+      if (tile >= a.n_tiles) break;
       const int j = job_of(a, tile);
       const JobDesc& J = a.jobs[j];
       const int n_seg = J.n_seg, m = J.m;
@@ -772,13 +801,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       int sp, s0, s1;
       tile_range(a, J, tile, j, &tile0, &sp, &s0, &s1);
       const long long tend = min(J.N, tile0 + J.tile_tracks);
-      // -------------------------------------------------------------- tile prologue
-      // Each track is evaluated relative to a warp-uniform base bin Bw (the FP64 mid-segment bin
-      // of the warp's first track): y = (x_mid - Bw) + sum_k c_k D_k,alpha in FP32, and the bin
-      // is Bw + rint(y).  One base per warp keeps a register per track free.  The helper warps
-      // prepared y0 = x_mid - Bw, the FP32 coefficients (0 for a track that FP32 cannot decide,
-      // whose y0 is 1/2), the warp's base and decision limit.
-      if (!warp_wait(pro_full, (uint32_t)(ltile & 1), flags, a.wait_ns)) break;
       // tracks in pairs for the packed FP32x2 arithmetic (an odd R gets an inactive partner):
       // track r is half (r & 1) of c2[r / 2][k] and y02[r / 2]
       constexpr int R2 = (R + 1) / 2;
