@@ -211,11 +211,11 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
   const int BW = 2 * KP + 2;
   const int bcap = std::min(seg_max, kBandCap);
   a.bcap = bcap;
-  size_t off = 8 * (2 * kMaxSlots + 7);
+  size_t off = 8 * (2 * kMaxSlots + 8);  // mbarriers
   off = (off + 15) & ~(size_t)15;
   a.off_hdr = (int)off;   off += (size_t)NS * sizeof(SlotHdr);
   off = (off + 15) & ~(size_t)15;
-  a.off_info = (int)off;  off += sizeof(WarpInfo) * kConsWarps + (size_t)kCons * 4 + (size_t)3 * BW * 4;
+  a.off_info = (int)off;  off += sizeof(WarpInfo) * kConsWarps + (size_t)kCons * 4 + (size_t)kConsWarps * BW * 4;
   off = (off + 15) & ~(size_t)15;
   a.off_flags = (int)off; off += 16 + kMaxSlots * 4 + (size_t)2 * BW * 4;
   off = (off + 15) & ~(size_t)15;

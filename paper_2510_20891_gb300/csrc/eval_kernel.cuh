@@ -388,6 +388,190 @@ struct WarpInfo {
   int pad0, pad1;
 };
 
+// ---------------------------------------------------------------- tile prologue (FP64 where the
+// bin decision needs it).  Run by the helper warps one tile ahead of the consumers, and by the
+// consumers themselves for a CTA's first tile, which no earlier tile hides.
+
+// The base bin of consumer warp w of a tile: the FP64 mid-segment bin of its first lane whose first
+// track is usable (one warp).
+template <int KP, bool CUTS>
+__device__ __forceinline__ void prologue_base(const JobDesc& J, long long tile0, long long tend, int w, int lane,
+                                              WarpInfo* winfo) {
+  const int n_seg = J.n_seg, K = J.K;
+  const long long t = tile0 + w * 32 + lane;
+  const bool active = t < tend;
+  double xm = 0.0;
+  bool ex = false;
+  if (active) {
+    double f = J.f_ref ? J.f_ref[t] : 0.0;
+    float A = 0.f;
+    const double* cp = J.coeffs + t * (long long)K;
+    for (int k = 0; k < K; ++k) {
+      const double cd = cp[k];
+      f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
+      A = fmaf(fabsf((float)cd), J.dmax[k], A);
+    }
+    A *= 1.0001f;
+    xm = f * J.T;
+    ex = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
+  }
+  const unsigned ok = __ballot_sync(0xffffffffu, active && !ex);
+  const int src = ok ? __ffs(ok) - 1 : 0;
+  const int Bw = __shfl_sync(0xffffffffu, (active && !ex) ? (int)rint(xm) : 0, src);
+  if (lane == 0) {
+    winfo[w].Bw = Bw;
+    winfo[w].ylo = CUTS ? (float)(kFLowHz * J.T - (double)Bw) : 0.f;
+  }
+}
+
+// The R tracks of consumer thread ctid (one warp: the 32 lanes of one consumer warp, whose base bin
+// is set): their FP32 coefficients and offsets y0 in the prologue columns, which of them FP32
+// decides, the warp's decision limits, and the range of their FP64 mid bins (bmin, bmax).
+template <int KP, int R, bool CUTS>
+__device__ __forceinline__ void prologue_tracks(const JobDesc& J, long long tile0, long long tend, int ctid, int lane,
+                                                float* cbuf, WarpInfo* winfo, uint32_t* inboxm, int& bmin, int& bmax) {
+  constexpr int kCR = kCons * R;
+  const int n_seg = J.n_seg, K = J.K;
+  const int w = ctid >> 5;
+  const int Bw = winfo[w].Bw;
+  float wl = 0.5f, mzl = 0.f, mwl = 0.f;
+  bool ztl = false;
+  uint32_t ib = 0u;
+  for (int r = 0; r < R; ++r) {
+    const long long t = tile0 + ctid + r * kCons;
+    float* col = cbuf + r * kCons + ctid;  // coefficient k at col[k * kCR], y0 at col[KP * kCR]
+    if (!(t < tend)) {
+      // inactive slot: c = 0 and y far from the table (|y| < 2^22), never pending
+      for (int k = 0; k < KP; ++k) col[k * kCR] = 0.f;
+      col[KP * kCR] = Bw >= 0 ? 4194303.0f : -4194303.0f;
+      continue;
+    }
+    const double fr = J.f_ref ? J.f_ref[t] : 0.0;
+    double f = fr;
+    float A = 0.f, Um = fabsf((float)fr), Az = 0.f, Aw = 0.f;
+    const double* cp = J.coeffs + t * (long long)K;
+    for (int k = 0; k < KP; ++k) {
+      const double cd = (k < K) ? cp[k] : 0.0;
+      if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
+      const float cf = (float)cd;
+      col[k * kCR] = cf;
+      A = fmaf(fabsf(cf), J.dmax[k], A);
+      Um = fmaf(fabsf(cf), J.umax[k], Um);
+      if (CUTS) {
+        Az = fmaf(fabsf(cf), J.emax[k], Az);
+        Aw = fmaf(fabsf(cf), J.gmax[k], Aw);
+      }
+    }
+    A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
+    Um *= 1.0001f;
+    float ezt = 0.f, ewt = 0.f, zbt = 0.f;
+    if (CUTS) {
+      // z = fddot T^3/6 and w = fdot are linear in c: z = sum_k c_k E_k, w = sum_k c_k G_k.
+      // |fp32 z - oracle z| <= 2^-24 (K+2) sum|c_k| max|E_k| (c, E and the K FMAs rounded)
+      // + (4K+40) 2^-53 Um T/6 (the oracle's rounded frequencies, its second difference
+      // and the FP64 rounding of E); |fp32 w - oracle w| likewise with G and
+      // (2K+12) 2^-53 Um / T_SFT, plus the FP32 rounding of the 1e-13 threshold
+      ezt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Az * 1.0001f +
+                     (4.f * K + 40.f) * 1.1102230246251565e-16f * Um * (float)(J.T / 6.0)) + 1e-12f;
+      ewt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Aw * 1.0001f +
+                     (2.f * K + 12.f) * 1.1102230246251565e-16f * Um / (float)J.T) + 1e-20f;
+      zbt = Az * 1.0001f + ezt;  // bounds |oracle z| in every segment
+    }
+    const double xm = f * J.T;
+    // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
+    // FP32, K rounded FMAs on partial sums below |y0| + A, and the FP32 roundings of c and
+    // D; e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid,
+    // the deltas D, and the oracle's own evaluation).  With g = 1.25 (err + e64) + 4e-9,
+    // pairs closer than g to a half-integer are resolved in FP64; outside that band the
+    // exact, the oracle's and this bin coincide and none of them is a 1e-9 tie.
+    const float e64 = 7.105427357601002e-15f * (float)J.T * Um;
+    const float eb = 1.25f * (5.9604644775390625e-08f * ((K + 2.001f) * A) + 2.f * e64) + 4e-9f;
+    bool exact = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
+    float y0 = 0.5f;
+    if (!exact) {
+      const double yd = xm - (double)Bw;
+      const float yf = (float)yd;
+      const float g = eb + 1.25f * 5.9604644775390625e-08f * (float)(K + 1) * fabsf(yf) * 1.0001f;
+      exact = !(fabs(yd) < 2097152.0) || !(g < 0.25f);
+      if (!exact) {
+        y0 = yf;
+        wl = fminf(wl, __fsub_rd(0.5f, g));
+        if (CUTS) {
+          mzl = fmaxf(mzl, ezt);
+          mwl = fmaxf(mwl, ewt);
+          ztl = ztl || !(zbt < 1.f);
+        }
+        const int Bd = (int)rint(xm);
+        bmin = min(bmin, Bd);
+        bmax = max(bmax, Bd);
+        ib |= 1u << r;
+      }
+    }
+    if (exact) {
+      // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
+      for (int k = 0; k < KP; ++k) col[k * kCR] = 0.f;
+    }
+    col[KP * kCR] = y0;
+  }
+  inboxm[ctid] = ib;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wl = fminf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+    if (CUTS) {
+      mzl = fmaxf(mzl, __shfl_xor_sync(0xffffffffu, mzl, o));
+      mwl = fmaxf(mwl, __shfl_xor_sync(0xffffffffu, mwl, o));
+    }
+  }
+  ztl = __any_sync(0xffffffffu, ztl);
+  if (lane == 0) {
+    winfo[w].wlim = wl;
+    winfo[w].mz = mzl;
+    winfo[w].mw = mwl;
+    winfo[w].zt = ztl ? 1 : 0;
+  }
+}
+
+// One warp's partial of the tile's coefficient box over the tracks decided in FP32 among consumer
+// threads ctid0 + 96 q, q < nq: per coefficient the lowest and highest FP32 value, then the range
+// of the FP64 mid bins, in bp[0..2 KP + 1].
+template <int KP, int R>
+__device__ __forceinline__ void prologue_box_part(const float* cbuf, const uint32_t* inboxm, int ctid0, int nq,
+                                                  int lane, int bmin, int bmax, float* bp) {
+  constexpr int kCR = kCons * R;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+    bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  }
+  if (lane == 0) {
+    reinterpret_cast<int*>(bp)[2 * KP] = bmin;
+    reinterpret_cast<int*>(bp)[2 * KP + 1] = bmax;
+  }
+  for (int k = 0; k < KP; ++k) {
+    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+    for (int q = 0; q < nq; ++q) {
+      const int ctid = ctid0 + 96 * q;
+      const uint32_t ib = inboxm[ctid];
+      for (int r = 0; r < R; ++r) {
+        if ((ib >> r) & 1u) {
+          const float v = cbuf[k * kCR + r * kCons + ctid];
+          lo = fminf(lo, v);
+          hi = fmaxf(hi, v);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      bp[k] = lo;
+      bp[KP + k] = hi;
+    }
+  }
+}
+
 template <int KP, int R, bool BINS, bool CUTS, int MJ>
 __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_constant__ EvalArgs<MJ> a) {
   constexpr bool kCutRegs = CUTS && KP <= 8;  // segment-cut forms held in registers
@@ -402,10 +586,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
   uint64_t* band_ready = pro_full + 2;        // [2] a tile's box and bands are ready (helpers)
   uint64_t* band_free = pro_full + 4;         // [2] the stager is done with them
   uint64_t* hold_bar = pro_full + 6;          // nothing arrives on it (timeout tests)
+  uint64_t* parts_ready = pro_full + 7;       // the consumers' box partials of their first tile (12 warps)
   SlotHdr* hdr = reinterpret_cast<SlotHdr*>(smem + a.off_hdr);                // [nslots]
   WarpInfo* winfo = reinterpret_cast<WarpInfo*>(smem + a.off_info);          // [kConsWarps]
   uint32_t* inboxm = reinterpret_cast<uint32_t*>(winfo + kConsWarps);         // [kCons] tracks decided in FP32
-  float* bpart = reinterpret_cast<float*>(inboxm + kCons);                    // [3][BW] box partials
+  float* bpart = reinterpret_cast<float*>(inboxm + kCons);                    // [12][BW] box partials
   // [0] abort, [1] the tile the helpers claimed, [2 + b] the tile of parity b for the stager and
   // the consumers (n_tiles or more: no more tiles)
   volatile int* flags = reinterpret_cast<volatile int*>(smem + a.off_flags);
@@ -439,6 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       mbar_init(&band_free[i], 1);
     }
     mbar_init(hold_bar, 1);
+    mbar_init(parts_ready, kConsWarps);
     fence_mbar_init();
   }
   __syncthreads();
@@ -569,169 +755,19 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         tile_range(a, J, tile, j, &tile0, &sp_unused, &s0, &s1);
         const int ns = s1 - s0;
         const long long tend = min(J.N, tile0 + J.tile_tracks);
-        // the base bin of each consumer warp: from its first lane whose first track is usable
-        for (int w = hw; w < kConsWarps; w += 3) {
-          const long long t = tile0 + w * 32 + lane;
-          const bool active = t < tend;
-          double xm = 0.0;
-          bool ex = false;
-          if (active) {
-            double f = J.f_ref ? J.f_ref[t] : 0.0;
-            float A = 0.f;
-            const double* cp = J.coeffs + t * (long long)K;
-            for (int k = 0; k < K; ++k) {
-              const double cd = cp[k];
-              f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
-              A = fmaf(fabsf((float)cd), J.dmax[k], A);
-            }
-            A *= 1.0001f;
-            xm = f * J.T;
-            ex = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
-          }
-          const unsigned ok = __ballot_sync(0xffffffffu, active && !ex);
-          const int src = ok ? __ffs(ok) - 1 : 0;
-          const int Bw = __shfl_sync(0xffffffffu, (active && !ex) ? (int)rint(xm) : 0, src);
-          if (lane == 0) {
-            winfo[w].Bw = Bw;
-            winfo[w].ylo = CUTS ? (float)(kFLowHz * J.T - (double)Bw) : 0.f;
-          }
-        }
-        if (help_bar_or(flags[0] != 0)) break;
-        // every track: the helper lanes of round q hold the 32 lanes of consumer warp hw + 3q
-        int bmin = 0x7fffffff, bmax = -0x7fffffff;
-        for (int q = 0; q < 4; ++q) {
-          const int ctid = hid + 96 * q;
-          const int w = ctid >> 5;
-          const int Bw = winfo[w].Bw;
-          float wl = 0.5f, mzl = 0.f, mwl = 0.f;
-          bool ztl = false;
-          uint32_t ib = 0u;
-          for (int r = 0; r < R; ++r) {
-            const long long t = tile0 + ctid + r * kCons;
-            float* col = cbuf + r * kCons + ctid;  // coefficient k at col[k * kCR], y0 at col[KP * kCR]
-            if (!(t < tend)) {
-              // inactive slot: c = 0 and y far from the table (|y| < 2^22), never pending
-              for (int k = 0; k < KP; ++k) col[k * kCR] = 0.f;
-              col[KP * kCR] = Bw >= 0 ? 4194303.0f : -4194303.0f;
-              continue;
-            }
-            const double fr = J.f_ref ? J.f_ref[t] : 0.0;
-            double f = fr;
-            float A = 0.f, Um = fabsf((float)fr), Az = 0.f, Aw = 0.f;
-            const double* cp = J.coeffs + t * (long long)K;
-            for (int k = 0; k < KP; ++k) {
-              const double cd = (k < K) ? cp[k] : 0.0;
-              if (k < K) f = fma(cd, J.U[(size_t)k * n_seg + J.alpha_mid], f);
-              const float cf = (float)cd;
-              col[k * kCR] = cf;
-              A = fmaf(fabsf(cf), J.dmax[k], A);
-              Um = fmaf(fabsf(cf), J.umax[k], Um);
-              if (CUTS) {
-                Az = fmaf(fabsf(cf), J.emax[k], Az);
-                Aw = fmaf(fabsf(cf), J.gmax[k], Aw);
-              }
-            }
-            A *= 1.0001f;  // covers the FP32 rounding of the bounds (|fl32(c)| <= |c| (1 + 2^-24))
-            Um *= 1.0001f;
-            float ezt = 0.f, ewt = 0.f, zbt = 0.f;
-            if (CUTS) {
-              // z = fddot T^3/6 and w = fdot are linear in c: z = sum_k c_k E_k, w = sum_k c_k G_k.
-              // |fp32 z - oracle z| <= 2^-24 (K+2) sum|c_k| max|E_k| (c, E and the K FMAs rounded)
-              // + (4K+40) 2^-53 Um T/6 (the oracle's rounded frequencies, its second difference
-              // and the FP64 rounding of E); |fp32 w - oracle w| likewise with G and
-              // (2K+12) 2^-53 Um / T_SFT, plus the FP32 rounding of the 1e-13 threshold
-              ezt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Az * 1.0001f +
-                             (4.f * K + 40.f) * 1.1102230246251565e-16f * Um * (float)(J.T / 6.0)) + 1e-12f;
-              ewt = 1.25f * (5.9604644775390625e-08f * (K + 2.001f) * Aw * 1.0001f +
-                             (2.f * K + 12.f) * 1.1102230246251565e-16f * Um / (float)J.T) + 1e-20f;
-              zbt = Az * 1.0001f + ezt;  // bounds |oracle z| in every segment
-            }
-            const double xm = f * J.T;
-            // |fp32 y - (x - Bw)| <= err = 2^-24 ((K+1) |y0| + (K+2.001) A) + e64: y0 rounded to
-            // FP32, K rounded FMAs on partial sums below |y0| + A, and the FP32 roundings of c and
-            // D; e64 = 2^-47 T (|f_ref| + sum_k |c_k| max|U_k|) bounds every FP64 rounding (x_mid,
-            // the deltas D, and the oracle's own evaluation).  With g = 1.25 (err + e64) + 4e-9,
-            // pairs closer than g to a half-integer are resolved in FP64; outside that band the
-            // exact, the oracle's and this bin coincide and none of them is a 1e-9 tie.
-            const float e64 = 7.105427357601002e-15f * (float)J.T * Um;
-            const float eb = 1.25f * (5.9604644775390625e-08f * ((K + 2.001f) * A) + 2.f * e64) + 4e-9f;
-            bool exact = !(fabs(xm) < 1073741824.0) || !(A < 1048576.0f);
-            float y0 = 0.5f;
-            if (!exact) {
-              const double yd = xm - (double)Bw;
-              const float yf = (float)yd;
-              const float g = eb + 1.25f * 5.9604644775390625e-08f * (float)(K + 1) * fabsf(yf) * 1.0001f;
-              exact = !(fabs(yd) < 2097152.0) || !(g < 0.25f);
-              if (!exact) {
-                y0 = yf;
-                wl = fminf(wl, __fsub_rd(0.5f, g));
-                if (CUTS) {
-                  mzl = fmaxf(mzl, ezt);
-                  mwl = fmaxf(mwl, ewt);
-                  ztl = ztl || !(zbt < 1.f);
-                }
-                const int Bd = (int)rint(xm);
-                bmin = min(bmin, Bd);
-                bmax = max(bmax, Bd);
-                ib |= 1u << r;
-              }
-            }
-            if (exact) {
-              // every pair of this track takes the FP64 path: y = 1/2 exactly is never decided
-              for (int k = 0; k < KP; ++k) col[k * kCR] = 0.f;
-            }
-            col[KP * kCR] = y0;
-          }
-          inboxm[ctid] = ib;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            wl = fminf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-            if (CUTS) {
-              mzl = fmaxf(mzl, __shfl_xor_sync(0xffffffffu, mzl, o));
-              mwl = fmaxf(mwl, __shfl_xor_sync(0xffffffffu, mwl, o));
-            }
-          }
-          ztl = __any_sync(0xffffffffu, ztl);
-          if (lane == 0) {
-            winfo[w].wlim = wl;
-            winfo[w].mz = mzl;
-            winfo[w].mw = mwl;
-            winfo[w].zt = ztl ? 1 : 0;
-          }
-        }
-        // the coefficient box of the tracks decided in FP32 (a partial per helper warp)
-        float* bp = bpart + hw * BW;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
-          bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-        }
-        if (lane == 0) {
-          reinterpret_cast<int*>(bp)[2 * KP] = bmin;
-          reinterpret_cast<int*>(bp)[2 * KP + 1] = bmax;
-        }
-        for (int k = 0; k < KP; ++k) {
-          float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-          for (int q = 0; q < 4; ++q) {
-            const int ctid = hid + 96 * q;
-            const uint32_t ib = inboxm[ctid];
-            for (int r = 0; r < R; ++r) {
-              if ((ib >> r) & 1u) {
-                const float v = cbuf[k * kCR + r * kCons + ctid];
-                lo = fminf(lo, v);
-                hi = fmaxf(hi, v);
-              }
-            }
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-          }
-          if (lane == 0) {
-            bp[k] = lo;
-            bp[KP + k] = hi;
-          }
+        if (ltile > 0) {
+          // the base bin of each consumer warp, then every track: the helper lanes of round q
+          // hold the 32 lanes of consumer warp hw + 3q
+          for (int w = hw; w < kConsWarps; w += 3) prologue_base<KP, CUTS>(J, tile0, tend, w, lane, winfo);
+          if (help_bar_or(flags[0] != 0)) break;
+          int bmin = 0x7fffffff, bmax = -0x7fffffff;
+          for (int q = 0; q < 4; ++q)
+            prologue_tracks<KP, R, CUTS>(J, tile0, tend, hid + 96 * q, lane, cbuf, winfo, inboxm, bmin, bmax);
+          // the coefficient box of the tracks decided in FP32 (a partial per helper warp)
+          prologue_box_part<KP, R>(cbuf, inboxm, hid, 4, lane, bmin, bmax, bpart + hw * BW);
+        } else {
+          // the consumers prepare their first tile themselves: wait for their partials
+          (void)warp_wait(parts_ready, 0u, flags, a.wait_ns);
         }
         __threadfence_block();  // the columns in global memory, before the consumers are told
         if (help_bar_or(flags[0] != 0)) break;
@@ -741,16 +777,17 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         if (hid == 0) {
           flags[2 + b] = tile;
           int bm = 0x7fffffff, bx = -0x7fffffff;
+          const int nparts = ltile == 0 ? kConsWarps : 3;
           for (int k = 0; k < KP; ++k) {
             float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-            for (int h = 0; h < 3; ++h) {
+            for (int h = 0; h < nparts; ++h) {
               lo = fminf(lo, bpart[h * BW + k]);
               hi = fmaxf(hi, bpart[h * BW + KP + k]);
             }
             box[k] = lo;
             box[KP + k] = hi;
           }
-          for (int h = 0; h < 3; ++h) {
+          for (int h = 0; h < nparts; ++h) {
             bm = min(bm, reinterpret_cast<const int*>(bpart + h * BW)[2 * KP]);
             bx = max(bx, reinterpret_cast<const int*>(bpart + h * BW)[2 * KP + 1]);
           }
@@ -771,7 +808,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
         }
         if (help_bar_or(flags[0] != 0)) break;
         if (hid == 0) {
-          mbar_arrive(pro_full);
+          if (ltile > 0) mbar_arrive(pro_full);  // the consumers prepared their first tile
           mbar_arrive(&band_ready[b]);
         }
       }
@@ -790,10 +827,15 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       // is Bw + rint(y).  One base per warp keeps a register per track free.  The helper warps
       // prepared y0 = x_mid - Bw, the FP32 coefficients (0 for a track that FP32 cannot decide,
       // whose y0 is 1/2), the warp's base and decision limit, and named the tile.
-      if (!warp_wait(pro_full, (uint32_t)(ltile & 1), flags, a.wait_ns)) break;
-      // (a plain load: the wait above acquired the helpers' write)
-      const int tile = reinterpret_cast<const int*>(const_cast<const int*>(flags))[2 + (ltile & 1)];
-      if (tile >= a.n_tiles) break;
+      // The first tile is this CTA's own and its consumers prepare it themselves (no earlier tile
+      // hides that prologue, and twelve warps do it four times as fast as three); each later one
+      // comes from the helpers, named in the tile ids (a plain load: the wait acquired the write).
+      int tile = (int)blockIdx.x;
+      if (ltile > 0) {
+        if (!warp_wait(pro_full, (uint32_t)((ltile - 1) & 1), flags, a.wait_ns)) break;
+        tile = reinterpret_cast<const int*>(const_cast<const int*>(flags))[2 + (ltile & 1)];
+        if (tile >= a.n_tiles) break;
+      }
       const int j = job_of(a, tile);
       const JobDesc& J = a.jobs[j];
       const int n_seg = J.n_seg, m = J.m;
@@ -801,6 +843,15 @@ __global__ void __launch_bounds__(kThreads, 1) eval_stat_kernel(const __grid_con
       int sp, s0, s1;
       tile_range(a, J, tile, j, &tile0, &sp, &s0, &s1);
       const long long tend = min(J.N, tile0 + J.tile_tracks);
+      if (ltile == 0) {
+        prologue_base<KP, CUTS>(J, tile0, tend, cwarp, lane, winfo);
+        __syncwarp();
+        int bmin = 0x7fffffff, bmax = -0x7fffffff;
+        prologue_tracks<KP, R, CUTS>(J, tile0, tend, ctid, lane, cbuf, winfo, inboxm, bmin, bmax);
+        prologue_box_part<KP, R>(cbuf, inboxm, ctid, 1, lane, bmin, bmax, bpart + cwarp * BW);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(parts_ready);
+      }
       // tracks in pairs for the packed FP32x2 arithmetic (an odd R gets an inactive partner):
       // track r is half (r & 1) of c2[r / 2][k] and y02[r / 2]
       constexpr int R2 = (R + 1) / 2;
