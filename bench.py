@@ -933,7 +933,9 @@ def run_served(args):
         tf, tb = dataset_tables(d, ("f32", "bf16"))
         ids[(d, "f32")] = srv.add_dataset(tf, basis)
         ids[(d, "bf16")] = srv.add_dataset(tb, basis)
-        f32_tables.append(dataset_tables(d, ("f32",))[0] if d < 4 else None)
+        # the plain path's own FP32 table of every dataset (the same data; its window sums and L2
+        # state are its own)
+        f32_tables.append(dataset_tables(d, ("f32",))[0])
     torch.cuda.synchronize()
 
     def coeffs_of(i):
@@ -1034,7 +1036,7 @@ def run_served(args):
     # the plain FP32 path: one request at a time, in arrival order, through tfs_eval_stat
     t_b0 = time.perf_counter()
     for i, (ta, d, N, dt) in enumerate(reqs):
-        T.eval_stat(f32_tables[d % 4], basis, coeffs_of(i), None, m=w.m, topk=16)
+        T.eval_stat(f32_tables[d], basis, coeffs_of(i), None, m=w.m, topk=16)
     base_sat_s = time.perf_counter() - t_b0
     lat = []
     t0 = time.perf_counter()
@@ -1042,7 +1044,7 @@ def run_served(args):
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        tb = f32_tables[d % 4]
+        tb = f32_tables[d]
         T.eval_stat(tb, basis, coeffs_of(i), None, m=w.m, topk=16)
         lat.append((time.perf_counter() - t0 - ta) * 1e3)
     t1 = time.perf_counter() - t0
