@@ -125,19 +125,19 @@ __device__ __forceinline__ double track_f(const ChirpJob& a, const double* c, do
 }
 
 __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_constant__ ChirpBatch B) {
-  __shared__ float4 s_wyq[16][16];            // sample m = l + 16 i at [i][l]: w(y), pi y, pi y^2
-  __shared__ float2 s_yq[16][16];             // y, y^2 (exact)
   __shared__ __align__(16) float2 s_buf[kCW][2][16][18];  // per half-warp transpose (rows padded to 16 B)
   __shared__ double s_c[kCW][32];             // the warp's track coefficients
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int hf = lane >> 4, l16 = lane & 15;  // half of the warp, lane within it
-  for (int m = tid; m < kM; m += kCThreads) {
-    const float s = sinpif((float)m / (float)kM);
-    const int mc = m - kM / 2;
-    const float y = (float)mc * (1.f / kM), q = (float)(mc * mc) * (1.f / (kM * kM));
-    s_wyq[m >> 4][m & 15] = make_float4(s * s, 3.14159265358979f * y, 3.14159265358979f * q, 0.f);
-    s_yq[m >> 4][m & 15] = make_float2(y, q);
+  // the window at this lane's samples m = l16 + 16 i (held in registers: read from shared memory
+  // they cost 48 wavefronts per pair, half of them bank conflicts), and y at i = 0, exact
+  float wreg[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float s = sinpif((float)(l16 + 16 * i) / (float)kM);
+    wreg[i] = s * s;
   }
+  const float y0 = (float)(l16 - kM / 2) * (1.f / kM);
   // e^{-2 pi i l16 j0 / 256}, j0 = 1..15 (exact arguments; j0 = 0 is 1)
   float2 tw[16];
   tw[0] = make_float2(1.f, 0.f);
@@ -260,16 +260,16 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
         // the phases first (in v[i].x, radians in [-pi, pi]), then sine and cosine
         if (__all_sync(0xffffffffu, fabsf(bs) <= 2.f)) {
           // |beta| <= 2: pi (2 delta0 y + beta y^2) lies in [-pi, pi] as it is
+          const float bsp = 3.14159265358979f * bs, d2p = 3.14159265358979f * d2;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float4 wyq = s_wyq[i][l16];
-            v[i].x = fmaf(bs, wyq.z, d2 * wyq.y);
+            const float y = y0 + 0.0625f * i, q = y * y;  // exact
+            v[i].x = fmaf(bsp, q, d2p * y);
           }
         } else {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float2 yq = s_yq[i][l16];
-            const float y = yq.x, q = yq.y;                        // y and y^2, exact
+            const float y = y0 + 0.0625f * i, q = y * y;             // y and y^2, exact
             const float p1 = bh * q;                               // exact
             const float r1 = p1 - 2.f * rintf(0.5f * p1);          // exact reduction modulo 2
             const float ph = r1 + fmaf(bl, q, d2 * y);
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kCThreads, 2) chirp_stat_kernel(const __grid_c
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const float wv = s_wyq[i][l16].x;
+          const float wv = wreg[i];
           float sn, cs;
           __sincosf(v[i].x, &sn, &cs);
           v[i] = make_float2(wv * cs, wv * sn);
