@@ -494,8 +494,8 @@ int tfs_topk(const float* val_in, int64_t N, int k, int64_t* idx, float* val, in
  * Ns[i] = 0 skips array i), idx[i] / val[i] device outputs of min(ks[i], Ns[i])
  * entries, each exactly what tfs_topk gives for that array alone (same order,
  * ties, -0 and NaN rules).  The host arrays vals, Ns, ks, idx, val (n entries)
- * are read during the call.  One set of 13 kernel launches covers up to 64
- * arrays (more take one set per 64), instead of 13 per array.  Device scratch
+ * are read during the call.  One set of 9 kernel launches covers up to 64
+ * arrays (more take one set per 64), instead of 9 per array.  Device scratch
  * (about 600 KB plus 4 bytes per 4096 elements) is stream-ordered; the call
  * returns without waiting unless stream is NULL. */
 int tfs_topk_batch(const float* const* vals, const int64_t* Ns, const int* ks, int n, int64_t* const* idx,

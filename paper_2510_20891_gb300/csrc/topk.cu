@@ -3,10 +3,13 @@
 // equal values ordered by lower index, -0.0 == +0.0, NaN below every number.
 //
 // Radix select on a monotone 32-bit key: four histogram passes of 8 bits
-// each fix the k-th largest key K*; one counting pass and one scan give each
-// chunk of the input the rank of its first element equal to K*, so the
-// (k - #{key > K*}) lowest-indexed equal elements are taken; a bitonic sort
-// of the <= 1024 selected (key, index) pairs orders the output.
+// each fix the k-th largest key K* (the last CTA of each pass picks the digit).
+// When every element equal to K* is among the k (the usual case: no tie at the
+// boundary), one pass collects the k elements with key >= K*.  Otherwise one
+// counting pass and one scan give each chunk of the input the rank of its
+// first element equal to K*, so the (k - #{key > K*}) lowest-indexed equal
+// elements are taken.  A bitonic sort of the <= 1024 selected (key, index)
+// pairs orders the output.
 #include "tfs_internal.cuh"
 
 namespace tfs {
@@ -19,6 +22,8 @@ constexpr int kPer = kChunk / kChunkThreads;
 
 struct TopkState {
   uint32_t prefix, mask, krem, ngt;
+  uint32_t done;  // CTAs of the current histogram pass that have merged their counts
+  uint32_t fast;  // every element equal to K* is taken: no ordering among them is needed
 };
 
 __device__ __forceinline__ uint32_t mono_key(float v) {
@@ -34,29 +39,26 @@ __global__ void topk_init(TopkState* s, uint32_t* hist, uint32_t k) {
     s->mask = 0;
     s->krem = k;
     s->ngt = 0;
+    s->done = 0;
+    s->fast = 0;
   }
   hist[threadIdx.x] = 0;
 }
 
-__global__ void topk_hist(const float* __restrict__ v, long long N, const TopkState* __restrict__ s,
-                          uint32_t* __restrict__ hist, int shift) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const uint32_t prefix = s->prefix, mask = s->mask;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const uint32_t key = mono_key(v[i]);
-    if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
-}
-
-// one CTA of 256 threads: pick the digit that holds the k_rem-th largest key
-__global__ void topk_select(TopkState* s, uint32_t* hist, int shift) {
+// After a CTA has added its counts to `hist`: the last CTA of the pass (of `n_cta`) picks the digit
+// that holds the k_rem-th largest key, records whether all keys equal to K* are taken (last pass),
+// and clears the histogram and the counter for the next pass.  256 threads.
+__device__ void merge_done_select(TopkState* s, uint32_t* hist, int shift, unsigned n_cta) {
   __shared__ uint32_t suf[257];
+  __shared__ bool last;
+  __threadfence();  // this thread's histogram atomics before the counter
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&s->done, 1u) == n_cta - 1u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   const int d = threadIdx.x;
-  suf[d] = hist[d];
+  suf[d] = __ldcg(&hist[d]);
   if (d == 0) suf[256] = 0;
   __syncthreads();
   // inclusive suffix sums (Hillis-Steele over 256 entries)
@@ -73,19 +75,38 @@ __global__ void topk_select(TopkState* s, uint32_t* hist, int shift) {
     s->prefix |= (uint32_t)d << shift;
     s->mask |= 255u << shift;
     s->krem = krem - above;
+    // in the last pass suf[d] - above keys equal K*: all of them are taken when that is k_rem
+    if (shift == 0) s->fast = suf[d] == krem ? 1u : 0u;
   }
   hist[d] = 0;  // ready for the next pass
+  if (d == 0) s->done = 0;
+}
+
+// 256 threads per CTA; the pass's last CTA selects the digit
+__global__ void topk_hist(const float* __restrict__ v, long long N, TopkState* s, uint32_t* hist, int shift) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t prefix = s->prefix, mask = s->mask;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t key = mono_key(v[i]);
+    if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+  merge_done_select(s, hist, shift, gridDim.x);
 }
 
 __global__ void topk_eqcount(const float* __restrict__ v, long long N, const TopkState* __restrict__ s,
                              uint32_t* __restrict__ cnt) {
   __shared__ uint32_t tot;
+  if (s->fast) return;  // the collecting pass needs no ranks
   if (threadIdx.x == 0) tot = 0;
   __syncthreads();
   const uint32_t kstar = s->prefix;
   const long long base = (long long)blockIdx.x * kChunk;
   uint32_t c = 0;
-  for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
+  for (int j = threadIdx.x; j < kChunk; j += kChunkThreads) {
     const long long i = base + j;
     if (i < N && mono_key(v[i]) == kstar) ++c;
   }
@@ -96,8 +117,9 @@ __global__ void topk_eqcount(const float* __restrict__ v, long long N, const Top
 }
 
 // exclusive scan of cnt[0..n) in place, one CTA of 1024 threads
-__global__ void topk_scan(uint32_t* cnt, int n) {
+__global__ void topk_scan(const TopkState* s, uint32_t* cnt, int n) {
   __shared__ uint32_t part[1024];
+  if (s->fast) return;
   const int per = (n + 1023) / 1024;
   const int b0 = threadIdx.x * per;
   uint32_t sum = 0;
@@ -124,6 +146,19 @@ __global__ void topk_collect(const float* __restrict__ v, long long N, TopkState
                              const uint32_t* __restrict__ eqbase, unsigned long long* __restrict__ cand, int k) {
   __shared__ uint32_t wsum[kChunkThreads / 32];
   const uint32_t kstar = s->prefix;
+  if (s->fast) {
+    // exactly k keys are >= K*: take them in any order (the sort orders them)
+    for (int t = threadIdx.x; t < kChunk; t += kChunkThreads) {
+      const long long i = (long long)blockIdx.x * kChunk + t;
+      if (i >= N) break;
+      const uint32_t key = mono_key(v[i]);
+      if (key >= kstar) {
+        const uint32_t pos = atomicAdd(&s->ngt, 1u);
+        if (pos < (uint32_t)k) cand[pos] = ((unsigned long long)key << 32) | (0xffffffffull - (unsigned long long)i);
+      }
+    }
+    return;
+  }
   const uint32_t need = s->krem;       // equal keys to take
   const uint32_t ngt = (uint32_t)k - need;
   const long long base = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPer;
@@ -166,11 +201,13 @@ __global__ void topk_sort(const float* __restrict__ v, long long N, const unsign
   __shared__ unsigned long long a[1024];
   const int t = threadIdx.x;
   a[t] = t < k ? cand[t] : 0ull;
+  int kp = 1;
+  while (kp < k) kp <<= 1;
   __syncthreads();
-  for (int size = 2; size <= 1024; size <<= 1) {
+  for (int size = 2; size <= kp; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       const int p = t ^ stride;
-      if (p > t) {
+      if (p > t && p < kp) {
         const bool desc = (t & size) == 0;
         const unsigned long long x = a[t], y = a[p];
         if (desc ? (x < y) : (x > y)) {
@@ -206,15 +243,12 @@ int topk_device(const float* v, int64_t N, int k, int64_t* idx_out, float* val_o
   const int nch = (int)((N + kChunk - 1) / kChunk);
   topk_init<<<1, 256, 0, st>>>(s, hist, (uint32_t)k);
   int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    topk_hist<<<grid, 256, 0, st>>>(v, N, s, hist, shift);
-    topk_select<<<1, 256, 0, st>>>(s, hist, shift);
-  }
+  for (int shift = 24; shift >= 0; shift -= 8) topk_hist<<<grid, 256, 0, st>>>(v, N, s, hist, shift);
   topk_eqcount<<<nch, kChunkThreads, 0, st>>>(v, N, s, cnt);
-  topk_scan<<<1, 1024, 0, st>>>(cnt, nch);
+  topk_scan<<<1, 1024, 0, st>>>(s, cnt, nch);
   topk_collect<<<nch, kChunkThreads, 0, st>>>(v, N, s, cnt, cand, k);
   topk_sort<<<1, 1024, 0, st>>>(v, N, cand, k, idx_out, val_out);
-  count_launch(13);
+  count_launch(9);
   TFS_CUDA(cudaGetLastError());
   return TFS_OK;
 }
@@ -268,7 +302,7 @@ extern "C" int tfs_topk_noalloc(const float* val_in, int64_t N, int k, int64_t* 
 // ---------------------------------------------------------------- segmented top-k over many jobs
 // The same selection for up to kTkJobs independent arrays at once (the per-chunk top-k of a batched
 // statistic launch, paper Sec. II.D keeping the best walkers of every chunk): every pass covers all
-// jobs, so a batch takes 13 launches whatever its number of jobs, and each job's result is that of
+// jobs, so a batch takes 9 launches whatever its number of jobs, and each job's result is that of
 // topk_device on the job alone (same passes, same order), bit for bit.
 namespace tfs {
 namespace {
@@ -310,11 +344,13 @@ __global__ void tkb_init(const __grid_constant__ TkArgs a) {
     s.mask = 0;
     s.krem = (uint32_t)a.jobs[j].k;
     s.ngt = 0;
+    s.done = 0;
+    s.fast = 0;
   }
   a.hist[j * 256 + threadIdx.x] = 0;
 }
 
-// one CTA per chunk of one job (flattened over all jobs)
+// one CTA per chunk of one job (flattened over all jobs); the job's last CTA selects its digit
 __global__ void tkb_hist(const __grid_constant__ TkArgs a, int shift) {
   __shared__ uint32_t h[256];
   const int j = tk_job_of(a, blockIdx.x);
@@ -323,7 +359,7 @@ __global__ void tkb_hist(const __grid_constant__ TkArgs a, int shift) {
   __syncthreads();
   const uint32_t prefix = a.state[j].prefix, mask = a.state[j].mask;
   const long long base = (long long)(blockIdx.x - a.chunk0[j]) * kChunk;
-  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+  for (int t = threadIdx.x; t < kChunk; t += kChunkThreads) {
     const long long i = base + t;
     if (i < J.N) {
       const uint32_t key = mono_key(J.v[i]);
@@ -332,45 +368,20 @@ __global__ void tkb_hist(const __grid_constant__ TkArgs a, int shift) {
   }
   __syncthreads();
   if (h[threadIdx.x]) atomicAdd(&a.hist[j * 256 + threadIdx.x], h[threadIdx.x]);
-}
-
-// one CTA of 256 threads per job: pick the digit that holds the job's k_rem-th largest key
-__global__ void tkb_select(const __grid_constant__ TkArgs a, int shift) {
-  __shared__ uint32_t suf[257];
-  const int j = blockIdx.x;
-  uint32_t* hist = a.hist + j * 256;
-  TopkState* s = a.state + j;
-  const int d = threadIdx.x;
-  suf[d] = hist[d];
-  if (d == 0) suf[256] = 0;
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const uint32_t add = (d + o < 256) ? suf[d + o] : 0u;
-    __syncthreads();
-    suf[d] += add;
-    __syncthreads();
-  }
-  const uint32_t krem = s->krem;
-  const uint32_t above = suf[d + 1];
-  __syncthreads();
-  if (above < krem && krem <= suf[d]) {
-    s->prefix |= (uint32_t)d << shift;
-    s->mask |= 255u << shift;
-    s->krem = krem - above;
-  }
-  hist[d] = 0;
+  merge_done_select(a.state + j, a.hist + j * 256, shift, (unsigned)J.nch);
 }
 
 __global__ void tkb_eqcount(const __grid_constant__ TkArgs a) {
   __shared__ uint32_t tot;
   const int j = tk_job_of(a, blockIdx.x);
   const TkJob& J = a.jobs[j];
+  if (a.state[j].fast) return;  // the collecting pass needs no ranks
   if (threadIdx.x == 0) tot = 0;
   __syncthreads();
   const uint32_t kstar = a.state[j].prefix;
   const long long base = (long long)(blockIdx.x - a.chunk0[j]) * kChunk;
   uint32_t c = 0;
-  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+  for (int t = threadIdx.x; t < kChunk; t += kChunkThreads) {
     const long long i = base + t;
     if (i < J.N && mono_key(J.v[i]) == kstar) ++c;
   }
@@ -384,6 +395,7 @@ __global__ void tkb_eqcount(const __grid_constant__ TkArgs a) {
 __global__ void tkb_scan(const __grid_constant__ TkArgs a) {
   __shared__ uint32_t part[1024];
   const int j = blockIdx.x;
+  if (a.state[j].fast) return;
   uint32_t* cnt = a.cnt + a.chunk0[j];
   const int n = a.jobs[j].nch;
   const int per = (n + 1023) / 1024;
@@ -415,9 +427,22 @@ __global__ void tkb_collect(const __grid_constant__ TkArgs a) {
   TopkState* s = a.state + j;
   unsigned long long* cand = a.cand + (size_t)j * 1024;
   const uint32_t kstar = s->prefix;
+  const long long chunk = blockIdx.x - a.chunk0[j];
+  if (s->fast) {
+    // exactly k keys are >= K*: take them in any order (the sort orders them)
+    for (int t = threadIdx.x; t < kChunk; t += kChunkThreads) {
+      const long long i = chunk * kChunk + t;
+      if (i >= J.N) break;
+      const uint32_t key = mono_key(J.v[i]);
+      if (key >= kstar) {
+        const uint32_t pos = atomicAdd(&s->ngt, 1u);
+        if (pos < (uint32_t)J.k) cand[pos] = ((unsigned long long)key << 32) | (0xffffffffull - (unsigned long long)i);
+      }
+    }
+    return;
+  }
   const uint32_t need = s->krem;
   const uint32_t ngt = (uint32_t)J.k - need;
-  const long long chunk = blockIdx.x - a.chunk0[j];
   const long long base = chunk * kChunk + (long long)threadIdx.x * kPer;
   uint32_t myeq = 0;
   for (int q = 0; q < kPer; ++q) {
@@ -458,11 +483,13 @@ __global__ void tkb_sort(const __grid_constant__ TkArgs a) {
   const unsigned long long* cand = a.cand + (size_t)j * 1024;
   const int t = threadIdx.x;
   x[t] = t < J.k ? cand[t] : 0ull;
+  int kp = 1;
+  while (kp < J.k) kp <<= 1;
   __syncthreads();
-  for (int size = 2; size <= 1024; size <<= 1) {
+  for (int size = 2; size <= kp; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       const int p = t ^ stride;
-      if (p > t) {
+      if (p > t && p < kp) {
         const bool desc = (t & size) == 0;
         const unsigned long long u = x[t], w = x[p];
         if (desc ? (u < w) : (u > w)) {
@@ -525,15 +552,12 @@ int topk_batch_device(const TopkTask* tasks, int n, void* ws, cudaStream_t st) {
     if (a.n == 0) continue;
     const unsigned chunks = (unsigned)a.chunk0[a.n];
     tkb_init<<<a.n, 256, 0, st>>>(a);
-    for (int shift = 24; shift >= 0; shift -= 8) {
-      tkb_hist<<<chunks, kChunkThreads, 0, st>>>(a, shift);
-      tkb_select<<<a.n, 256, 0, st>>>(a, shift);
-    }
+    for (int shift = 24; shift >= 0; shift -= 8) tkb_hist<<<chunks, kChunkThreads, 0, st>>>(a, shift);
     tkb_eqcount<<<chunks, kChunkThreads, 0, st>>>(a);
     tkb_scan<<<a.n, 1024, 0, st>>>(a);
     tkb_collect<<<chunks, kChunkThreads, 0, st>>>(a);
     tkb_sort<<<a.n, 1024, 0, st>>>(a);
-    count_launch(13);
+    count_launch(9);
     TFS_CUDA(cudaGetLastError());
   }
   return TFS_OK;

@@ -476,6 +476,23 @@ def test_topk_parity(T, N, k):
     assert np.array_equal(val.astype(np.float64), rv, equal_nan=True)
 
 
+@pytest.mark.parametrize("N", [9, 5000, 300_001])
+def test_topk_boundary_ties(T, N):
+    """Equal values at the k-th place: when all of them are among the k (k = 4, 9, 10 here) one pass
+    collects them without ranks, when some are left out (k = 6) the lowest indices are taken; in
+    both the output orders equal values by lower index."""
+    rng = np.random.default_rng(N)
+    v = (rng.permutation(N).astype(np.float32) + 1.0) / (N + 1.0)   # distinct values in (0, 1)
+    top = rng.choice(N, 9, replace=False)
+    v[top[:4]] = 3.0                                                # four equal maxima
+    v[top[4:]] = 2.0                                                # five equal values below them
+    for k in (4, 6, 9, 10):
+        idx, val = T.topk(v, k)
+        ri, rv = O.topk(v.astype(np.float64), k)
+        assert np.array_equal(idx, ri), k
+        assert np.array_equal(val.astype(np.float64), rv), k
+
+
 def test_topk_device_distinct_values(T):
     torch = pytest.importorskip("torch")
     v = torch.randn(3_000_001, device="cuda")
