@@ -94,7 +94,8 @@ __device__ double2* small_fft(double2* d0, double2* d1, int ncol, const FftPlan&
       const int k = j % Ns;
       double2 v[5];
       for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * step]);
+      if (Ns > 1)  // the first stage's twiddles are all 1
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * step]);
       dft_r(v, R, K);
       const int o = (j / Ns) * Ns * R + k;
       for (int r = 0; r < R; ++r) out[o + r * Ns] = v[r];
@@ -185,9 +186,11 @@ __global__ void sft_rows(const double2* __restrict__ Y, int N1, int N2, int RB, 
   }
 }
 
-// Step 3: real spectrum and normalised power, FP64, P [n_seg][n_bin].
+// Step 3: real spectrum and normalised power, FP64, P [n_seg][n_bin].  With E = z_k + conj(z_{N-k})
+// and O = z_k - conj(z_{N-k}), X_k = (E - i W_L^k O) / 2: the halving is exact, so it is left to the
+// per-bin scale (pscale4 = pscale / 4 for |X_k|^2), which gives the same bits.
 __global__ void sft_power(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
-                          const double* __restrict__ pscale, double* __restrict__ P) {
+                          const double* __restrict__ pscale4, double* __restrict__ P) {
   const int seg = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > N) return;
@@ -195,16 +198,14 @@ __global__ void sft_power(const double2* __restrict__ Z, int N, const double2* _
   const double2 zk = z[k == N ? 0 : k];
   const double2 zn0 = z[k == 0 ? 0 : N - k];
   const double2 zn = make_double2(zn0.x, -zn0.y);
-  const double2 e = cscale(cadd(zk, zn), 0.5);
-  const double2 o = cscale(csub(zk, zn), 0.5);
-  const double2 X = cadd(e, mul_mi(cmul(twU[k], o)));
-  P[(size_t)seg * (N + 1) + k] = (X.x * X.x + X.y * X.y) * pscale[k];
+  const double2 X2 = cadd(cadd(zk, zn), mul_mi(cmul(twU[k], csub(zk, zn))));  // 2 X_k
+  P[(size_t)seg * (N + 1) + k] = (X2.x * X2.x + X2.y * X2.y) * pscale4[k];
 }
 
 // Step 3 for the linear-chirp table: the complex spectrum scaled per bin, FP32 pairs
-// z [n_seg][n_bin] = X_k zscale_k.
+// z [n_seg][n_bin] = X_k zscale_k, computed as 2 X_k times zscale2 = zscale / 2 (the same bits).
 __global__ void sft_cspec(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
-                          const double* __restrict__ zscale, float2* __restrict__ zout) {
+                          const double* __restrict__ zscale2, float2* __restrict__ zout) {
   const int seg = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > N) return;
@@ -212,10 +213,8 @@ __global__ void sft_cspec(const double2* __restrict__ Z, int N, const double2* _
   const double2 zk = z[k == N ? 0 : k];
   const double2 zn0 = z[k == 0 ? 0 : N - k];
   const double2 zn = make_double2(zn0.x, -zn0.y);
-  const double2 e = cscale(cadd(zk, zn), 0.5);
-  const double2 o = cscale(csub(zk, zn), 0.5);
-  const double2 X = cadd(e, mul_mi(cmul(twU[k], o)));
-  zout[(size_t)seg * (N + 1) + k] = make_float2((float)(X.x * zscale[k]), (float)(X.y * zscale[k]));
+  const double2 X2 = cadd(cadd(zk, zn), mul_mi(cmul(twU[k], csub(zk, zn))));  // 2 X_k
+  zout[(size_t)seg * (N + 1) + k] = make_float2((float)(X2.x * zscale2[k]), (float)(X2.y * zscale2[k]));
 }
 
 }  // namespace
@@ -479,8 +478,8 @@ struct SftPlan {
   int N = 0, N1 = 0, N2 = 0, CB = 1, RB = 1;
   FftPlan p1{}, p2{};
   double* win = nullptr;      // [L]
-  double* pscale = nullptr;   // [n_bin]: 4 dt / (sum w^2 S_n), 0 where unusable
-  double* zscale = nullptr;   // [n_bin]: sqrt(4 dt / (sum w^2 S_ref)) S_ref / S_n, 0 where unusable
+  double* pscale = nullptr;   // [n_bin]: 4 dt / (sum w^2 S_n) / 4, 0 where unusable (scales |2 X_k|^2)
+  double* zscale = nullptr;   // [n_bin]: sqrt(4 dt / (sum w^2 S_ref)) S_ref / S_n / 2, 0 where unusable
   float* wt = nullptr;        // [n_bin]: S_ref / S_n, 0 where unusable
   double s_ref = 1.0;         // median of the usable S_n (keeps the chirp table's values near 1)
   double2* tw1 = nullptr;     // [N1]
@@ -569,8 +568,14 @@ static int make_sft_plan(int64_t L, double dt, int window, const double* psd, in
     if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   };
   up((void**)&s->win, win.data(), L * 8);
-  up((void**)&s->pscale, pscale.data(), n_bin * 8);
-  up((void**)&s->zscale, zscale.data(), n_bin * 8);
+  // on the device the scales take the untangling's exact factor 1/2 of X_k (sft_power, sft_cspec)
+  std::vector<double> pscale4(n_bin), zscale2(n_bin);
+  for (int k = 0; k < n_bin; ++k) {
+    pscale4[k] = 0.25 * pscale[k];
+    zscale2[k] = 0.5 * zscale[k];
+  }
+  up((void**)&s->pscale, pscale4.data(), n_bin * 8);
+  up((void**)&s->zscale, zscale2.data(), n_bin * 8);
   up((void**)&s->wt, wt.data(), n_bin * 4);
   s->s_ref = s_ref;
   up((void**)&s->tw1, tw1.data(), (size_t)N1 * 16);
