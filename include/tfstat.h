@@ -175,8 +175,10 @@ int tfs_basis_free(tfs_basis* b);
  * table's.  N may be 0.  stat may be NULL only if topk > 0 (then the
  * per-track values are kept in library scratch).  mem = HOST without a tie
  * report: the inputs go up in chunks (whole rounds of full tiles over the SMs,
- * at least 64 MB of coefficients each, at most 8 chunks) on a library stream,
- * each chunk evaluated on `stream` by its own launch as soon as it has arrived
+ * at least 64 MB of coefficients each, at most 6 chunks) on a library stream,
+ * each chunk evaluated by its own launch as soon as it has arrived (the
+ * launches alternate between `stream` and a library stream that first waits
+ * for the work enqueued on `stream`; `stream` waits for both before the top-k)
  * and its values read back while the next one runs; the bins are unchanged and
  * the statistic agrees with the one-launch result within FP32 rounding (which
  * pairs the FP32 filter leaves to the FP64 fix-up depends on the tiling).  Host

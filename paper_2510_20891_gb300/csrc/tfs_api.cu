@@ -329,10 +329,11 @@ static size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 // evaluated by its own launch as soon as it has arrived, so that the upload of chunk c+1
 // overlaps the statistic of chunk c.  A chunk is a whole number of rounds of full tiles
 // over the SMs (so that the chunks' launches together take no more rounds than one launch
-// over all the tracks), at least 64 MB of coefficients, at most 4 chunks (each launch costs
-// about 0.1 ms of start-up and drain that a longer launch pays once: 10^7 one-year tracks from
-// host buffers ran 4.71 ms per step in 8 chunks, 4.49 in 4, 4.56 in 3).  Returns the tracks per
-// chunk (N: no chunking).
+// over all the tracks), at least 64 MB of coefficients, at most 6 chunks (a launch costs about
+// 0.1 ms of start-up and drain, partly hidden by alternating the launches over two streams:
+// 10^7 one-year tracks from host buffers ran 3.91 ms per step in 4 chunks, 3.80 in 5 (3 rounds
+// each, the most this cap allows), 3.92 in 8; 4.01 in 4 chunks on one stream).  Returns the
+// tracks per chunk (N: no chunking).
 static int64_t host_chunk_tracks(const EvalLaunch& L, int64_t N, int K) {
   int div = 1;
   {
@@ -342,7 +343,7 @@ static int64_t host_chunk_tracks(const EvalLaunch& L, int64_t N, int K) {
   }
   const int64_t round = eval_round_tracks(L.jobs[0].sp->KP, L.jobs[0].cuts != 0, div);
   const int64_t min_tracks = ((int64_t)64 << 20) / (8 * (int64_t)K);
-  const int64_t r = std::max<int64_t>({1, (min_tracks + round - 1) / round, (N + 4 * round - 1) / (4 * round)});
+  const int64_t r = std::max<int64_t>({1, (min_tracks + round - 1) / round, (N + 6 * round - 1) / (6 * round)});
   return r * round >= N ? N : r * round;
 }
 
@@ -364,7 +365,7 @@ struct CrossBuf {
 // Side streams of one call, drained before the call's scratch is freed (declare after the
 // Arena and any CrossBuf so that this is destroyed first) and on every early return.
 struct SideStreams {
-  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> ev;
   int init() {
     for (auto& x : s) TFS_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
@@ -647,32 +648,41 @@ int tfs_eval_stat(const tfs_table* table, const tfs_basis* basis_c, const double
               g_dbg_last[0], g_dbg_last[1], (long long)g_dbg_last[2], (long long)g_dbg_last[3]);
 #endif
   } else {
-    // uploads on side stream 0, launches on `stream` as each chunk arrives, the per-track
-    // values read back on side stream 1 as each launch ends.  The read-backs are enqueued after
-    // every upload and launch: a copy into pageable memory returns only once it is done, and
-    // enqueued inside the loop it would hold back the next chunk's upload.
+    // uploads on side stream 0; the launches, each as soon as its chunk has arrived, alternate
+    // between `stream` and side stream 2 (after everything enqueued on `stream` so far), so that
+    // a launch's first tile and its last CTAs overlap its neighbours' (no CTA of the kernel waits
+    // for another, so two launches may share the SMs in any way); the per-track values are read
+    // back on side stream 1 as each launch ends.  The read-backs are enqueued after every upload
+    // and launch: a copy into pageable memory returns only once it is done, and enqueued inside
+    // the loop it would hold back the next chunk's upload.
+    rc = side.order(st, side.s[2]);
+    if (rc) return rc;
     std::vector<cudaEvent_t> ran;
-    for (int64_t t0 = 0; t0 < N; t0 += per) {
+    int ci = 0;
+    for (int64_t t0 = 0; t0 < N; t0 += per, ++ci) {
       const int64_t n = std::min(per, N - t0);
+      cudaStream_t xs = (ci & 1) ? side.s[2] : st;
       TFS_CUDA(cudaMemcpyAsync(up_c + t0 * K, coeffs + t0 * K, (size_t)n * K * 8,
                                cudaMemcpyHostToDevice, side.s[0]));
       if (f_ref)
         TFS_CUDA(cudaMemcpyAsync(up_f + t0, f_ref + t0, (size_t)n * 8, cudaMemcpyHostToDevice,
                                  side.s[0]));
-      rc = side.order(side.s[0], st);
+      rc = side.order(side.s[0], xs);
       if (rc) return rc;
       EvalJob Jc{table, basis, sp, d_c + t0 * K, d_f ? d_f + t0 : nullptr, n, m, d_stat + t0, nullptr};
       EvalLaunch Lc{&Jc, 1, d_tc, d_tt, d_ts, 0, d_status};
-      rc = launch_eval(Lc, EvalTuning(), st);
+      rc = launch_eval(Lc, EvalTuning(), xs);
       if (rc) return rc;
       if (stat) {
         cudaEvent_t e;
         rc = side.event(&e);
         if (rc) return rc;
-        TFS_CUDA(cudaEventRecord(e, st));
+        TFS_CUDA(cudaEventRecord(e, xs));
         ran.push_back(e);
       }
     }
+    rc = side.order(side.s[2], st);
+    if (rc) return rc;
     for (size_t c = 0; c < ran.size(); ++c) {
       const int64_t t0 = (int64_t)c * per, n = std::min(per, N - t0);
       TFS_CUDA(cudaStreamWaitEvent(side.s[1], ran[c], 0));
