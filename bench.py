@@ -701,16 +701,27 @@ def run_tpl_search(args):
         res = de.run(n_iter=n_iter, U_full=U)
     # the captured iteration is counted once by the library; its other replays are added here
     launches = L.tfs_kernel_launches() - launches0 + de.uncounted_launches
-    # device time of one iteration's batched statistic launch (events around an uncaptured call)
-    coeffs = [torch.tensor(cmin + (cmax - cmin) * rng.random((W, w.K)), device="cuda") for _ in cs.sizes]
-    stats = [torch.empty(W, device="cuda") for _ in cs.sizes]
-    jobs = cs.jobs(coeffs, m=w.m, stats=stats, segment_cuts=True, statistic=args.statistic)
+    # device time of one iteration's batched statistic launch (events around an uncaptured call) on
+    # the trial walkers of the search's last iteration (uniform draws from the prior box leave many
+    # tracks outside the band, whose pairs cost far less, and the converged population shares its
+    # bands more than the proposals do)
+    jobs = de.trial_jobs
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     cs.launch(jobs, args.statistic, dev_status=status)
+    # replayed from a CUDA graph, as in the search, so that no host time falls between launches
+    # (its kernels are not added to gpu_launches: they run after the timed search)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            cs.launch(jobs, args.statistic, dev_status=status, stream=side.cuda_stream)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(20):
-        cs.launch(jobs, args.statistic, dev_status=status)
+        g.replay()
     e1.record()
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / 20
@@ -769,11 +780,13 @@ def run_tpl_search(args):
                        "walkers": W, "initial": 1024, "iterations": n_iter, "table_dtype": args.dtype,
                        "launch_shape": shape, "statistic": args.statistic,
                        "l2": "the 12.6 MB table and every chunk's walkers stay in L2"},
-            "search": {"evaluations": res.evaluations, "seconds": res.seconds, "segment_cuts": True,
+            "search": {"evaluations": res.evaluations, "seconds": res.seconds, "setup_s": de.t_setup,
+                       "iterations_s": de.t_iter, "segment_cuts": True,
                        "best_chunk_segments": cs.sizes[best], "best_stat": float(res.stat[best]),
                        "best_normalised": None if chirp else float(res.normalised[best]),
                        "injection": {k: float(v) for k, v in inj.items() if k != "kind"}},
-            "breakdown_ms": {"batched_statistic_per_iteration": batch_ms},
+            "breakdown_ms": {"batched_statistic_per_iteration": batch_ms,
+                             "iteration": 1e3 * de.t_iter / max(1, n_iter)},
             "roofline": roof,
             "e2e": {"value": res.evaluations / res.seconds, "unit": "evals/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,

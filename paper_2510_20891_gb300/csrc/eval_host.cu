@@ -171,19 +171,44 @@ static int launch_eval_jobs(const EvalLaunch& L, const EvalTuning& tune, cudaStr
     qpitch_max = std::max(qpitch_max, D.qpitch);
   }
   if (nt == 0) return TFS_OK;
-  // Few track tiles (small jobs): split each job's segments over several tiles so that every
-  // SM gets work, at least 16 segments per tile; the tiles' partial sums are added in segment
-  // order by a second small kernel.
+  // Few track tiles (small jobs): split the jobs' segments over several tiles so that every
+  // SM gets work; the tiles' partial sums are added in segment order by a second small kernel.
+  // A tile's time grows with its segments, so the split balances them: the longest tile gets
+  // the fewest whole 32-segment blocks for which all tiles still fit one per SM (so a job of
+  // many segments takes more tiles than a short one), and no tile has fewer than 16 segments.
   const long long sms_all = sm_count();
   if (!bins && nt < sms_all && !split_jobs) {
-    const int S = (int)std::min<long long>(8, sms_all / nt);
-    if (S > 1) {
+    long long work = 0;  // track tiles x segments
+    int seg_max_all = 1;
+    for (int i = 0; i < L.n_jobs; ++i) {
+      const JobDesc& D = a.jobs[i];
+      const long long ntj = D.N > 0 ? (D.N + D.tile_tracks - 1) / D.tile_tracks : 0;
+      work += ntj * D.n_seg;
+      seg_max_all = std::max(seg_max_all, D.n_seg);
+    }
+    const auto split_of = [](int n_seg, long long cap) {
+      return (int)std::max<long long>(1, std::min<long long>((n_seg + cap - 1) / cap, n_seg / 16));
+    };
+    long long cap = std::max<long long>(kSegTile, (work + sms_all - 1) / sms_all);
+    cap = (cap + kSegTile - 1) / kSegTile * kSegTile;
+    for (; cap < seg_max_all; cap += kSegTile) {
+      long long units = 0;
+      for (int i = 0; i < L.n_jobs; ++i) {
+        const JobDesc& D = a.jobs[i];
+        const long long ntj = D.N > 0 ? (D.N + D.tile_tracks - 1) / D.tile_tracks : 0;
+        const int Sj = split_of(D.n_seg, cap);
+        const int chunk = ((D.n_seg + Sj - 1) / Sj + kSegTile - 1) / kSegTile * kSegTile;
+        units += ntj * ((D.n_seg + chunk - 1) / chunk);
+      }
+      if (units <= sms_all) break;
+    }
+    if (cap < seg_max_all) {
       nt = 0;
       part_floats = 0;
       for (int i = 0; i < L.n_jobs; ++i) {
         JobDesc& D = a.jobs[i];
         const long long ntj = D.N > 0 ? (D.N + D.tile_tracks - 1) / D.tile_tracks : 0;
-        const int Sj = std::max(1, std::min(S, D.n_seg / 16));
+        const int Sj = split_of(D.n_seg, cap);
         // chunks of whole 32-segment blocks: the FP32 block sums are those of an unsplit launch
         D.seg_chunk = ((D.n_seg + Sj - 1) / Sj + kSegTile - 1) / kSegTile * kSegTile;
         D.seg_split = (D.n_seg + D.seg_chunk - 1) / D.seg_chunk;

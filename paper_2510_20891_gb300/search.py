@@ -121,6 +121,8 @@ class DESearch:
         self.statistic = statistic  # "nearest" (nearest-bin power sums) or "chirp" (the paper's S_alpha)
         self.uncounted_launches = 0  # kernels of graph replays beyond the captured one (set by run)
         self.t_setup = self.t_iter = 0.0  # wall seconds of the last run's set-up and iterations
+        self.population = None  # the last run's walkers [n_chunks * n_walkers, K] (device)
+        self.trial_jobs = None  # the last run's batch of trial walkers (its last iteration's proposals)
 
     def _initial(self, U_chunk):
         """n_init candidates uniform in the prior box, each track shifted by a constant so that
@@ -163,6 +165,7 @@ class DESearch:
         views = [ct[i * W:(i + 1) * W] for i in range(n_ch)]
         stats = [s_trial[i * W:(i + 1) * W] for i in range(n_ch)]
         trial_jobs = s.jobs(views, m=self.m, stats=stats, segment_cuts=self.cuts, statistic=self.statistic)
+        self.trial_jobs = trial_jobs
         # the random draws of every iteration (r1 != r2 != t within the walker's own chunk,
         # F_DE ~ U[0.3, 1.5]) come from a counter-based generator on the device, keyed by one
         # seed and an iteration number that each draw advances
@@ -213,6 +216,7 @@ class DESearch:
         torch.cuda.synchronize()
         self.t_iter = time.perf_counter() - t_it  # the iterations (capture included), synchronised
         secs = time.perf_counter() - t0
+        self.population = c
         st_h = st.cpu().numpy().reshape(n_ch, W)
         c_h = c.cpu().numpy().reshape(n_ch, W, K)
         best = st_h.argmax(axis=1)
