@@ -189,17 +189,22 @@ __global__ void sft_rows(const double2* __restrict__ Y, int N1, int N2, int RB, 
 // Step 3: real spectrum and normalised power, FP64, P [n_seg][n_bin].  With E = z_k + conj(z_{N-k})
 // and O = z_k - conj(z_{N-k}), X_k = (E - i W_L^k O) / 2: the halving is exact, so it is left to the
 // per-bin scale (pscale4 = pscale / 4 for |X_k|^2), which gives the same bits.
-__global__ void sft_power(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
-                          const double* __restrict__ pscale4, double* __restrict__ P) {
-  const int seg = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > N) return;
+__device__ __forceinline__ double power_bin(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
+                                            const double* __restrict__ pscale4, int seg, int k) {
   const double2* z = Z + (size_t)seg * N;
   const double2 zk = z[k == N ? 0 : k];
   const double2 zn0 = z[k == 0 ? 0 : N - k];
   const double2 zn = make_double2(zn0.x, -zn0.y);
   const double2 X2 = cadd(cadd(zk, zn), mul_mi(cmul(twU[k], csub(zk, zn))));  // 2 X_k
-  P[(size_t)seg * (N + 1) + k] = (X2.x * X2.x + X2.y * X2.y) * pscale4[k];
+  return (X2.x * X2.x + X2.y * X2.y) * pscale4[k];
+}
+
+__global__ void sft_power(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
+                          const double* __restrict__ pscale4, double* __restrict__ P) {
+  const int seg = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  P[(size_t)seg * (N + 1) + k] = power_bin(Z, N, twU, pscale4, seg, k);
 }
 
 // Step 3 for the linear-chirp table: the complex spectrum scaled per bin, FP32 pairs
@@ -320,6 +325,18 @@ __global__ void dequantise_rows(const void* __restrict__ data, const float* __re
     const double v = load_q<DT>(row, k);
     P[(size_t)seg * n_bin + k] = DT == TFS_F8E4M3 ? (double)((float)v * s) : v;
   }
+}
+
+// Step 3 straight into an FP32, BF16 or FP16 table: the elementwise rounding that quantise_rows
+// would store from sft_power's output (FP8 needs each row's scale first: it keeps both passes).
+template <int DT>
+__global__ void sft_power_store(const double2* __restrict__ Z, int N, const double2* __restrict__ twU,
+                                const double* __restrict__ pscale4, void* __restrict__ data, int row_stride) {
+  const int seg = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  void* row = static_cast<char*>(data) + (size_t)seg * row_stride * (DT == TFS_F32 ? 4 : 2);
+  store_q<DT>(row, k, power_bin(Z, N, twU, pscale4, seg, k), 1.0);
 }
 
 int quantise_into(const double* P, int64_t ld, tfs_table* t, cudaStream_t st) {
@@ -638,7 +655,8 @@ static int run_sft(const SftPlan* p, const double* d_x, tfs_table* t, cudaStream
   double* P = nullptr;
   TFS_CUDA(cudaMallocAsync((void**)&Y, nz * 16, st));
   if (p->N2 > 1) TFS_CUDA(cudaMallocAsync((void**)&Z, nz * 16, st));
-  TFS_CUDA(cudaMallocAsync((void**)&P, (size_t)n_seg * n_bin * 8, st));
+  const bool f8 = t->dtype == TFS_F8E4M3;
+  if (f8) TFS_CUDA(cudaMallocAsync((void**)&P, (size_t)n_seg * n_bin * 8, st));
   dim3 g1((p->N2 + p->CB - 1) / p->CB, (unsigned)n_seg);
   sft_cols<<<g1, 256, p->sm1, st>>>(d_x, p->win, (int)p->L, p->N1, p->N2, p->CB, p->p1, p->tw1, p->twN, Y);
   count_launch();
@@ -650,13 +668,24 @@ static int run_sft(const SftPlan* p, const double* d_x, tfs_table* t, cudaStream
     Zp = Z;
   }
   dim3 g3((unsigned)((n_bin + 255) / 256), (unsigned)n_seg);
-  sft_power<<<g3, 256, 0, st>>>(Zp, p->N, p->twU, p->pscale, P);
+  const int rs = (int)t->row_stride;
+  switch (t->dtype) {
+    case TFS_F32: sft_power_store<TFS_F32><<<g3, 256, 0, st>>>(Zp, p->N, p->twU, p->pscale, t->data, rs); break;
+    case TFS_BF16: sft_power_store<TFS_BF16><<<g3, 256, 0, st>>>(Zp, p->N, p->twU, p->pscale, t->data, rs); break;
+    case TFS_F16: sft_power_store<TFS_F16><<<g3, 256, 0, st>>>(Zp, p->N, p->twU, p->pscale, t->data, rs); break;
+    case TFS_F8E4M3: sft_power<<<g3, 256, 0, st>>>(Zp, p->N, p->twU, p->pscale, P); break;
+    default:
+      cudaFreeAsync(Y, st);
+      if (Z) cudaFreeAsync(Z, st);
+      set_error("bad dtype");
+      return TFS_ERR_INVALID_ARG;
+  }
   count_launch();
   cudaError_t e = cudaGetLastError();
-  int rc = e == cudaSuccess ? quantise_into(P, n_bin, t, st) : cuda_fail(e, "SFT kernels");
+  int rc = e == cudaSuccess ? (f8 ? quantise_into(P, n_bin, t, st) : TFS_OK) : cuda_fail(e, "SFT kernels");
   cudaFreeAsync(Y, st);
   if (Z) cudaFreeAsync(Z, st);
-  cudaFreeAsync(P, st);
+  if (P) cudaFreeAsync(P, st);
   return rc;
 }
 
